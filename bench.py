@@ -1,0 +1,323 @@
+"""Throughput of the kinetic Monte Carlo step on GB300 (particle-steps/s).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--lam L]
+                    [--impl ours|reference]
+
+A step is one pass of the whole hot path: closest-candidate search, pairing,
+CM scattering, free flight and walls, binning (histogram, scan, counting-sort
+scatter) and per-c-bin moments.  Default workload: the 16M-particle FP32 Sod
+tube with 2000 c-bins at lambda/L = 1e-3.  The timed region runs K steps
+launched kernel by kernel with CUDA events on the library's stream, bracketed
+by a barrier and device synchronisation; the state (16M x 64 B x 2 buffers)
+is far larger than L2, so no flush is needed between steps.
+
+The reference arm (--impl reference) times the CPU oracle on the host cores,
+on a bounded slice of the same workload (central c-bins at full density).
+Under torchrun every rank runs its own replica (weak scaling, no collective on
+the data path); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/sec and HBM GB/s fraction on 1 GB300; batched vs plain at fixed L1 error"
+UNIT = "particle-steps/s"
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [ln.strip().split(",") for ln in self.file.read().strip().splitlines() if ln.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(n, n_keys, n_bins, frac_paired, phase):
+    """Bytes each kernel must move at least (binary32 state), per launch.
+    State of a particle: position 12 B + id 4 B, velocity 12 B + instance 4 B."""
+    if phase == "search":
+        return n * (32 + 4)                    # read own state once, write closest candidate
+    if phase == "move":
+        return n * (32 + 4 + 4 + 32 + 4 + 4) + n * frac_paired * 32 + n * 4 + n_bins * 72 * 2
+    if phase == "scan":
+        return n_keys * (4 + 4 + 4)            # read count, write start, clear count
+    if phase == "scatter":
+        return n * (4 + 4 + 4 + 32 + 32)       # key, slot, start[key], read B, write A
+    return 0
+
+
+def make_workload(args):
+    from paper_1210_8084_gb300 import inputs
+    w = dict(inputs.WORKLOADS[args.workload])
+    if args.lam is not None:
+        w["lam"] = args.lam
+    if args.n is not None:
+        w["n"] = args.n
+    return w
+
+
+def ours(args):
+    import torch
+    import paper_1210_8084_gb300 as k
+    from paper_1210_8084_gb300 import inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    w = make_workload(args)
+    n = w["n"]
+    pos, vel = inputs.make_state(w, seed=w["seed"] + rank)
+    dtype = np.float32 if w["precision"] == 32 else np.float64
+    pos = np.ascontiguousarray(pos, dtype=dtype)
+    vel = np.ascontiguousarray(vel, dtype=dtype)
+    stream = torch.cuda.Stream()
+    cfg = k.make_config(dim_pos=w["dim_pos"], n_cells=w["n_cells"], lo=w["lo"], hi=w["hi"], bc=w["bc"],
+                        lam=w["lam"], dt=w["dt"], seed=w["seed"] + rank, precision=w["precision"],
+                        stream=stream.cuda_stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---------------- device-resident throughput (inputs already in HBM)
+    sim = k.Simulation(cfg, pos, vel)
+    info = sim.info()
+    sim.step_profiled(args.warmup, want_moments=1)
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    barrier()
+    prof = sim.step_profiled(args.steps, want_moments=1)
+    barrier()
+    clk = clocks.stop()
+    elapsed_ms = prof["total"]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    raw, der, glob = sim.moments()
+    pairs = float(glob[0, 6])
+    frac_paired = 2 * pairs / n
+    sim.close()
+
+    # ---------------- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin_pos = torch.from_numpy(pos).pin_memory()
+        pin_vel = torch.from_numpy(vel).pin_memory()
+        mom_mask = k.KMC_MOM_RAW | k.KMC_MOM_DERIVED | k.KMC_MOM_GLOBAL
+        barrier()
+        t0 = time.perf_counter()
+        h = k.kmc_init(cfg, n, pin_pos.numpy(), pin_vel.numpy(), k.KMC_WHERE_HOST)
+        mom = torch.empty(k.kmc_moments_size(h, mom_mask), dtype=torch.float64).pin_memory()
+        for _ in range(args.steps):
+            k.kmc_step(h, 1, 1)
+            k.kmc_moments(h, mom.numpy(), k.KMC_WHERE_HOST, mom_mask)
+        k.kmc_get_state(h, pin_pos.numpy(), pin_vel.numpy(), k.KMC_WHERE_HOST)
+        k.kmc_free(h)
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        state_bytes = pos.nbytes + vel.nbytes
+        e2e = {"value": n * world * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(state_bytes / args.steps),
+               "d2h_bytes_per_step": int(mom.numel() * 8 + state_bytes / args.steps)}
+
+    if rank != 0:
+        return None
+
+    # ---------------- roofline of the dominant kernel
+    peaks, peak_src = measured_peaks()
+    phases = {p: prof[p] / args.steps for p in ("search", "move", "scan", "scatter", "finalize", "clear")}
+    dom = max(("search", "move", "scan", "scatter"), key=lambda p: phases[p])
+    ab = algorithmic_bytes(n, info.n_search_cells, info.n_bins, frac_paired, dom)
+    achieved = ab / (phases[dom] * 1e-3) / 1e9
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_src,
+            "ms_per_launch": round(phases[dom], 4), "algorithmic_bytes_per_launch": int(ab)}
+    value = n * world * args.steps / (elapsed_ms * 1e-3)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if w["precision"] == 32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload} lambda/L={w['lam']:g}", "n_particles": n,
+                   "n_cells": list(w["n_cells"]), "dt": w["dt"], "precision": w["precision"],
+                   "search_cells": int(info.n_search_cells), "sub_cells": list(info.sub_cells),
+                   "l2": "no flush: state 2 x %.2f GB > 129 MB L2" % (n * 64 / 1e9),
+                   "parallelism": f"replicas x{world}"},
+        "phase_ms_per_step": {p: round(v, 4) for p, v in phases.items()},
+        "collision_fraction": round(frac_paired, 4),
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": 6 * args.steps,
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_slice_bins)
+    return out
+
+
+def oracle_slice(w, n_bins_slice, seed=0):
+    """Central c-bins of the workload at full density: the same particles per
+    c-bin and per neighbourhood as the full run."""
+    from paper_1210_8084_gb300 import inputs
+    n, ncx = w["n"], w["n_cells"][0]
+    dx = (w["hi"][0] - w["lo"][0]) / ncx
+    half = n_bins_slice // 2
+    lo = (0.5 - half * dx, w["lo"][1], w["lo"][2])
+    hi = (0.5 + half * dx, w["hi"][1], w["hi"][2])
+    # particles of the full tube that fall in the slice
+    n_l = int(round(n * 8 / 9))
+    dens_l = n_l / 0.5
+    dens_r = (n - n_l) / 0.5
+    n_sl = int(round(dens_l * half * dx))
+    n_sr = int(round(dens_r * half * dx))
+    pl, vl = inputs.sod_tube(2 * n_sl, seed, lo=lo, hi=hi, rho=(1.0, 1.0), p=(1.0, 1.0))
+    pr, vr = inputs.sod_tube(2 * n_sr, seed + 1, lo=lo, hi=hi, rho=(1.0, 1.0), p=(0.8, 0.8))
+    pos = np.concatenate([pl[pl[:, 0] < 0.5][:n_sl], pr[pr[:, 0] >= 0.5][:n_sr]])
+    vel = np.concatenate([vl[pl[:, 0] < 0.5][:n_sl], vr[pr[:, 0] >= 0.5][:n_sr]])
+    return pos, vel, lo, hi
+
+
+def cpu_baseline(w, n_bins_slice=8, steps=1):
+    import oracle
+    pos, vel, lo, hi = oracle_slice(w, n_bins_slice)
+    m = pos.shape[0]
+    nbar = w["n"] / 1.0
+    P = oracle.make_params(w["dim_pos"], (n_bins_slice, 1, 1), lo, hi, w["bc"],
+                           R2=oracle.contact_R2(w["lam"], 0.0, nbar), dt=w["dt"], seed=0,
+                           decide32=w["precision"] == 32)
+    t0 = time.perf_counter()
+    for s in range(steps):
+        P.step = s
+        pos, vel = oracle.step(P, pos, vel)[:2]
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": m * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle", "particles": m,
+            "sample": f"{steps} oracle step(s) of the {n_bins_slice} central c-bins at full density: "
+                      f"{m} particles with the full run's neighbourhood occupancy, {el:.2f} s"}
+
+
+def reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    w = make_workload(args)
+    samples = []
+    for s in range(args.warmup + args.steps):
+        r = cpu_baseline(w, args.ref_slice_bins)
+        if s >= args.warmup:
+            samples.append(r)
+    value = statistics.median([r["value"] for r in samples])
+    n_part = samples[0]["particles"]
+    cb = dict(samples[0])
+    cb["value"] = value
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_part / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload} lambda/L={w['lam']:g}", "n_particles": w["n"],
+                   "n_cells": list(w["n_cells"]), "sample_bins": args.ref_slice_bins},
+        "cpu_baseline": cb,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="sod1d_fp32_16M")
+    ap.add_argument("--lam", type=float, default=None)
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-slice-bins", type=int, default=8)
+    ap.add_argument("--ref-slice-bins", type=int, default=2)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    out = reference(args) if args.impl == "reference" else ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

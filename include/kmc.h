@@ -1,0 +1,189 @@
+/*
+ * kmc.h -- C ABI of the GB300 (sm_103a) test-particle kinetic Monte Carlo step
+ * of Sagert et al., "Hydrodynamic Shock Wave Studies within a Kinetic Monte Carlo
+ * Approach" (arXiv:1210.8084).
+ *
+ * One step (Sect. "Simulation setup", Fig. 2 flow chart):
+ *   1. bin particles by cell key (c-bins, Sect. "Simulation setup");
+ *   2. for every particle, the closest collision candidate in its 3^D
+ *      neighbourhood of c-bins that passes the PoCA acceptance test
+ *      (negative crossing number chi, Eq. c_value; real overlap times,
+ *      Eqs. collision_time/collision_time2; minimum distance, criterion 3);
+ *   3. keep only unambiguous (mutually closest) pairs;
+ *   4. isotropic elastic scattering in the pair's centre-of-mass frame;
+ *   5. split free flight r + v_old t_poca + v_new (dt - t_poca) (Eqs. 12-14),
+ *      plain free flight r + v dt for the others, reflective walls / periodic wrap;
+ *   6. per-c-bin moments n, v_b, T, p (Eqs. vel_b, stress, 18, 19).
+ *
+ * Conventions: m = 1, k_B = 1, velocities 3-D.  Particle ids are the input
+ * indices (instance-local in batched mode).  Every call returns KMC_OK (0) or a
+ * negative KMC_E* code; kmc_last_error() gives a message.  All device work runs
+ * on the stream given in kmc_config.stream (a private stream when NULL), in
+ * order; calls that return host data synchronise that stream.
+ *
+ * Precision: precision = 32 holds particle state in binary32 (per-cell moment
+ * sums in binary64); precision = 64 holds everything in binary64.  The decision
+ * quantities of the acceptance test are evaluated with a fixed operation order
+ * (fused multiply-adds included) in the state precision.
+ */
+#ifndef KMC_H
+#define KMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define KMC_API __attribute__((visibility("default")))
+#else
+#define KMC_API
+#endif
+
+#define KMC_OK 0
+#define KMC_EINVAL (-1)   /* invalid argument or configuration */
+#define KMC_ENOMEM (-2)   /* device or host allocation failed */
+#define KMC_ECUDA (-3)    /* a CUDA runtime call failed */
+#define KMC_ETIMEOUT (-4) /* a bounded device-side wait gave up (state invalid) */
+#define KMC_ERANGE (-5)   /* a size exceeds an internal limit */
+#define KMC_ESTATE (-6)   /* call not valid in the handle's current state */
+
+#define KMC_WHERE_HOST 0   /* pointer is host memory (pageable or pinned) */
+#define KMC_WHERE_DEVICE 1 /* pointer is device memory of the current device */
+
+#define KMC_BC_PERIODIC 0
+#define KMC_BC_WALL 1      /* specular (reflective) wall, Sect. "Sod test" */
+
+#define KMC_FLAG_RECORD 1   /* keep each particle's closest candidate and partner of the last step */
+#define KMC_FLAG_NO_GRAPH 2 /* launch kernels directly instead of replaying a captured CUDA graph */
+
+#define KMC_MOM_RAW 1       /* per c-bin: N, Sum vx, Sum vy, Sum vz, Sum vx^2, Sum vy^2, Sum vz^2, Sum W */
+#define KMC_MOM_DERIVED 2   /* per c-bin: n, ux, uy, uz, T, p_kin, p_vir, p */
+#define KMC_MOM_GLOBAL 4    /* per instance: N, E = 1/2 Sum |v|^2, Px, Py, Pz, Sum W, pairs, 0 */
+
+typedef struct kmc_handle kmc_handle;
+
+/* One independent problem of a batched run (kmc_config.n_instances > 1).
+ * Instances share geometry and precision; their particles are consecutive
+ * blocks of the pos/vel arrays, in instance order. */
+typedef struct kmc_instance {
+    int64_t n_particles;
+    double lambda;   /* mean free path (Eq. 7); used when sigma <= 0 */
+    double sigma;    /* cross-section; > 0 overrides lambda */
+    double dt;       /* timestep, > 0 */
+    uint64_t seed;   /* Philox-4x32-10 key (low word, high word) */
+} kmc_instance;
+
+typedef struct kmc_config {
+    int dim_pos;        /* position dimensions: 2 (x, y) or 3 (x, y, z) */
+    int n_cells[3];     /* c-bins per dimension, each >= 1 (n_cells[2] ignored if dim_pos == 2) */
+    double lo[3];       /* box lower corner */
+    double hi[3];       /* box upper corner, hi > lo */
+    int bc[3];          /* KMC_BC_PERIODIC or KMC_BC_WALL per dimension */
+    double lambda;      /* single run: mean free path (used when sigma <= 0) */
+    double sigma;       /* single run: cross-section (> 0 overrides lambda) */
+    double dt;          /* single run: timestep */
+    uint64_t seed;      /* single run: Philox key */
+    int precision;      /* 32 or 64 */
+    int n_instances;    /* 0 or 1: single run from the fields above; > 1: batched from instances[] */
+    const kmc_instance* instances; /* n_instances entries when batched; read during kmc_init only */
+    void* stream;       /* cudaStream_t; NULL = a stream owned by the handle */
+    int sub_cells[3];   /* search-grid subdivision of each c-bin per dimension; 0 = automatic */
+    double occupancy_target; /* automatic subdivision: particles per search cell aimed at (0 = 2.0) */
+    int flags;          /* KMC_FLAG_* */
+} kmc_config;
+
+/* Read-only description of a handle (kmc_get_info). */
+typedef struct kmc_info {
+    int64_t n_particles;     /* total over instances */
+    int64_t n_bins;          /* c-bins over all instances (moment rows) */
+    int64_t n_search_cells;  /* search-grid cells over all instances */
+    int n_instances;
+    int precision;
+    uint32_t step;           /* steps taken since init (Philox counter word 1 of the next step) */
+    int sub_cells[3];        /* subdivision of instance 0 */
+    double R2;               /* instance 0: squared contact distance (2 r_eff)^2 = sigma / pi */
+    double sigma;            /* instance 0 */
+    double dt;               /* instance 0 */
+    double vmax;             /* instance 0: largest speed of the current state */
+    int window[3];           /* instance 0: search half-width in search cells for the next step */
+    int64_t bytes_device;    /* device memory held by the handle */
+} kmc_info;
+
+/* Create a simulation.  pos and vel are n x 3 row-major arrays of float
+ * (precision 32) or double (precision 64), in host or device memory per
+ * `where`; in 2-D mode the z column of pos is carried unchanged.  The data are
+ * copied (the caller keeps ownership).  Single run: n particles, ids 0..n-1.
+ * Batched: n must equal the sum of instances[].n_particles.  Positions must be
+ * finite and inside the box (walls: [lo, hi]; periodic: [lo, hi)), velocities
+ * finite; violations give KMC_EINVAL.  *out is set only on success. */
+KMC_API int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
+             int where, kmc_handle** out);
+
+/* Advance every instance by nsteps >= 0 steps (asynchronous on the handle's
+ * stream).  want_moments != 0 accumulates the per-c-bin moments of each step's
+ * end state (kmc_moments then returns those of the last step).  Returns
+ * KMC_ETIMEOUT / KMC_ECUDA for failures detected so far (launch errors now,
+ * device-side flags at the next synchronising call). */
+KMC_API int kmc_step(kmc_handle* h, int nsteps, int want_moments);
+
+/* Phases of one step, in launch order, for kmc_step_profiled. */
+#define KMC_PHASE_CLEAR 0    /* zero the moment accumulators (want_moments only) */
+#define KMC_PHASE_SEARCH 1   /* closest candidate per particle (criteria 1-3) */
+#define KMC_PHASE_MOVE 2     /* pairs, scattering, free flight, walls, next key, moment sums */
+#define KMC_PHASE_SCAN 3     /* exclusive scan of the key histogram */
+#define KMC_PHASE_SCATTER 4  /* counting-sort scatter into key order */
+#define KMC_PHASE_FINALIZE 5 /* derived moments and per-instance totals (want_moments only) */
+#define KMC_NPHASES 6
+
+/* Same work as kmc_step, launched kernel by kernel (no graph) with a CUDA
+ * event recorded on the handle's stream before and after every phase.
+ * Synchronises the stream, then writes ms_out[KMC_NPHASES + 1]: the device
+ * time of each phase summed over the nsteps steps, and the total from the
+ * first to the last event.  Used to measure per-kernel durations. */
+KMC_API int kmc_step_profiled(kmc_handle* h, int nsteps, int want_moments, double* ms_out);
+
+/* Copy moments into out (caller-allocated doubles): the blocks selected by
+ * fields_mask, in the order RAW (n_bins x 8), DERIVED (n_bins x 8),
+ * GLOBAL (n_instances x 8).  Rows are c-bins with key c_x + n_x (c_y + n_y c_z),
+ * instance-major.  Moments are those accumulated by the last kmc_step with
+ * want_moments != 0, or, if none since the state was last set, of the current
+ * state with zero virial.  Synchronises the stream when where == HOST. */
+KMC_API int kmc_moments(kmc_handle* h, double* out, int where, int fields_mask);
+
+/* Number of doubles kmc_moments writes for fields_mask. */
+KMC_API int64_t kmc_moments_size(const kmc_handle* h, int fields_mask);
+
+/* Release all device and host memory of the handle.  NULL-safe. */
+KMC_API void kmc_free(kmc_handle* h);
+
+/* Wait for the handle's stream; report device-side error flags. */
+KMC_API int kmc_sync(kmc_handle* h);
+
+/* Message of the last error on h (or of the last failed kmc_init if h is NULL). */
+KMC_API const char* kmc_last_error(const kmc_handle* h);
+
+KMC_API int kmc_get_info(kmc_handle* h, kmc_info* info);
+
+/* Current state in id order (n x 3 each, state precision).  Synchronises
+ * the stream when where == HOST.  Either pointer may be NULL. */
+KMC_API int kmc_get_state(kmc_handle* h, void* pos, void* vel, int where);
+
+/* Replace the state (same layout and checks as kmc_init) and set the step
+ * counter; used for checkpoint/resume.  Discards pending moments. */
+KMC_API int kmc_set_state(kmc_handle* h, const void* pos, const void* vel, int where, uint32_t step);
+
+/* c-bin key c_x + n_x (c_y + n_y c_z) of every particle of the current state,
+ * id order (int32, instance-local keys). */
+KMC_API int kmc_get_cell_keys(kmc_handle* h, int32_t* keys, int where);
+
+/* Requires KMC_FLAG_RECORD.  best: closest candidate (instance-local id) of
+ * each particle in the last step, -1 if none; partner: collision partner of the
+ * last step (mutually closest), -1 if none.  Either pointer may be NULL. */
+KMC_API int kmc_get_partners(kmc_handle* h, int32_t* best, int32_t* partner, int where);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

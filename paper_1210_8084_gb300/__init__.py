@@ -1,0 +1,341 @@
+"""Python binding of the sm_103a kinetic Monte Carlo library (libkmc.so).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+behind the C ABI of ``include/kmc.h``.  The names mirror that header
+(``kmc_init``, ``kmc_step``, ``kmc_moments``, ``kmc_free`` and the getters).
+Host arrays are numpy arrays; device arrays are anything with a
+``data_ptr()`` (torch tensors), passed with ``where=KMC_WHERE_DEVICE``.
+
+Importing this package loads ``libkmc.so`` and raises if it was not built
+(``python -c "import __graft_entry__ as g; g.build()"``): there is no fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkmc.so")
+
+KMC_OK = 0
+KMC_EINVAL = -1
+KMC_ENOMEM = -2
+KMC_ECUDA = -3
+KMC_ETIMEOUT = -4
+KMC_ERANGE = -5
+KMC_ESTATE = -6
+KMC_WHERE_HOST = 0
+KMC_WHERE_DEVICE = 1
+KMC_BC_PERIODIC = 0
+KMC_BC_WALL = 1
+KMC_FLAG_RECORD = 1
+KMC_FLAG_NO_GRAPH = 2
+KMC_MOM_RAW = 1
+KMC_MOM_DERIVED = 2
+KMC_MOM_GLOBAL = 4
+KMC_NPHASES = 6
+PHASES = ("clear", "search", "move", "scan", "scatter", "finalize")
+
+ABI_FUNCTIONS = (
+    "kmc_init", "kmc_step", "kmc_moments", "kmc_moments_size", "kmc_free", "kmc_sync",
+    "kmc_last_error", "kmc_get_info", "kmc_get_state", "kmc_set_state", "kmc_get_cell_keys",
+    "kmc_get_partners", "kmc_step_profiled",
+)
+
+
+class KmcInstance(ctypes.Structure):
+    _fields_ = [
+        ("n_particles", ctypes.c_int64),
+        ("lambda_", ctypes.c_double),
+        ("sigma", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class KmcConfig(ctypes.Structure):
+    _fields_ = [
+        ("dim_pos", ctypes.c_int),
+        ("n_cells", ctypes.c_int * 3),
+        ("lo", ctypes.c_double * 3),
+        ("hi", ctypes.c_double * 3),
+        ("bc", ctypes.c_int * 3),
+        ("lambda_", ctypes.c_double),
+        ("sigma", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("precision", ctypes.c_int),
+        ("n_instances", ctypes.c_int),
+        ("instances", ctypes.POINTER(KmcInstance)),
+        ("stream", ctypes.c_void_p),
+        ("sub_cells", ctypes.c_int * 3),
+        ("occupancy_target", ctypes.c_double),
+        ("flags", ctypes.c_int),
+    ]
+
+
+class KmcInfo(ctypes.Structure):
+    _fields_ = [
+        ("n_particles", ctypes.c_int64),
+        ("n_bins", ctypes.c_int64),
+        ("n_search_cells", ctypes.c_int64),
+        ("n_instances", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("step", ctypes.c_uint32),
+        ("sub_cells", ctypes.c_int * 3),
+        ("R2", ctypes.c_double),
+        ("sigma", ctypes.c_double),
+        ("dt", ctypes.c_double),
+        ("vmax", ctypes.c_double),
+        ("window", ctypes.c_int * 3),
+        ("bytes_device", ctypes.c_int64),
+    ]
+
+
+class KmcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"kmc error {code}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; g.build()\"`"
+        )
+    L = ctypes.CDLL(LIB_PATH)
+    H = ctypes.c_void_p
+    vp = ctypes.c_void_p
+    L.kmc_init.argtypes = [ctypes.POINTER(KmcConfig), ctypes.c_int64, vp, vp, ctypes.c_int, ctypes.POINTER(H)]
+    L.kmc_init.restype = ctypes.c_int
+    L.kmc_step.argtypes = [H, ctypes.c_int, ctypes.c_int]
+    L.kmc_step.restype = ctypes.c_int
+    L.kmc_moments.argtypes = [H, vp, ctypes.c_int, ctypes.c_int]
+    L.kmc_moments.restype = ctypes.c_int
+    L.kmc_moments_size.argtypes = [H, ctypes.c_int]
+    L.kmc_moments_size.restype = ctypes.c_int64
+    L.kmc_free.argtypes = [H]
+    L.kmc_free.restype = None
+    L.kmc_sync.argtypes = [H]
+    L.kmc_sync.restype = ctypes.c_int
+    L.kmc_last_error.argtypes = [H]
+    L.kmc_last_error.restype = ctypes.c_char_p
+    L.kmc_get_info.argtypes = [H, ctypes.POINTER(KmcInfo)]
+    L.kmc_get_info.restype = ctypes.c_int
+    L.kmc_get_state.argtypes = [H, vp, vp, ctypes.c_int]
+    L.kmc_get_state.restype = ctypes.c_int
+    L.kmc_set_state.argtypes = [H, vp, vp, ctypes.c_int, ctypes.c_uint32]
+    L.kmc_set_state.restype = ctypes.c_int
+    L.kmc_get_cell_keys.argtypes = [H, vp, ctypes.c_int]
+    L.kmc_get_cell_keys.restype = ctypes.c_int
+    L.kmc_get_partners.argtypes = [H, vp, vp, ctypes.c_int]
+    L.kmc_get_partners.restype = ctypes.c_int
+    L.kmc_step_profiled.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    L.kmc_step_profiled.restype = ctypes.c_int
+    return L
+
+
+lib = _load()
+
+
+def _ptr(a):
+    """Raw address of a numpy array (host) or a tensor-like with data_ptr()."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if hasattr(a, "is_contiguous") and not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, int):
+        return a
+    raise TypeError(f"cannot take the address of {type(a)}")
+
+
+def _check(rc, h=None):
+    if rc != KMC_OK:
+        msg = lib.kmc_last_error(h)
+        raise KmcError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def make_config(dim_pos=3, n_cells=(1, 1, 1), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
+                bc=(KMC_BC_WALL, KMC_BC_PERIODIC, KMC_BC_PERIODIC), lam=1e-3, sigma=0.0, dt=1e-3,
+                seed=0, precision=32, instances=None, stream=None, sub_cells=(0, 0, 0),
+                occupancy_target=0.0, flags=0):
+    """Fill a KmcConfig.  `instances` is a list of dicts with keys n, lam, sigma, dt, seed;
+    the returned object keeps the instance array alive."""
+    c = KmcConfig()
+    c.dim_pos = int(dim_pos)
+    for d in range(3):
+        c.n_cells[d] = int(n_cells[d]) if d < len(n_cells) else 1
+        c.lo[d] = float(lo[d]) if d < len(lo) else 0.0
+        c.hi[d] = float(hi[d]) if d < len(hi) else 1.0
+        c.bc[d] = int(bc[d]) if d < len(bc) else KMC_BC_PERIODIC
+        c.sub_cells[d] = int(sub_cells[d]) if d < len(sub_cells) else 0
+    c.lambda_ = float(lam)
+    c.sigma = float(sigma)
+    c.dt = float(dt)
+    c.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    c.precision = int(precision)
+    c.stream = stream
+    c.occupancy_target = float(occupancy_target)
+    c.flags = int(flags)
+    if instances:
+        arr = (KmcInstance * len(instances))()
+        for i, inst in enumerate(instances):
+            arr[i].n_particles = int(inst["n"])
+            arr[i].lambda_ = float(inst.get("lam", 0.0))
+            arr[i].sigma = float(inst.get("sigma", 0.0))
+            arr[i].dt = float(inst["dt"])
+            arr[i].seed = int(inst.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
+        c.n_instances = len(instances)
+        c.instances = ctypes.cast(arr, ctypes.POINTER(KmcInstance))
+        c._keep = arr
+    else:
+        c.n_instances = 0
+    return c
+
+
+# ------------------------------------------------------------- the C ABI names
+
+def kmc_init(cfg, n, pos, vel, where=KMC_WHERE_HOST):
+    h = ctypes.c_void_p()
+    _check(lib.kmc_init(ctypes.byref(cfg), int(n), _ptr(pos), _ptr(vel), int(where), ctypes.byref(h)))
+    return h
+
+
+def kmc_step(h, nsteps=1, want_moments=1):
+    return _check(lib.kmc_step(h, int(nsteps), int(want_moments)), h)
+
+
+def kmc_moments(h, out, where=KMC_WHERE_HOST, fields_mask=KMC_MOM_RAW | KMC_MOM_DERIVED | KMC_MOM_GLOBAL):
+    return _check(lib.kmc_moments(h, _ptr(out), int(where), int(fields_mask)), h)
+
+
+def kmc_step_profiled(h, nsteps=1, want_moments=1):
+    """Returns a dict phase -> summed device milliseconds, plus 'total'."""
+    ms = (ctypes.c_double * (KMC_NPHASES + 1))()
+    _check(lib.kmc_step_profiled(h, int(nsteps), int(want_moments), ms), h)
+    out = {name: ms[i] for i, name in enumerate(PHASES)}
+    out["total"] = ms[KMC_NPHASES]
+    return out
+
+
+def kmc_moments_size(h, fields_mask):
+    return int(lib.kmc_moments_size(h, int(fields_mask)))
+
+
+def kmc_free(h):
+    lib.kmc_free(h)
+
+
+def kmc_sync(h):
+    return _check(lib.kmc_sync(h), h)
+
+
+def kmc_last_error(h=None):
+    m = lib.kmc_last_error(h)
+    return m.decode() if m else ""
+
+
+def kmc_get_info(h):
+    info = KmcInfo()
+    _check(lib.kmc_get_info(h, ctypes.byref(info)), h)
+    return info
+
+
+def kmc_get_state(h, pos, vel, where=KMC_WHERE_HOST):
+    return _check(lib.kmc_get_state(h, _ptr(pos), _ptr(vel), int(where)), h)
+
+
+def kmc_set_state(h, pos, vel, where=KMC_WHERE_HOST, step=0):
+    return _check(lib.kmc_set_state(h, _ptr(pos), _ptr(vel), int(where), int(step)), h)
+
+
+def kmc_get_cell_keys(h, keys, where=KMC_WHERE_HOST):
+    return _check(lib.kmc_get_cell_keys(h, _ptr(keys), int(where)), h)
+
+
+def kmc_get_partners(h, best, partner, where=KMC_WHERE_HOST):
+    return _check(lib.kmc_get_partners(h, _ptr(best), _ptr(partner), int(where)), h)
+
+
+# --------------------------------------------------------- convenience wrapper
+
+class Simulation:
+    """Owns one handle; host-side numpy in/out around the C ABI calls."""
+
+    def __init__(self, cfg, pos, vel, where=KMC_WHERE_HOST):
+        self.cfg = cfg
+        self.dtype = np.float32 if cfg.precision == 32 else np.float64
+        if where == KMC_WHERE_HOST:
+            pos = np.ascontiguousarray(pos, dtype=self.dtype).reshape(-1, 3)
+            vel = np.ascontiguousarray(vel, dtype=self.dtype).reshape(-1, 3)
+            n = pos.shape[0]
+        else:
+            n = pos.shape[0]
+        self.n = n
+        self.h = kmc_init(cfg, n, pos, vel, where)
+        info = kmc_get_info(self.h)
+        self.n_bins = info.n_bins
+        self.n_instances = info.n_instances
+
+    def close(self):
+        if self.h is not None:
+            kmc_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, nsteps=1, want_moments=1):
+        kmc_step(self.h, nsteps, want_moments)
+
+    def step_profiled(self, nsteps=1, want_moments=1):
+        return kmc_step_profiled(self.h, nsteps, want_moments)
+
+    def sync(self):
+        kmc_sync(self.h)
+
+    def info(self):
+        return kmc_get_info(self.h)
+
+    def state(self):
+        pos = np.zeros((self.n, 3), dtype=self.dtype)
+        vel = np.zeros((self.n, 3), dtype=self.dtype)
+        kmc_get_state(self.h, pos, vel)
+        return pos, vel
+
+    def set_state(self, pos, vel, step=0):
+        pos = np.ascontiguousarray(pos, dtype=self.dtype).reshape(-1, 3)
+        vel = np.ascontiguousarray(vel, dtype=self.dtype).reshape(-1, 3)
+        kmc_set_state(self.h, pos, vel, KMC_WHERE_HOST, step)
+
+    def cell_keys(self):
+        k = np.zeros(self.n, dtype=np.int32)
+        kmc_get_cell_keys(self.h, k)
+        return k
+
+    def partners(self):
+        best = np.zeros(self.n, dtype=np.int32)
+        partner = np.zeros(self.n, dtype=np.int32)
+        kmc_get_partners(self.h, best, partner)
+        return best, partner
+
+    def moments(self):
+        """(raw [bins, 8], derived [bins, 8], glob [instances, 8])"""
+        mask = KMC_MOM_RAW | KMC_MOM_DERIVED | KMC_MOM_GLOBAL
+        out = np.zeros(kmc_moments_size(self.h, mask), dtype=np.float64)
+        kmc_moments(self.h, out, KMC_WHERE_HOST, mask)
+        nb = self.n_bins
+        raw = out[: 8 * nb].reshape(nb, 8)
+        der = out[8 * nb: 16 * nb].reshape(nb, 8)
+        glob = out[16 * nb:].reshape(-1, 8)
+        return raw, der, glob

@@ -1,0 +1,134 @@
+// kmc_internal.h -- shared declarations of the sm_103a kinetic Monte Carlo library
+// (device tables, handle, kernel launchers).  Host code and kernels include it;
+// nothing outside csrc/ does.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/kmc.h"
+
+namespace kmc {
+
+constexpr int kThreads = 256;          // threads per block of the particle kernels
+constexpr int kScanThreads = 256;      // scan: threads per tile
+constexpr int kScanItems = 16;         // scan: keys per thread (4 x uint4)
+constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr uint32_t kSpinCap = 1u << 22;  // bounded waits: iterations before giving up
+constexpr int kFoldCap = 64;           // wall folds per coordinate per step
+constexpr int kAccFields = 9;          // per c-bin accumulator: 8 moment sums + collided count
+
+// device error flags (DevState::error)
+constexpr uint32_t kErrScanTimeout = 1u;
+constexpr uint32_t kErrKeyRange = 2u;
+
+// Per-instance constants.  Geometry (box, c-bins, walls) is shared; the search
+// grid subdivision s[] and the interaction constants are per instance.
+struct InstDev {
+    int64_t p_off;       // first particle of the instance (global index)
+    int64_t n;           // particles of the instance
+    uint32_t key_base;   // first search-grid key of the instance
+    uint32_t bin_base;   // first c-bin (moment row) of the instance
+    int s[3];            // subdivision of a c-bin into search cells per dimension
+    int M[3];            // search cells per dimension = n_cells * s
+    double R2;           // squared contact distance
+    double dt;           // timestep
+    uint32_t seed_lo, seed_hi;
+    double w[3];         // search-cell width per dimension
+};
+
+// Per-instance quantities that change every step (written on the device).
+struct InstDyn {
+    unsigned long long vmax2_cur;   // bits of the largest |v|^2 (binary64) of the current state
+    unsigned long long vmax2_next;  // accumulated by the step's move kernel
+    int k[3];                       // search half-window in search cells
+    int pad;
+};
+
+struct Geo {
+    int dim;
+    int n[3];
+    int bc[3];
+    double lo[3], hi[3], L[3], inv_dx[3];
+};
+
+struct DevState {
+    uint32_t step;        // Philox counter word 1 of the step being taken
+    uint32_t error;       // kErr* bits
+    unsigned long long candidates;  // RECORD mode counters
+    unsigned long long pairs;
+};
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    using type = float4;
+};
+struct __align__(32) dvec4 {
+    double x, y, z, w;
+};
+template <>
+struct Vec4<double> {
+    using type = dvec4;
+};
+
+// Pointers and sizes of one simulation, passed by value to every launcher.
+template <typename T>
+struct Bufs {
+    using V = typename Vec4<T>::type;
+    int64_t n;
+    int n_inst;
+    const InstDev* inst;     // [n_inst]
+    InstDyn* dyn;            // [n_inst]
+    DevState* st;
+    Geo geo;
+    V* posA; V* velA;        // sorted state (search-grid key order)
+    V* posB; V* velB;        // staging / unsorted end-of-step state
+    int32_t* best;           // [n] sorted position of the closest candidate or -1
+    uint32_t* key;           // [n] search key of B
+    uint32_t* slot;          // [n] rank of B[p] within its search cell
+    uint32_t* count;         // [n_keys + 1] histogram (zero outside the step)
+    uint32_t* start;         // [n_keys + 1] exclusive scan of count
+    unsigned long long* scan_status;  // [1 + n_tiles]: ticket + tile descriptors
+    uint32_t n_keys;
+    uint32_t n_tiles;
+    double* acc;             // [n_bins * kAccFields] moment sums
+    double* mom;             // [n_bins * 16] raw + derived
+    double* glob;            // [n_inst * 8]
+    int64_t n_bins;
+    int32_t* rec_best;       // RECORD: [n] by global id
+    int32_t* rec_partner;    // RECORD: [n] by global id
+    int record;
+};
+
+// Launchers (defined in kmc_kernels.cuh, instantiated per precision).
+template <typename T>
+cudaError_t launch_pack(const Bufs<T>& b, const T* pos3, const T* vel3, uint32_t* bad, cudaStream_t s);
+template <typename T>
+cudaError_t launch_bin_init(const Bufs<T>& b, cudaStream_t s);
+template <typename T>
+cudaError_t launch_search(const Bufs<T>& b, cudaStream_t s);
+template <typename T>
+cudaError_t launch_move(const Bufs<T>& b, int want_moments, cudaStream_t s);
+template <typename T>
+cudaError_t launch_scatter(const Bufs<T>& b, cudaStream_t s);
+template <typename T>
+cudaError_t launch_gather_state(const Bufs<T>& b, T* pos3, T* vel3, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cell_keys(const Bufs<T>& b, int32_t* keys, cudaStream_t s);
+template <typename T>
+cudaError_t launch_moments_state(const Bufs<T>& b, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cbin_hist(const Bufs<T>& b, uint32_t* hist, unsigned long long* vmax2, cudaStream_t s);
+
+// precision-independent
+cudaError_t launch_scan(uint32_t* count, uint32_t* start, uint32_t n_keys, uint32_t n_tiles,
+                        unsigned long long* status, InstDyn* dyn, const InstDev* inst,
+                        int n_inst, DevState* st, Geo geo, int bump_step, cudaStream_t s);
+cudaError_t launch_finalize(const InstDev* inst, int n_inst, Geo geo, const double* acc,
+                            double* mom, double* glob, int64_t n_bins, cudaStream_t s);
+
+}  // namespace kmc

@@ -1,0 +1,747 @@
+// kmc_kernels.cuh -- sm_103a kernels of one kinetic Monte Carlo step, templated on
+// the state precision T (float or double) and the position dimension DIM.
+//
+// Step structure (Sagert et al., Sect. "Simulation setup" and Fig. 2):
+//   search  : closest PoCA candidate per particle over its c-bin neighbourhood
+//   move    : unambiguous pairs, CM scattering, split free flight, walls,
+//             next search key + histogram, moment sums (fused)
+//   scan    : exclusive scan of the key histogram (kmc_scan.cu)
+//   scatter : counting-sort scatter into search-key order
+//
+// Layout: SoA of 16-byte (binary32) or 32-byte (binary64) vectors,
+//   pos = (x, y, z, id bits), vel = (vx, vy, vz, instance bits),
+// sorted by search key = key_base + (gx * My + gy) * Mz + gz where g is the
+// search cell (a c-bin subdivided s_d times per dimension, x slowest).
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#include "kmc_internal.h"
+
+namespace kmc {
+
+// ---------------------------------------------------------------- arithmetic
+// Decision arithmetic uses explicitly rounded operations so the compiler cannot
+// contract or reorder them; the fused multiply-adds are the explicit fma calls.
+template <typename T>
+struct R;
+template <>
+struct R<float> {
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+    static __device__ __forceinline__ float sqrt_(float a) { return sqrtf(a); }
+    static __device__ __forceinline__ uint32_t bits(float a) { return __float_as_uint(a); }
+    static __device__ __forceinline__ float from_bits(uint32_t u) { return __uint_as_float(u); }
+    static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+};
+template <>
+struct R<double> {
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+    static __device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
+    static __device__ __forceinline__ uint32_t bits(double a) {
+        return (uint32_t)(unsigned long long)__double_as_longlong(a);
+    }
+    static __device__ __forceinline__ double from_bits(uint32_t u) {
+        return __longlong_as_double((long long)(unsigned long long)u);
+    }
+    static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000LL); }
+};
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32 multiplies with
+// the published multipliers; the key advances by the Weyl increments.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Uniform deviates in (0, 1) with an odd mantissa: binary32 from one word,
+// binary64 from two.
+template <typename T>
+__device__ __forceinline__ void uniforms(uint4 x, T& u1, T& u2);
+template <>
+__device__ __forceinline__ void uniforms<float>(uint4 x, float& u1, float& u2) {
+    u1 = (float)((x.x >> 8) | 1u) * 0x1p-24f;
+    u2 = (float)((x.z >> 8) | 1u) * 0x1p-24f;
+}
+template <>
+__device__ __forceinline__ void uniforms<double>(uint4 x, double& u1, double& u2) {
+    const unsigned long long m1 = ((unsigned long long)x.x << 20) | (x.y >> 12);
+    const unsigned long long m2 = ((unsigned long long)x.z << 20) | (x.w >> 12);
+    u1 = (double)(2ull * m1 + 1ull) * 0x1p-53;
+    u2 = (double)(2ull * m2 + 1ull) * 0x1p-53;
+}
+
+__device__ __forceinline__ void sincos_2pi(float u, float* s, float* c) { sincospif(2.0f * u, s, c); }
+__device__ __forceinline__ void sincos_2pi(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }
+
+// ------------------------------------------------------------- geometry
+// Per-dimension constants in the state precision.  For walled dimensions the
+// half length is +inf so the minimum-image shift never fires.
+template <typename T>
+struct GeoT {
+    T lo[3], hi[3], inv[3], L[3], hL[3];
+    int n[3];
+    bool wall[3];
+    __device__ __forceinline__ void load(const Geo& g) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = (T)g.lo[d];
+            hi[d] = (T)g.hi[d];
+            inv[d] = (T)g.inv_dx[d];
+            L[d] = (T)g.L[d];
+            wall[d] = g.bc[d] != 0;
+            hL[d] = wall[d] ? R<T>::inf() : (T)0.5 * L[d];
+            n[d] = g.n[d];
+        }
+    }
+};
+
+// c-bin index c = floor((x - lo) * n / (hi - lo)) clamped to [0, n-1], and the
+// search cell g = c * s + floor(frac * s) inside it.
+template <typename T>
+__device__ __forceinline__ void cell_and_search(T x, T lo, T inv, int n, int s, int& c, int& g) {
+    const T t = R<T>::mul(R<T>::sub(x, lo), inv);
+    int ci;
+    if (t < (T)0) ci = 0;
+    else if (t >= (T)n) ci = n - 1;
+    else ci = (int)t;
+    c = ci;
+    if (s == 1) { g = ci; return; }
+    const T fs = R<T>::mul(R<T>::sub(t, (T)ci), (T)s);
+    int si;
+    if (fs < (T)0) si = 0;
+    else if (fs >= (T)s) si = s - 1;
+    else si = (int)fs;
+    g = ci * s + si;
+}
+
+template <typename T>
+__device__ __forceinline__ T min_image(T x, T hL, T L) {
+    if (x > hL) return R<T>::sub(x, L);
+    if (x < -hL) return R<T>::add(x, L);
+    return x;
+}
+
+// Keys of a position: search key (global) and c-bin (global row).
+template <typename T, int DIM>
+__device__ __forceinline__ void keys_of(const GeoT<T>& G, const InstDev& I, const T x[3],
+                                        uint32_t& skey, uint32_t& bin) {
+    int c[3] = {0, 0, 0}, g[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) cell_and_search<T>(x[d], G.lo[d], G.inv[d], G.n[d], I.s[d], c[d], g[d]);
+    if (DIM == 3) {
+        skey = I.key_base + ((uint32_t)g[0] * (uint32_t)I.M[1] + (uint32_t)g[1]) * (uint32_t)I.M[2] + (uint32_t)g[2];
+        bin = I.bin_base + (uint32_t)c[0] + (uint32_t)G.n[0] * ((uint32_t)c[1] + (uint32_t)G.n[1] * (uint32_t)c[2]);
+    } else {
+        skey = I.key_base + (uint32_t)g[0] * (uint32_t)I.M[1] + (uint32_t)g[1];
+        bin = I.bin_base + (uint32_t)c[0] + (uint32_t)G.n[0] * (uint32_t)c[1];
+    }
+}
+
+// Instance of a global particle index (instances are consecutive blocks).
+__device__ __forceinline__ int instance_of(const InstDev* inst, int n_inst, int64_t gidx) {
+    int lo = 0, hi = n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (inst[mid].p_off <= gidx) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------ warp helpers
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+
+// Histogram increment aggregated over lanes with the same key; returns the
+// lane's rank within its key (the counting-sort slot).
+__device__ __forceinline__ uint32_t aggregated_increment(uint32_t* count, uint32_t key, unsigned active) {
+    const unsigned peers = __match_any_sync(active, key);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if ((int)lane_id() == leader) base = atomicAdd(count + key, (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    const unsigned lt = (1u << lane_id()) - 1u;
+    return base + (uint32_t)__popc(peers & lt);
+}
+
+// Largest |v|^2 per instance: warp maximum, then one atomicMax per warp and
+// instance, skipped when it cannot raise the stored value.
+template <typename T>
+__device__ __forceinline__ void warp_vmax(InstDyn* dyn, bool valid, int inst, T v2) {
+    unsigned todo = __ballot_sync(kFull, valid);
+    while (todo) {
+        const int leader = __ffs(todo) - 1;
+        const int gi = __shfl_sync(kFull, inst, leader);
+        const bool mine = valid && inst == gi;
+        const unsigned grp = __ballot_sync(kFull, mine);
+        double m = mine ? (double)v2 : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
+        if ((int)lane_id() == leader) {
+            const unsigned long long bitsm = (unsigned long long)__double_as_longlong(m);
+            unsigned long long* dst = &dyn[gi].vmax2_next;
+            if (bitsm > *((volatile unsigned long long*)dst)) atomicMax(dst, bitsm);
+        }
+        todo &= ~grp;
+    }
+}
+
+// Moment sums per c-bin: lanes with the same bin are reduced with warp
+// shuffles, then the group leader adds the totals to the binary64 accumulator.
+template <typename T>
+__device__ __forceinline__ void warp_moments(double* acc, bool valid, uint32_t bin, const T v[3], T W,
+                                             bool collided) {
+    unsigned todo = __ballot_sync(kFull, valid);
+    const unsigned coll = __ballot_sync(kFull, valid && collided);
+    while (todo) {
+        const int leader = __ffs(todo) - 1;
+        const uint32_t gb = __shfl_sync(kFull, bin, leader);
+        const bool mine = valid && bin == gb;
+        const unsigned grp = __ballot_sync(kFull, mine);
+        T f[7];
+        f[0] = mine ? v[0] : (T)0;
+        f[1] = mine ? v[1] : (T)0;
+        f[2] = mine ? v[2] : (T)0;
+        f[3] = f[0] * f[0];
+        f[4] = f[1] * f[1];
+        f[5] = f[2] * f[2];
+        f[6] = mine ? W : (T)0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int k = 0; k < 7; ++k) f[k] += __shfl_xor_sync(kFull, f[k], o);
+        }
+        if ((int)lane_id() == leader) {
+            double* a = acc + (size_t)gb * kAccFields;
+            atomicAdd(a + 0, (double)__popc(grp));
+#pragma unroll
+            for (int k = 0; k < 7; ++k) atomicAdd(a + 1 + k, (double)f[k]);
+            const int nc = __popc(grp & coll);
+            if (nc) atomicAdd(a + 8, (double)nc);
+        }
+        todo &= ~grp;
+    }
+}
+
+// --------------------------------------------------------------- kernels
+
+// Pack n x 3 input arrays into (pos, id) / (vel, instance) vectors of B and
+// count particles that are non-finite or outside the box.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) pack_kernel(Bufs<T> b, const T* __restrict__ pos3,
+                                                        const T* __restrict__ vel3, uint32_t* bad) {
+    using V = typename Vec4<T>::type;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= b.n) return;
+    const int inst = instance_of(b.inst, b.n_inst, p);
+    const uint32_t id = (uint32_t)(p - b.inst[inst].p_off);
+    T x[3], v[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        x[d] = pos3[3 * p + d];
+        v[d] = vel3[3 * p + d];
+    }
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ok = ok && isfinite(x[d]) && isfinite(v[d]);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        const T lo = (T)b.geo.lo[d], hi = (T)b.geo.hi[d];
+        if (b.geo.bc[d] != 0) ok = ok && x[d] >= lo && x[d] <= hi;
+        else ok = ok && x[d] >= lo && x[d] < hi;
+    }
+    if (!ok) atomicAdd(bad, 1u);
+    V P, Q;
+    P.x = x[0]; P.y = x[1]; P.z = x[2]; P.w = R<T>::from_bits(id);
+    Q.x = v[0]; Q.y = v[1]; Q.z = v[2]; Q.w = R<T>::from_bits((uint32_t)inst);
+    b.posB[p] = P;
+    b.velB[p] = Q;
+}
+
+// Keys, counting-sort slots, histogram and |v|max of the packed state in B
+// (used after packing: at init and when the state is replaced).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) bin_kernel(Bufs<T> b) {
+    using V = typename Vec4<T>::type;
+    __shared__ GeoT<T> G;
+    if (threadIdx.x == 0) G.load(b.geo);
+    __syncthreads();
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = p < b.n;
+    V P = {}, Q = {};
+    int inst = 0;
+    if (valid) {
+        P = b.posB[p];
+        Q = b.velB[p];
+        inst = (int)R<T>::bits(Q.w);
+    }
+    const InstDev I = b.inst[inst];
+    const T x[3] = {P.x, P.y, P.z};
+    uint32_t skey = 0, bin = 0;
+    keys_of<T, DIM>(G, I, x, skey, bin);
+    const unsigned active = __ballot_sync(kFull, valid);
+    if (valid) {
+        const uint32_t slot = aggregated_increment(b.count, skey, active);
+        b.key[p] = skey;
+        b.slot[p] = slot;
+    }
+    const T v2 = Q.x * Q.x + Q.y * Q.y + Q.z * Q.z;
+    warp_vmax<T>(b.dyn, valid, inst, v2);
+}
+
+// The PoCA acceptance test of the ordered pair (i, j) and its closest-approach
+// distance, in the operation order shared with the CPU oracle:
+//   a = r.v, b = |v|^2, r2 = |r|^2 (first product rounded, then fused adds),
+//   chi < 0  <=>  a < 0 and fma(b, dt, a) > 0           (Eq. c_value)
+//   disc = fma(a, a, -(b * (r2 - R^2))) >= 0             (Eq. collision_time2)
+//   d2 = r2 - (a * a) / b                                (criterion 3)
+template <typename T, int DIM>
+__device__ __forceinline__ bool poca_test(const GeoT<T>& G, const T xi[3], const T vi[3], const T xj[3],
+                                          const T vj[3], T dt, T R2, T& d2) {
+    T dr[3], dv[3];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        dr[d] = min_image<T>(R<T>::sub(xi[d], xj[d]), G.hL[d], G.L[d]);
+        dv[d] = R<T>::sub(vi[d], vj[d]);
+    }
+    T a = R<T>::mul(dr[0], dv[0]);
+    a = R<T>::fma(dr[1], dv[1], a);
+    T bb = R<T>::mul(dv[0], dv[0]);
+    bb = R<T>::fma(dv[1], dv[1], bb);
+    if (DIM == 3) {
+        a = R<T>::fma(dr[2], dv[2], a);
+        bb = R<T>::fma(dv[2], dv[2], bb);
+    }
+    if (!(bb > (T)0 && a < (T)0 && R<T>::fma(bb, dt, a) > (T)0)) return false;
+    T r2 = R<T>::mul(dr[0], dr[0]);
+    r2 = R<T>::fma(dr[1], dr[1], r2);
+    if (DIM == 3) r2 = R<T>::fma(dr[2], dr[2], r2);
+    const T disc = R<T>::fma(a, a, -R<T>::mul(bb, R<T>::sub(r2, R2)));
+    if (!(disc >= (T)0)) return false;
+    d2 = R<T>::sub(r2, R<T>::div(R<T>::mul(a, a), bb));
+    return true;
+}
+
+// Search window of one dimension in search-cell coordinates: within k cells of
+// g and inside the c-bins c-1 .. c+1.  Periodic windows are taken modulo M
+// (the full row when they would cover it); walled ones are cut at the box.
+struct Win {
+    int lo, hi;
+    bool wrap;
+};
+__device__ __forceinline__ Win window_1d(int g, int c, int s, int M, int k, bool wall) {
+    Win w;
+    w.lo = max(g - k, (c - 1) * s);
+    w.hi = min(g + k, (c + 2) * s - 1);
+    if (wall) {
+        w.lo = max(w.lo, 0);
+        w.hi = min(w.hi, M - 1);
+        w.wrap = false;
+    } else if (w.hi - w.lo + 1 >= M) {
+        w.lo = 0;
+        w.hi = M - 1;
+        w.wrap = false;
+    } else {
+        w.wrap = true;
+    }
+    return w;
+}
+__device__ __forceinline__ int wrap_idx(int t, int M) {
+    t %= M;
+    return t < 0 ? t + M : t;
+}
+
+// Closest candidate of every particle (criterion 3 over the 3^D c-bin
+// neighbourhood, restricted to search cells that can hold a candidate).
+// One thread per particle in sorted order; candidates are read through L1.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) search_kernel(Bufs<T> b) {
+    using V = typename Vec4<T>::type;
+    __shared__ GeoT<T> G;
+    if (threadIdx.x == 0) G.load(b.geo);
+    __syncthreads();
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= b.n) return;
+    const V P = b.posA[p];
+    const V Q = b.velA[p];
+    const int inst = (int)R<T>::bits(Q.w);
+    const InstDev& I = b.inst[inst];
+    const int* kk = b.dyn[inst].k;
+    const T xi[3] = {P.x, P.y, P.z};
+    const T vi[3] = {Q.x, Q.y, Q.z};
+    const T dt = (T)I.dt, R2 = (T)I.R2;
+    int c[3] = {0, 0, 0}, g[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) cell_and_search<T>(xi[d], G.lo[d], G.inv[d], G.n[d], I.s[d], c[d], g[d]);
+    Win wx = window_1d(g[0], c[0], I.s[0], I.M[0], kk[0], G.wall[0]);
+    Win wy = window_1d(g[1], c[1], I.s[1], I.M[1], kk[1], G.wall[1]);
+    Win wz = {0, 0, false};
+    if (DIM == 3) wz = window_1d(g[2], c[2], I.s[2], I.M[2], kk[2], G.wall[2]);
+    // z segments (z is the fastest key dimension, so a z window is 1 or 2 ranges)
+    int z0a = wz.lo, z1a = wz.hi, z0b = 1, z1b = 0;
+    if (DIM == 3 && wz.wrap) {
+        const int a0 = wrap_idx(wz.lo, I.M[2]), a1 = wrap_idx(wz.hi, I.M[2]);
+        if (a0 <= a1) { z0a = a0; z1a = a1; }
+        else { z0a = a0; z1a = I.M[2] - 1; z0b = 0; z1b = a1; }
+    }
+    const uint32_t Mz = (DIM == 3) ? (uint32_t)I.M[2] : 1u;
+    const uint32_t My = (uint32_t)I.M[1];
+    T bd = R<T>::inf();
+    uint32_t bid = 0xffffffffu;
+    int32_t bq = -1;
+    uint32_t ncand = 0;
+    for (int tx = wx.lo; tx <= wx.hi; ++tx) {
+        const int gx = wx.wrap ? wrap_idx(tx, I.M[0]) : tx;
+        for (int ty = wy.lo; ty <= wy.hi; ++ty) {
+            const int gy = wy.wrap ? wrap_idx(ty, I.M[1]) : ty;
+            const uint32_t row = I.key_base + ((uint32_t)gx * My + (uint32_t)gy) * Mz;
+            for (int seg = 0; seg < 2; ++seg) {
+                const int za = seg == 0 ? z0a : z0b;
+                const int zb = seg == 0 ? z1a : z1b;
+                if (za > zb) continue;
+                // clamped so that a corrupted scan (flagged on the host) cannot read outside A
+                const int32_t q0 = (int32_t)min(b.start[row + (uint32_t)za], (uint32_t)b.n);
+                const int32_t q1 = (int32_t)min(b.start[row + (uint32_t)zb + 1u], (uint32_t)b.n);
+                ncand += (uint32_t)(q1 - q0);
+                for (int32_t q = q0; q < q1; ++q) {
+                    if (q == (int32_t)p) continue;
+                    const V Pj = b.posA[q];
+                    const V Qj = b.velA[q];
+                    const T xj[3] = {Pj.x, Pj.y, Pj.z};
+                    const T vj[3] = {Qj.x, Qj.y, Qj.z};
+                    T d2;
+                    if (poca_test<T, DIM>(G, xi, vi, xj, vj, dt, R2, d2)) {
+                        const uint32_t idj = R<T>::bits(Pj.w);
+                        if (d2 < bd || (d2 == bd && idj < bid)) {
+                            bd = d2;
+                            bid = idj;
+                            bq = q;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    b.best[p] = bq;
+    if (b.record) atomicAdd(&b.st->candidates, (unsigned long long)(ncand > 0 ? ncand - 1 : 0));
+}
+
+// Unambiguous pairs, CM-frame scattering, split free flight, walls, then the
+// next step's search key / slot / histogram and the moment sums.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) move_kernel(Bufs<T> b, int want_moments) {
+    using V = typename Vec4<T>::type;
+    __shared__ GeoT<T> G;
+    if (threadIdx.x == 0) G.load(b.geo);
+    __syncthreads();
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = p < b.n;
+    V P = {}, Q = {};
+    int inst = 0;
+    int32_t j = -1;
+    if (valid) {
+        P = b.posA[p];
+        Q = b.velA[p];
+        inst = (int)R<T>::bits(Q.w);
+        j = b.best[p];
+    }
+    const InstDev I = b.inst[inst];
+    const uint32_t id = R<T>::bits(P.w);
+    const T x[3] = {P.x, P.y, P.z};
+    const T v[3] = {Q.x, Q.y, Q.z};
+    const T dt = (T)I.dt;
+    T xn[3] = {x[0], x[1], x[2]}, vn[3] = {v[0], v[1], v[2]};
+    T W = (T)0;
+    bool paired = false;
+    uint32_t idj = 0xffffffffu;
+    if (j >= 0) {
+        paired = b.best[j] == (int32_t)p;
+        if (paired || b.record) idj = R<T>::bits(b.posA[j].w);
+    }
+    if (paired) {
+        const V Pj = b.posA[j];
+        const V Qj = b.velA[j];
+        const T xj[3] = {Pj.x, Pj.y, Pj.z};
+        const T vj[3] = {Qj.x, Qj.y, Qj.z};
+        T dr[3] = {0, 0, 0}, dv[3];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) dr[d] = min_image<T>(R<T>::sub(x[d], xj[d]), G.hL[d], G.L[d]);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) dv[d] = R<T>::sub(v[d], vj[d]);
+        T a = R<T>::mul(dr[0], dv[0]);
+        a = R<T>::fma(dr[1], dv[1], a);
+        T bb = R<T>::mul(dv[0], dv[0]);
+        bb = R<T>::fma(dv[1], dv[1], bb);
+        if (DIM == 3) {
+            a = R<T>::fma(dr[2], dv[2], a);
+            bb = R<T>::fma(dv[2], dv[2], bb);
+        }
+        const T b3 = (DIM == 3) ? bb : R<T>::fma(dv[2], dv[2], bb);
+        const T tp = R<T>::div(-a, bb);                         // Eq. 12
+        const uint32_t lo_id = id < idj ? id : idj;
+        const T sgn = id < idj ? (T)1 : (T)-1;
+        const uint4 rnd = philox4x32_10(make_uint4(lo_id, b.st->step, 0u, 0u), I.seed_lo, I.seed_hi);
+        T u1, u2;
+        uniforms<T>(rnd, u1, u2);
+        const T cth = (T)1 - (T)2 * u1;
+        const T sth = (T)2 * R<T>::sqrt_(u1 * ((T)1 - u1));
+        T sphi, cphi;
+        sincos_2pi(u2, &sphi, &cphi);
+        const T nh[3] = {sth * cphi, sth * sphi, cth};
+        const T h = (T)0.5 * R<T>::sqrt_(b3);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const T vcm = (T)0.5 * (v[d] + vj[d]);
+            vn[d] = vcm + sgn * (h * nh[d]);
+        }
+        const T rest = R<T>::sub(dt, tp);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            xn[d] = R<T>::add(R<T>::add(x[d], R<T>::mul(v[d], tp)), R<T>::mul(vn[d], rest));  // Eq. 13
+            W += (dr[d] + dv[d] * tp) * (vn[d] - v[d]);
+        }
+    } else {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) xn[d] = R<T>::add(x[d], R<T>::mul(v[d], dt));  // Eq. 14
+    }
+    // reflective walls (fold) and periodic wrap
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        const T lo = G.lo[d], hi = G.hi[d];
+        if (G.wall[d]) {
+            for (int it = 0; it < kFoldCap && (xn[d] < lo || xn[d] > hi); ++it) {
+                xn[d] = (xn[d] < lo) ? R<T>::sub((T)2 * lo, xn[d]) : R<T>::sub((T)2 * hi, xn[d]);
+                vn[d] = -vn[d];
+            }
+            if (xn[d] < lo) xn[d] = lo;
+            if (xn[d] > hi) xn[d] = hi;
+        } else {
+            const T L = G.L[d];
+            if (xn[d] >= hi) xn[d] = R<T>::sub(xn[d], L);
+            else if (xn[d] < lo) xn[d] = R<T>::add(xn[d], L);
+            if (xn[d] < lo || xn[d] >= hi) {
+                const T f = floor(R<T>::div(R<T>::sub(xn[d], lo), L));
+                xn[d] = R<T>::sub(R<T>::add(lo, R<T>::sub(xn[d], lo)), R<T>::mul(L, f));
+            }
+            if (xn[d] >= hi) xn[d] = lo;
+        }
+    }
+    uint32_t skey = 0, bin = 0;
+    keys_of<T, DIM>(G, I, xn, skey, bin);
+    const unsigned active = __ballot_sync(kFull, valid);
+    if (valid) {
+        const uint32_t slot = aggregated_increment(b.count, skey, active);
+        V Pn, Qn;
+        Pn.x = xn[0]; Pn.y = xn[1]; Pn.z = xn[2]; Pn.w = P.w;
+        Qn.x = vn[0]; Qn.y = vn[1]; Qn.z = vn[2]; Qn.w = Q.w;
+        b.posB[p] = Pn;
+        b.velB[p] = Qn;
+        b.key[p] = skey;
+        b.slot[p] = slot;
+        if (b.record) {
+            const int64_t gid = I.p_off + (int64_t)id;
+            b.rec_best[gid] = (j >= 0) ? (int32_t)idj : -1;
+            b.rec_partner[gid] = paired ? (int32_t)idj : -1;
+        }
+    }
+    const T v2 = vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2];
+    warp_vmax<T>(b.dyn, valid, inst, v2);
+    if (want_moments) warp_moments<T>(b.acc, valid, bin, vn, W, paired);
+}
+
+// Counting-sort scatter B -> A in search-key order.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) scatter_kernel(Bufs<T> b) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= b.n) return;
+    const uint32_t dst = b.start[b.key[p]] + b.slot[p];
+    if (dst >= (uint32_t)b.n) {  // only after a failed scan; reported as a device error
+        atomicOr(&b.st->error, kErrKeyRange);
+        return;
+    }
+    b.posA[dst] = b.posB[p];
+    b.velA[dst] = b.velB[p];
+}
+
+// State of A in id order.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) gather_kernel(Bufs<T> b, T* __restrict__ pos3, T* __restrict__ vel3) {
+    using V = typename Vec4<T>::type;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= b.n) return;
+    const V P = b.posA[p];
+    const V Q = b.velA[p];
+    const int inst = (int)R<T>::bits(Q.w);
+    const int64_t gid = b.inst[inst].p_off + (int64_t)R<T>::bits(P.w);
+    if (pos3) { pos3[3 * gid] = P.x; pos3[3 * gid + 1] = P.y; pos3[3 * gid + 2] = P.z; }
+    if (vel3) { vel3[3 * gid] = Q.x; vel3[3 * gid + 1] = Q.y; vel3[3 * gid + 2] = Q.z; }
+}
+
+// c-bin key (instance-local) of every particle of A, id order.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) cellkey_kernel(Bufs<T> b, int32_t* __restrict__ keys) {
+    using V = typename Vec4<T>::type;
+    __shared__ GeoT<T> G;
+    if (threadIdx.x == 0) G.load(b.geo);
+    __syncthreads();
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= b.n) return;
+    const V P = b.posA[p];
+    const V Q = b.velA[p];
+    const int inst = (int)R<T>::bits(Q.w);
+    const InstDev& I = b.inst[inst];
+    const T x[3] = {P.x, P.y, P.z};
+    uint32_t skey, bin;
+    keys_of<T, DIM>(G, I, x, skey, bin);
+    keys[I.p_off + (int64_t)R<T>::bits(P.w)] = (int32_t)(bin - I.bin_base);
+}
+
+// Moment sums of the current state A (zero virial).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) state_moments_kernel(Bufs<T> b) {
+    using V = typename Vec4<T>::type;
+    __shared__ GeoT<T> G;
+    if (threadIdx.x == 0) G.load(b.geo);
+    __syncthreads();
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = p < b.n;
+    V P = {}, Q = {};
+    int inst = 0;
+    if (valid) {
+        P = b.posA[p];
+        Q = b.velA[p];
+        inst = (int)R<T>::bits(Q.w);
+    }
+    const InstDev I = b.inst[inst];
+    const T x[3] = {P.x, P.y, P.z};
+    const T v[3] = {Q.x, Q.y, Q.z};
+    uint32_t skey = 0, bin = 0;
+    keys_of<T, DIM>(G, I, x, skey, bin);
+    warp_moments<T>(b.acc, valid, bin, v, (T)0, false);
+}
+
+// Particles per c-bin and largest |v|^2 per instance of the packed state in B
+// (statistics for the host's choice of search grid at init).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) cbin_hist_kernel(Bufs<T> b, uint32_t* __restrict__ hist,
+                                                             unsigned long long* vmax2) {
+    using V = typename Vec4<T>::type;
+    __shared__ GeoT<T> G;
+    if (threadIdx.x == 0) G.load(b.geo);
+    __syncthreads();
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= b.n) return;
+    const V P = b.posB[p];
+    const V Q = b.velB[p];
+    const int inst = (int)R<T>::bits(Q.w);
+    const InstDev& I = b.inst[inst];
+    const T x[3] = {P.x, P.y, P.z};
+    uint32_t skey, bin;
+    keys_of<T, DIM>(G, I, x, skey, bin);
+    atomicAdd(hist + bin, 1u);
+    const double v2 = (double)Q.x * Q.x + (double)Q.y * Q.y + (double)Q.z * Q.z;
+    atomicMax(vmax2 + inst, (unsigned long long)__double_as_longlong(v2));
+}
+
+// ------------------------------------------------------------- launchers
+inline unsigned blocks_for(int64_t n) { return (unsigned)((n + kThreads - 1) / kThreads); }
+
+#define KMC_DIM_DISPATCH(dim, KERNEL, ...)                                      \
+    do {                                                                        \
+        if ((dim) == 3) KERNEL<T, 3><<<blocks_for(b.n), kThreads, 0, s>>>(__VA_ARGS__); \
+        else KERNEL<T, 2><<<blocks_for(b.n), kThreads, 0, s>>>(__VA_ARGS__);    \
+    } while (0)
+
+template <typename T>
+cudaError_t launch_pack(const Bufs<T>& b, const T* pos3, const T* vel3, uint32_t* bad, cudaStream_t s) {
+    if (b.n == 0) return cudaSuccess;
+    KMC_DIM_DISPATCH(b.geo.dim, pack_kernel, b, pos3, vel3, bad);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_bin_init(const Bufs<T>& b, cudaStream_t s) {
+    if (b.n == 0) return cudaSuccess;
+    KMC_DIM_DISPATCH(b.geo.dim, bin_kernel, b);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_search(const Bufs<T>& b, cudaStream_t s) {
+    if (b.n == 0) return cudaSuccess;
+    KMC_DIM_DISPATCH(b.geo.dim, search_kernel, b);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_move(const Bufs<T>& b, int want_moments, cudaStream_t s) {
+    if (b.n == 0) return cudaSuccess;
+    KMC_DIM_DISPATCH(b.geo.dim, move_kernel, b, want_moments);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_scatter(const Bufs<T>& b, cudaStream_t s) {
+    if (b.n == 0) return cudaSuccess;
+    scatter_kernel<T><<<blocks_for(b.n), kThreads, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_gather_state(const Bufs<T>& b, T* pos3, T* vel3, cudaStream_t s) {
+    if (b.n == 0) return cudaSuccess;
+    gather_kernel<T><<<blocks_for(b.n), kThreads, 0, s>>>(b, pos3, vel3);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cell_keys(const Bufs<T>& b, int32_t* keys, cudaStream_t s) {
+    if (b.n == 0) return cudaSuccess;
+    KMC_DIM_DISPATCH(b.geo.dim, cellkey_kernel, b, keys);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_moments_state(const Bufs<T>& b, cudaStream_t s) {
+    if (b.n == 0) return cudaSuccess;
+    KMC_DIM_DISPATCH(b.geo.dim, state_moments_kernel, b);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cbin_hist(const Bufs<T>& b, uint32_t* hist, unsigned long long* vmax2, cudaStream_t s) {
+    if (b.n == 0) return cudaSuccess;
+    KMC_DIM_DISPATCH(b.geo.dim, cbin_hist_kernel, b, hist, vmax2);
+    return cudaGetLastError();
+}
+
+#define KMC_INSTANTIATE(T)                                                                        \
+    template cudaError_t launch_pack<T>(const Bufs<T>&, const T*, const T*, uint32_t*, cudaStream_t); \
+    template cudaError_t launch_bin_init<T>(const Bufs<T>&, cudaStream_t);                         \
+    template cudaError_t launch_search<T>(const Bufs<T>&, cudaStream_t);                           \
+    template cudaError_t launch_move<T>(const Bufs<T>&, int, cudaStream_t);                        \
+    template cudaError_t launch_scatter<T>(const Bufs<T>&, cudaStream_t);                          \
+    template cudaError_t launch_gather_state<T>(const Bufs<T>&, T*, T*, cudaStream_t);             \
+    template cudaError_t launch_cell_keys<T>(const Bufs<T>&, int32_t*, cudaStream_t);              \
+    template cudaError_t launch_moments_state<T>(const Bufs<T>&, cudaStream_t);                   \
+    template cudaError_t launch_cbin_hist<T>(const Bufs<T>&, uint32_t*, unsigned long long*, cudaStream_t);
+
+}  // namespace kmc

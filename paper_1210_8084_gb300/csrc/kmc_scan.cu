@@ -1,0 +1,232 @@
+// kmc_scan.cu -- single-pass exclusive scan of the search-key histogram
+// (decoupled look-back) and the moment finalisation kernels.
+//
+// The scan turns count[k] (particles per search cell) into start[k], the first
+// sorted position of cell k, and clears count for the next step.  Tiles are
+// claimed with an atomic ticket, so every predecessor of a tile has already
+// started when the tile looks back; each wait is bounded (kSpinCap) and sets
+// kErrScanTimeout instead of hanging.
+//
+// The block holding tile 0 also rolls the per-instance step bookkeeping: the
+// largest speed of the new state becomes current and the search half-window
+// k_d = ceil(D' / w_d) with D' = 1.001 (R + 2 v_max dt) + 1e-5 L_d is derived
+// from it.  Any pair that passes the acceptance test is closer than
+// R + |v_rel| t_poca <= R + 2 v_max dt at the start of the step, so the window
+// never drops a candidate of the 3^D c-bin neighbourhood.
+#include <math.h>
+
+#include "kmc_internal.h"
+
+namespace kmc {
+
+namespace {
+
+constexpr unsigned long long kFlagAgg = 1ull << 32;
+constexpr unsigned long long kFlagInc = 2ull << 32;
+
+__device__ __forceinline__ unsigned long long load_status(const unsigned long long* p) {
+    return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+__device__ void step_bookkeeping(InstDyn* dyn, const InstDev* inst, int n_inst, DevState* st, const Geo& geo,
+                                 int bump) {
+    for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
+        const unsigned long long nx = dyn[i].vmax2_next;
+        dyn[i].vmax2_cur = nx;
+        dyn[i].vmax2_next = 0ull;
+        const double vmax = sqrt(__longlong_as_double((long long)nx));
+        const double D = sqrt(inst[i].R2) + 2.0 * vmax * inst[i].dt;
+        for (int d = 0; d < 3; ++d) {
+            const double Dp = D * 1.001 + 1e-5 * geo.L[d];
+            const double r = Dp / inst[i].w[d];
+            int k = inst[i].M[d];
+            if (r < (double)inst[i].M[d]) k = (int)ceil(r);
+            dyn[i].k[d] = k < 1 ? 1 : k;
+        }
+    }
+    if (threadIdx.x == 0 && bump) st->step += 1u;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_kernel(uint32_t* __restrict__ count,
+                                                            uint32_t* __restrict__ start,
+                                                            unsigned long long* status, InstDyn* dyn,
+                                                            const InstDev* inst, int n_inst, DevState* st,
+                                                            Geo geo, int bump) {
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_warp[kScanThreads / 32];
+    __shared__ uint32_t s_prefix;
+    if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(&status[0], 1ull);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile == 0) step_bookkeeping(dyn, inst, n_inst, st, geo, bump);
+
+    const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const size_t base = (size_t)tile * kScanTile + (size_t)threadIdx.x * kScanItems;
+    uint32_t it[kScanItems];
+    const uint4* src = reinterpret_cast<const uint4*>(count + base);
+#pragma unroll
+    for (int q = 0; q < kScanItems / 4; ++q) {
+        const uint4 v = src[q];
+        it[4 * q + 0] = v.x; it[4 * q + 1] = v.y; it[4 * q + 2] = v.z; it[4 * q + 3] = v.w;
+    }
+    uint32_t total = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const uint32_t c = it[i];
+        it[i] = total;          // exclusive within the thread
+        total += c;
+    }
+    // block-wide exclusive scan of the thread totals
+    uint32_t inc = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        if ((int)lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < kScanThreads / 32 ? s_warp[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if ((int)lane >= o) wi += y;
+        }
+        const uint32_t aggregate = __shfl_sync(0xffffffffu, wi, kScanThreads / 32 - 1);
+        if (lane < kScanThreads / 32) s_warp[lane] = wi - w;  // exclusive warp offsets
+        // decoupled look-back
+        uint32_t prefix = 0;
+        if (tile == 0) {
+            if (lane == 0) atomicExch(&status[1], kFlagInc | (unsigned long long)aggregate);
+        } else {
+            if (lane == 0) atomicExch(&status[1 + tile], kFlagAgg | (unsigned long long)aggregate);
+            long long pred = (long long)tile - 1;
+            bool done = false;
+            while (!done) {
+                const long long t = pred - (long long)lane;
+                unsigned long long sv = kFlagInc;
+                if (t >= 0) {
+                    uint32_t spins = 0;
+                    for (;;) {
+                        sv = load_status(&status[1 + t]);
+                        if ((sv >> 32) != 0ull) break;
+                        if (++spins > kSpinCap) {
+                            atomicOr(&st->error, kErrScanTimeout);
+                            sv = kFlagInc;
+                            break;
+                        }
+                        if (spins > 16) __nanosleep(64);
+                    }
+                }
+                const uint32_t flag = (uint32_t)(sv >> 32);
+                const uint32_t val = (uint32_t)sv;
+                const unsigned incl = __ballot_sync(0xffffffffu, flag == 2u);
+                uint32_t contrib;
+                if (incl) {
+                    const int first = __ffs(incl) - 1;
+                    contrib = ((int)lane <= first) ? val : 0u;
+                    done = true;
+                } else {
+                    contrib = val;
+                    pred -= 32;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+                prefix += contrib;
+            }
+            if (lane == 0) atomicExch(&status[1 + tile], kFlagInc | (unsigned long long)(prefix + aggregate));
+        }
+        if (lane == 0) s_prefix = prefix;
+    }
+    __syncthreads();
+    const uint32_t off = s_prefix + s_warp[warp] + (inc - total);
+    uint4* dst = reinterpret_cast<uint4*>(start + base);
+    uint4* clr = reinterpret_cast<uint4*>(count + base);
+#pragma unroll
+    for (int q = 0; q < kScanItems / 4; ++q) {
+        dst[q] = make_uint4(off + it[4 * q], off + it[4 * q + 1], off + it[4 * q + 2], off + it[4 * q + 3]);
+        clr[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// Derived per-c-bin moments (Eqs. vel_b, stress, 18, 19 with the readings
+// u = Sum v / N, v_rms^2 = <|v - u|^2>, T = v_rms^2 / 3, p = n T + virial).
+__global__ void finalize_bins_kernel(const InstDev* __restrict__ inst, Geo geo, const double* __restrict__ acc,
+                                     double* __restrict__ mom, int64_t n_bins, int64_t bins_per_inst) {
+    const int64_t bidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (bidx >= n_bins) return;
+    const double* a = acc + bidx * kAccFields;
+    double* o = mom + bidx * 16;
+    for (int k = 0; k < 8; ++k) o[k] = a[k];
+    double Vc = 1.0;
+    for (int d = 0; d < geo.dim; ++d) Vc *= geo.L[d] / (double)geo.n[d];
+    const double N = a[0];
+    if (N <= 0.0) {
+        for (int k = 8; k < 16; ++k) o[k] = 0.0;
+        return;
+    }
+    const double dt = inst[bidx / bins_per_inst].dt;
+    const double ux = a[1] / N, uy = a[2] / N, uz = a[3] / N;
+    const double c2 = (a[4] + a[5] + a[6]) / N - (ux * ux + uy * uy + uz * uz);
+    const double T = c2 / 3.0;
+    const double nd = N / Vc;
+    const double pkin = nd * T;
+    const double pvir = a[7] / (2.0 * geo.dim * Vc * dt);
+    o[8] = nd; o[9] = ux; o[10] = uy; o[11] = uz;
+    o[12] = T; o[13] = pkin; o[14] = pvir; o[15] = pkin + pvir;
+}
+
+// Per-instance totals (N, energy, momentum, virial, pairs) in a fixed order.
+__global__ void __launch_bounds__(256) finalize_glob_kernel(const double* __restrict__ acc,
+                                                            double* __restrict__ glob, int64_t bins_per_inst) {
+    __shared__ double sh[7][256];
+    const int i = blockIdx.x;
+    double s[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t b = threadIdx.x; b < bins_per_inst; b += blockDim.x) {
+        const double* a = acc + ((int64_t)i * bins_per_inst + b) * kAccFields;
+        s[0] += a[0];
+        s[1] += 0.5 * (a[4] + a[5] + a[6]);
+        s[2] += a[1];
+        s[3] += a[2];
+        s[4] += a[3];
+        s[5] += a[7];
+        s[6] += a[8];
+    }
+    for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] = s[k];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double* g = glob + (int64_t)i * 8;
+        for (int k = 0; k < 6; ++k) g[k] = sh[k][0];
+        g[6] = 0.5 * sh[6][0];  // collided particles / 2 = pairs
+        g[7] = 0.0;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_scan(uint32_t* count, uint32_t* start, uint32_t n_keys, uint32_t n_tiles,
+                        unsigned long long* status, InstDyn* dyn, const InstDev* inst, int n_inst,
+                        DevState* st, Geo geo, int bump_step, cudaStream_t s) {
+    (void)n_keys;
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(unsigned long long) * (1 + (size_t)n_tiles), s);
+    if (e != cudaSuccess) return e;
+    scan_kernel<<<n_tiles, kScanThreads, 0, s>>>(count, start, status, dyn, inst, n_inst, st, geo, bump_step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const InstDev* inst, int n_inst, Geo geo, const double* acc, double* mom,
+                            double* glob, int64_t n_bins, cudaStream_t s) {
+    if (n_bins == 0 || n_inst == 0) return cudaSuccess;
+    const int64_t per = n_bins / n_inst;
+    finalize_bins_kernel<<<(unsigned)((n_bins + 255) / 256), 256, 0, s>>>(inst, geo, acc, mom, n_bins, per);
+    finalize_glob_kernel<<<n_inst, 256, 0, s>>>(acc, glob, per);
+    return cudaGetLastError();
+}
+
+}  // namespace kmc

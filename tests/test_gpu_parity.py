@@ -1,0 +1,281 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer results (cell keys, closest candidates, pairs) must match bit for
+bit: in binary64 against the binary64 oracle, in binary32 against the
+oracle's binary32 decision mode.  Post-collision velocities must agree to
+1e-5 relative (binary32 state vs binary64 oracle) or 1e-12 (binary64 state),
+positions to the corresponding rounding.  Every case starts from the same
+seeded state on both sides.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+WALL, PER = 1, 0
+
+
+def _setup():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+def run_gpu_step(pos, vel, dim, n_cells, lo, hi, bc, lam, dt, seed, precision, step=0, sub_cells=(0, 0, 0),
+                 nsteps=1):
+    import paper_1210_8084_gb300 as k
+    cfg = k.make_config(dim_pos=dim, n_cells=n_cells, lo=lo, hi=hi, bc=bc, lam=lam, dt=dt, seed=seed,
+                        precision=precision, flags=k.KMC_FLAG_RECORD, sub_cells=sub_cells)
+    sim = k.Simulation(cfg, pos, vel)
+    if step:
+        p0, v0 = sim.state()
+        sim.set_state(p0, v0, step=step)
+    info = sim.info()
+    keys = sim.cell_keys()
+    sim.step(nsteps, want_moments=1)
+    best, partner = sim.partners()
+    p, v = sim.state()
+    raw, der, glob = sim.moments()
+    sim.close()
+    return dict(info=info, keys=keys, best=best, partner=partner, pos=p, vel=v, raw=raw, der=der, glob=glob)
+
+
+def oracle_step(pos, vel, dim, n_cells, lo, hi, bc, R2, dt, seed, step, decide32):
+    import oracle
+    P = oracle.make_params(dim, n_cells, lo, hi, bc, R2=R2, dt=dt, seed=seed, step=step, decide32=decide32)
+    key, _ = oracle.cell_keys(P, pos)
+    best = oracle.best_partners(P, pos, vel)
+    po, vo, W, paired = oracle.collide_move(P, pos, vel, best)
+    raw, der, glob = oracle.moments(P, po, vo, W)
+    return dict(P=P, keys=key, best=best, partner=paired, pos=po, vel=vo, W=W, raw=raw, der=der, glob=glob)
+
+
+def compare_step(g, o, precision, pos0, vel0, dim):
+    assert np.array_equal(g["keys"], o["keys"]), "cell keys"
+    nb = (g["best"] != o["best"]).sum()
+    assert nb == 0, f"{nb} closest candidates differ"
+    assert np.array_equal(g["partner"], o["partner"]), "pairs"
+    vscale = np.abs(vel0).max()
+    tol_v = 1e-12 if precision == 64 else 1e-5
+    dv = np.abs(g["vel"] - o["vel"]).max(1) / np.maximum(np.linalg.norm(o["vel"], axis=1), 1e-3 * vscale)
+    assert dv.max() <= tol_v, f"velocity rel err {dv.max()}"
+    tol_x = 1e-12 if precision == 64 else 4e-6
+    assert np.abs(g["pos"][:, :dim] - o["pos"][:, :dim]).max() <= tol_x * max(1.0, np.abs(pos0).max())
+    # moments: counts exact when every end position is binned the same way
+    same_bins = np.array_equal(g["raw"][:, 0], o["raw"][:, 0])
+    if precision == 64:
+        assert same_bins
+    rel = 1e-10 if precision == 64 else 1e-5
+    e_g, e_o = g["glob"][0, 1], o["glob"][1]
+    assert abs(e_g - e_o) <= rel * e_o
+    assert g["glob"][0, 6] == len(np.nonzero(o["partner"] >= 0)[0]) / 2
+
+
+CASES = [
+    # name, n, dim, n_cells, lo, hi, bc, lam, dt, precision
+    ("sod1d_fp64_200k", 200_000, 3, (200, 1, 1), (0, 0, 0), (1, 1, 1), (WALL, PER, PER), 1e-3, 1e-3, 64),
+    ("sod1d_fp32_1M_k1e-3", 1_000_000, 3, (500, 1, 1), (0, 0, 0), (1, 1, 1), (WALL, PER, PER), 1e-3, 4e-4, 32),
+    ("sod1d_fp32_1M_k1e-4", 1_000_000, 3, (500, 1, 1), (0, 0, 0), (1, 1, 1), (WALL, PER, PER), 1e-4, 4e-4, 32),
+    ("sod1d_fp32_1M_k1", 1_000_000, 3, (500, 1, 1), (0, 0, 0), (1, 1, 1), (WALL, PER, PER), 1.0, 4e-4, 32),
+    ("quad2d_fp32_300k", 300_000, 2, (96, 96, 1), (0, 0, 0), (1, 1, 1), (WALL, WALL, PER), 5e-4, 0.2 / 96, 32),
+    ("sod3d_fp32_400k", 400_000, 3, (128, 8, 8), (0, 0, 0), (1, 1 / 16, 1 / 16), (WALL, PER, PER), 2e-4,
+     0.2 / 128, 32),
+    ("box3d_fp64_ragged", 12_345, 3, (5, 4, 3), (-1, 0, 2), (1, 0.5, 3), (PER, WALL, PER), 1e-2, 5e-3, 64),
+    ("box2d_fp32_periodic_2cells", 3_001, 2, (2, 2, 1), (0, 0, 0), (1, 1, 1), (PER, PER, PER), 1e-2, 5e-3, 32),
+]
+
+
+def make_inputs(name, n, dim, lo, hi):
+    from paper_1210_8084_gb300 import inputs
+    if name.startswith("quad"):
+        return inputs.quadrants_2d(n, seed=3)
+    if name.startswith("sod"):
+        return inputs.sod_tube(n, seed=3, lo=lo, hi=hi)
+    pos, vel = inputs.periodic_box(n, seed=3, lo=lo, hi=hi)
+    if dim == 2:
+        pos[:, 2] = 0.0
+    return pos, vel
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_one_step_parity(case):
+    _setup()
+    name, n, dim, n_cells, lo, hi, bc, lam, dt, prec = case
+    pos, vel = make_inputs(name, n, dim, lo, hi)
+    if prec == 32:
+        pos = pos.astype(np.float32).astype(np.float64)
+        vel = vel.astype(np.float32).astype(np.float64)
+    seed = 11
+    g = run_gpu_step(pos, vel, dim, n_cells, lo, hi, bc, lam, dt, seed, prec)
+    o = oracle_step(pos, vel, dim, n_cells, lo, hi, bc, g["info"].R2, dt, seed, 0, prec == 32)
+    assert (g["best"] >= 0).mean() > 0.02 or lam >= 1.0
+    compare_step(g, o, prec, pos, vel, dim)
+
+
+def test_contact_distance_matches_oracle_bitwise():
+    _setup()
+    import oracle
+    pos, vel = make_inputs("sod", 5000, 3, (0, 0, 0), (1, 1, 1))
+    for lam in (1e-4, 1e-3, 0.37, 1.0):
+        g = run_gpu_step(pos, vel, 3, (10, 1, 1), (0, 0, 0), (1, 1, 1), (WALL, PER, PER), lam, 1e-3, 0, 64, nsteps=0)
+        assert g["info"].R2 == oracle.contact_R2(lam, 0.0, 5000.0)
+
+
+@pytest.mark.parametrize("sub", [(1, 1, 1), (1, 3, 2), (1, 40, 40), (0, 0, 0)])
+def test_search_grid_subdivision_does_not_change_results(sub):
+    """Any subdivision of the c-bins into search cells returns the same
+    closest candidates as the plain 3^D neighbourhood (the window adapts)."""
+    _setup()
+    pos, vel = make_inputs("sod", 60_000, 3, (0, 0, 0), (1, 1, 1))
+    pos = pos.astype(np.float32).astype(np.float64)
+    vel = vel.astype(np.float32).astype(np.float64)
+    args = (3, (40, 1, 1), (0, 0, 0), (1, 1, 1), (WALL, PER, PER), 1e-3, 1e-3, 5)
+    g = run_gpu_step(pos, vel, *args, precision=32, sub_cells=sub)
+    o = oracle_step(pos, vel, 3, (40, 1, 1), (0, 0, 0), (1, 1, 1), (WALL, PER, PER), g["info"].R2, 1e-3, 5, 0, True)
+    assert np.array_equal(g["best"], o["best"])
+    assert np.array_equal(g["partner"], o["partner"])
+
+
+def test_multi_step_each_step_from_device_state():
+    """Five steps: every device step equals the oracle step taken from the
+    device's own state at that point (binary64 integers bit-exact)."""
+    _setup()
+    import paper_1210_8084_gb300 as k
+    import oracle
+    pos, vel = make_inputs("sod", 50_000, 3, (0, 0, 0), (1, 1, 1))
+    cfg = k.make_config(dim_pos=3, n_cells=(50, 1, 1), bc=(WALL, PER, PER), lam=1e-3, dt=4e-3, seed=21,
+                        precision=64, flags=k.KMC_FLAG_RECORD)
+    sim = k.Simulation(cfg, pos, vel)
+    R2 = sim.info().R2
+    for s in range(5):
+        p0, v0 = sim.state()
+        sim.step(1)
+        best, partner = sim.partners()
+        p1, v1 = sim.state()
+        P = oracle.make_params(3, (50, 1, 1), (0, 0, 0), (1, 1, 1), (WALL, PER, PER), R2=R2, dt=4e-3, seed=21, step=s)
+        bo = oracle.best_partners(P, p0, v0)
+        po, vo, W, paired = oracle.collide_move(P, p0, v0, bo)
+        assert np.array_equal(best, bo) and np.array_equal(partner, paired), f"step {s}"
+        assert np.abs(v1 - vo).max() <= 1e-12 * np.abs(v0).max()
+        assert sim.info().step == s + 1
+    sim.close()
+
+
+def test_checkpoint_resume_is_bit_identical():
+    _setup()
+    import paper_1210_8084_gb300 as k
+    pos, vel = make_inputs("sod", 100_000, 3, (0, 0, 0), (1, 1, 1))
+    cfg = k.make_config(dim_pos=3, n_cells=(100, 1, 1), bc=(WALL, PER, PER), lam=1e-3, dt=2e-3, seed=3,
+                        precision=32)
+    a = k.Simulation(cfg, pos, vel)
+    a.step(6)
+    pa, va = a.state()
+    b = k.Simulation(cfg, pos, vel)
+    b.step(3)
+    pb, vb = b.state()
+    step = b.info().step
+    b.close()
+    c = k.Simulation(cfg, pos, vel)
+    c.set_state(pb, vb, step=step)
+    c.step(3)
+    pc, vc = c.state()
+    assert np.array_equal(pa, pc) and np.array_equal(va, vc)
+    a.close()
+    c.close()
+
+
+def test_batched_equals_plain_instances():
+    """Instances of a batched run evolve exactly as separate runs."""
+    _setup()
+    import paper_1210_8084_gb300 as k
+    from paper_1210_8084_gb300 import inputs
+    ns = [7_000, 20_001, 3_333, 50_000]
+    lams = [1e-3, 1e-1, 1e-4, 1.0]
+    insts, P, V = [], [], []
+    for i, (n, lam) in enumerate(zip(ns, lams)):
+        p, v = inputs.sod_tube(n, seed=100 + i)
+        P.append(p)
+        V.append(v)
+        insts.append(dict(n=n, lam=lam, dt=5e-3, seed=1000 + i))
+    base = dict(dim_pos=3, n_cells=(40, 1, 1), bc=(WALL, PER, PER), precision=32)
+    batch = k.Simulation(k.make_config(**base, instances=insts), np.concatenate(P), np.concatenate(V))
+    batch.step(8)
+    pb, vb = batch.state()
+    raw_b, der_b, glob_b = batch.moments()
+    off = 0
+    for i, inst in enumerate(insts):
+        plain = k.Simulation(k.make_config(**base, lam=inst["lam"], dt=inst["dt"], seed=inst["seed"]), P[i], V[i])
+        plain.step(8)
+        pp, vp = plain.state()
+        raw_p, der_p, glob_p = plain.moments()
+        assert np.array_equal(pp, pb[off:off + ns[i]]), i
+        assert np.array_equal(vp, vb[off:off + ns[i]]), i
+        assert np.array_equal(raw_p[:, 0], raw_b[40 * i:40 * (i + 1), 0])
+        assert glob_p[0, 6] == glob_b[i, 6]
+        assert np.allclose(raw_p, raw_b[40 * i:40 * (i + 1)], rtol=1e-12, atol=1e-9)
+        off += ns[i]
+        plain.close()
+    batch.close()
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 255, 257])
+def test_tiny_and_ragged_sizes(n):
+    _setup()
+    import paper_1210_8084_gb300 as k
+    rng = np.random.default_rng(n)
+    pos = rng.random((n, 3))
+    vel = rng.normal(0, 1, (n, 3))
+    if n == 2:  # a head-on pair
+        pos = np.array([[0.4, 0.5, 0.5], [0.6, 0.5, 0.5]])
+        vel = np.array([[1.0, 0, 0], [-1.0, 0, 0]])
+    cfg = k.make_config(dim_pos=3, n_cells=(3, 2, 1), bc=(WALL, PER, PER), sigma=0.5, dt=0.15, seed=1,
+                        precision=64, flags=k.KMC_FLAG_RECORD)
+    sim = k.Simulation(cfg, pos, vel)
+    sim.step(2)
+    p, v = sim.state()
+    raw, der, glob = sim.moments()
+    assert raw[:, 0].sum() == n
+    if n == 2:
+        best, partner = sim.partners()
+        assert glob[0, 1] == pytest.approx(1.0, rel=1e-14)   # energy kept across the collision
+        assert np.allclose(v.sum(0), 0.0, atol=1e-15)
+    sim.close()
+
+
+def test_invalid_particles_rejected():
+    _setup()
+    import paper_1210_8084_gb300 as k
+    pos = np.full((10, 3), 0.5)
+    vel = np.zeros((10, 3))
+    cfg = k.make_config(dim_pos=3, n_cells=(2, 1, 1), lam=1e-3, dt=1e-3, precision=64)
+    for bad in ("nan", "outside", "periodic_hi"):
+        p = pos.copy()
+        if bad == "nan":
+            p[3, 1] = np.nan
+        elif bad == "outside":
+            p[4, 0] = 1.5
+        else:
+            p[5, 1] = 1.0   # periodic dims are [lo, hi)
+        with pytest.raises(k.KmcError) as e:
+            k.Simulation(cfg, p, vel)
+        assert e.value.code == k.KMC_EINVAL
+
+
+def test_energy_conservation_fp32():
+    """Binary32 state: total energy drifts by < 1e-6 relative over 100 steps
+    (binary64 per-bin sums)."""
+    _setup()
+    import paper_1210_8084_gb300 as k
+    pos, vel = make_inputs("sod", 1_000_000, 3, (0, 0, 0), (1, 1, 1))
+    cfg = k.make_config(dim_pos=3, n_cells=(500, 1, 1), bc=(WALL, PER, PER), lam=1e-3, dt=4e-4, seed=2,
+                        precision=32)
+    sim = k.Simulation(cfg, pos, vel)
+    e0 = sim.moments()[2][0, 1]
+    sim.step(100)
+    e1 = sim.moments()[2][0, 1]
+    sim.close()
+    assert abs(e1 - e0) <= 1e-6 * e0, (e0, e1)
