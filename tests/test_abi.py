@@ -20,9 +20,8 @@ def header_functions():
 @pytest.fixture(scope="module")
 def built_lib():
     import __graft_entry__ as g
-    from paper_1210_8084_gb300 import build as kb
-    kb.build()
-    return kb.LIB
+    g.build()
+    return os.path.join(ROOT, "paper_1210_8084_gb300", "libkmc.so")
 
 
 def test_header_declares_the_boundary():
