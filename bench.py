@@ -134,8 +134,7 @@ def ours(args):
     n = w["n"]
     pos, vel = inputs.make_state(w, seed=w["seed"] + rank)
     dtype = np.float32 if w["precision"] == 32 else np.float64
-    pos = np.ascontiguousarray(pos, dtype=dtype)
-    vel = np.ascontiguousarray(vel, dtype=dtype)
+    pos, vel = inputs.cast_state(pos, vel, dtype, w["lo"], w["hi"], w["bc"])
     stream = torch.cuda.Stream()
     cfg = k.make_config(dim_pos=w["dim_pos"], n_cells=w["n_cells"], lo=w["lo"], hi=w["hi"], bc=w["bc"],
                         lam=w["lam"], dt=w["dt"], seed=w["seed"] + rank, precision=w["precision"],

@@ -94,6 +94,18 @@ def periodic_box(n, seed=0, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), T=1.0, v_in=
     return pos, vel
 
 
+def cast_state(pos, vel, dtype, lo, hi, bc):
+    """Round a state to the working precision; a periodic coordinate that
+    rounds up to the upper face is the same point as the lower face."""
+    pos = np.ascontiguousarray(pos, dtype=dtype).copy()
+    vel = np.ascontiguousarray(vel, dtype=dtype)
+    for d in range(3):
+        if bc[d] == PERIODIC:
+            h = dtype(hi[d])
+            pos[:, d] = np.where(pos[:, d] >= h, dtype(lo[d]), pos[:, d])
+    return pos, vel
+
+
 def log_uniform_instances(n_instances, seed=0, n_range=(50_000, 2_000_000), lam_range=(1e-4, 1.0)):
     """Per-instance particle counts and mean free paths, log-uniform."""
     g = _rng(seed, 3)

@@ -89,6 +89,13 @@ CASES = [
 ]
 
 
+def f32_state(pos, vel, lo, hi, bc):
+    """The binary32 state both sides start from, held in float64."""
+    from paper_1210_8084_gb300 import inputs
+    p, v = inputs.cast_state(pos, vel, np.float32, lo, hi, bc)
+    return p.astype(np.float64), v.astype(np.float64)
+
+
 def make_inputs(name, n, dim, lo, hi):
     from paper_1210_8084_gb300 import inputs
     if name.startswith("quad"):
@@ -107,8 +114,7 @@ def test_one_step_parity(case):
     name, n, dim, n_cells, lo, hi, bc, lam, dt, prec = case
     pos, vel = make_inputs(name, n, dim, lo, hi)
     if prec == 32:
-        pos = pos.astype(np.float32).astype(np.float64)
-        vel = vel.astype(np.float32).astype(np.float64)
+        pos, vel = f32_state(pos, vel, lo, hi, bc)
     seed = 11
     g = run_gpu_step(pos, vel, dim, n_cells, lo, hi, bc, lam, dt, seed, prec)
     o = oracle_step(pos, vel, dim, n_cells, lo, hi, bc, g["info"].R2, dt, seed, 0, prec == 32)
@@ -131,8 +137,7 @@ def test_search_grid_subdivision_does_not_change_results(sub):
     closest candidates as the plain 3^D neighbourhood (the window adapts)."""
     _setup()
     pos, vel = make_inputs("sod", 60_000, 3, (0, 0, 0), (1, 1, 1))
-    pos = pos.astype(np.float32).astype(np.float64)
-    vel = vel.astype(np.float32).astype(np.float64)
+    pos, vel = f32_state(pos, vel, (0, 0, 0), (1, 1, 1), (WALL, PER, PER))
     args = (3, (40, 1, 1), (0, 0, 0), (1, 1, 1), (WALL, PER, PER), 1e-3, 1e-3, 5)
     g = run_gpu_step(pos, vel, *args, precision=32, sub_cells=sub)
     o = oracle_step(pos, vel, 3, (40, 1, 1), (0, 0, 0), (1, 1, 1), (WALL, PER, PER), g["info"].R2, 1e-3, 5, 0, True)
@@ -169,6 +174,7 @@ def test_checkpoint_resume_is_bit_identical():
     _setup()
     import paper_1210_8084_gb300 as k
     pos, vel = make_inputs("sod", 100_000, 3, (0, 0, 0), (1, 1, 1))
+    pos, vel = f32_state(pos, vel, (0, 0, 0), (1, 1, 1), (WALL, PER, PER))
     cfg = k.make_config(dim_pos=3, n_cells=(100, 1, 1), bc=(WALL, PER, PER), lam=1e-3, dt=2e-3, seed=3,
                         precision=32)
     a = k.Simulation(cfg, pos, vel)
@@ -197,7 +203,7 @@ def test_batched_equals_plain_instances():
     lams = [1e-3, 1e-1, 1e-4, 1.0]
     insts, P, V = [], [], []
     for i, (n, lam) in enumerate(zip(ns, lams)):
-        p, v = inputs.sod_tube(n, seed=100 + i)
+        p, v = f32_state(*inputs.sod_tube(n, seed=100 + i), (0, 0, 0), (1, 1, 1), (WALL, PER, PER))
         P.append(p)
         V.append(v)
         insts.append(dict(n=n, lam=lam, dt=5e-3, seed=1000 + i))
@@ -271,6 +277,7 @@ def test_energy_conservation_fp32():
     _setup()
     import paper_1210_8084_gb300 as k
     pos, vel = make_inputs("sod", 1_000_000, 3, (0, 0, 0), (1, 1, 1))
+    pos, vel = f32_state(pos, vel, (0, 0, 0), (1, 1, 1), (WALL, PER, PER))
     cfg = k.make_config(dim_pos=3, n_cells=(500, 1, 1), bc=(WALL, PER, PER), lam=1e-3, dt=4e-4, seed=2,
                         precision=32)
     sim = k.Simulation(cfg, pos, vel)
