@@ -222,7 +222,10 @@ def test_batched_equals_plain_instances():
         assert np.array_equal(vp, vb[off:off + ns[i]]), i
         assert np.array_equal(raw_p[:, 0], raw_b[40 * i:40 * (i + 1), 0])
         assert glob_p[0, 6] == glob_b[i, 6]
-        assert np.allclose(raw_p, raw_b[40 * i:40 * (i + 1)], rtol=1e-12, atol=1e-9)
+        # moment sums: binary32 warp partials summed in binary64, so the grouping
+        # of particles into warps (which differs between the two runs) shows
+        # at the binary32 rounding level only
+        assert np.allclose(raw_p, raw_b[40 * i:40 * (i + 1)], rtol=2e-6, atol=1e-6 * raw_p[:, 4:7].max())
         off += ns[i]
         plain.close()
     batch.close()
