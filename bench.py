@@ -138,7 +138,7 @@ def ours(args):
     stream = torch.cuda.Stream()
     cfg = k.make_config(dim_pos=w["dim_pos"], n_cells=w["n_cells"], lo=w["lo"], hi=w["hi"], bc=w["bc"],
                         lam=w["lam"], dt=w["dt"], seed=w["seed"] + rank, precision=w["precision"],
-                        stream=stream.cuda_stream)
+                        stream=stream.cuda_stream, occupancy_target=args.occ)
 
     def barrier():
         torch.cuda.synchronize()
@@ -217,6 +217,7 @@ def ours(args):
         "config": {"workload": f"{args.workload} lambda/L={w['lam']:g}", "n_particles": n,
                    "n_cells": list(w["n_cells"]), "dt": w["dt"], "precision": w["precision"],
                    "search_cells": int(info.n_search_cells), "sub_cells": list(info.sub_cells),
+                   "occupancy_target": args.occ,
                    "l2": "no flush: state 2 x %.2f GB > 129 MB L2" % (n * 64 / 1e9),
                    "parallelism": f"replicas x{world}"},
         "phase_ms_per_step": {p: round(v, 4) for p, v in phases.items()},
@@ -306,6 +307,7 @@ def main():
     ap.add_argument("--workload", default="sod1d_fp32_16M")
     ap.add_argument("--lam", type=float, default=None)
     ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--occ", type=float, default=0.0, help="particles per search cell (0: library default)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

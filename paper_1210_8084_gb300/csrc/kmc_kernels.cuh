@@ -204,11 +204,23 @@ __device__ __forceinline__ void warp_vmax(InstDyn* dyn, bool valid, int inst, T 
     }
 }
 
-// Moment sums per c-bin: lanes with the same bin are reduced with warp
-// shuffles, then the group leader adds the totals to the binary64 accumulator.
+// Moment sums per c-bin, aggregated in three levels so that few binary64
+// atomics reach any one bin: lanes with the same bin are reduced with warp
+// shuffles; each warp group's totals go to a shared-memory slot list; after a
+// block barrier the first slot of every distinct bin adds up its duplicates and
+// issues the global atomics.  All threads of the block must call this.
 template <typename T>
-__device__ __forceinline__ void warp_moments(double* acc, bool valid, uint32_t bin, const T v[3], T W,
-                                             bool collided) {
+struct MomentSlots {
+    uint32_t bin[kThreads];
+    T f[7][kThreads];
+    int cnt[kThreads];
+    int coll[kThreads];
+    int n;
+};
+
+template <typename T>
+__device__ __forceinline__ void block_moments(MomentSlots<T>& S, double* acc, bool valid, uint32_t bin,
+                                              const T v[3], T W, bool collided) {
     unsigned todo = __ballot_sync(kFull, valid);
     const unsigned coll = __ballot_sync(kFull, valid && collided);
     while (todo) {
@@ -230,14 +242,37 @@ __device__ __forceinline__ void warp_moments(double* acc, bool valid, uint32_t b
             for (int k = 0; k < 7; ++k) f[k] += __shfl_xor_sync(kFull, f[k], o);
         }
         if ((int)lane_id() == leader) {
-            double* a = acc + (size_t)gb * kAccFields;
-            atomicAdd(a + 0, (double)__popc(grp));
+            const int slot = atomicAdd(&S.n, 1);
+            S.bin[slot] = gb;
 #pragma unroll
-            for (int k = 0; k < 7; ++k) atomicAdd(a + 1 + k, (double)f[k]);
-            const int nc = __popc(grp & coll);
-            if (nc) atomicAdd(a + 8, (double)nc);
+            for (int k = 0; k < 7; ++k) S.f[k][slot] = f[k];
+            S.cnt[slot] = __popc(grp);
+            S.coll[slot] = __popc(grp & coll);
         }
         todo &= ~grp;
+    }
+    __syncthreads();
+    const int ns = S.n;
+    for (int t = threadIdx.x; t < ns; t += blockDim.x) {
+        const uint32_t mb = S.bin[t];
+        bool first = true;
+        for (int u = 0; u < t; ++u)
+            if (S.bin[u] == mb) { first = false; break; }
+        if (!first) continue;
+        double tot[7] = {0, 0, 0, 0, 0, 0, 0};
+        int c = 0, cc = 0;
+        for (int u = t; u < ns; ++u) {
+            if (S.bin[u] != mb) continue;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) tot[k] += (double)S.f[k][u];
+            c += S.cnt[u];
+            cc += S.coll[u];
+        }
+        double* a = acc + (size_t)mb * kAccFields;
+        atomicAdd(a + 0, (double)c);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) atomicAdd(a + 1 + k, tot[k]);
+        if (cc) atomicAdd(a + 8, (double)cc);
     }
 }
 
@@ -340,37 +375,135 @@ __device__ __forceinline__ bool poca_test(const GeoT<T>& G, const T xi[3], const
     return true;
 }
 
+// Candidate data through the read-only path.
+__device__ __forceinline__ float4 ldg_vec(const float4* p) { return __ldg(p); }
+__device__ __forceinline__ dvec4 ldg_vec(const dvec4* p) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 c = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    dvec4 r;
+    r.x = a.x; r.y = a.y; r.z = c.x; r.w = c.y;
+    return r;
+}
+
+// The acceptance test with the separation r_i - r_j formed as
+// (x_i - x_j) + shift_d: the shift is the periodic image of the candidate's
+// row (0, +L or -L) when MINIMG is false, and the per-candidate minimum image
+// of every periodic dimension when MINIMG is true.  Both give the same bits as
+// the oracle's minimum image: inside a window narrower than half the box the
+// image of a row is the same for all its candidates.
+template <typename T, int DIM, bool MINIMG>
+__device__ __forceinline__ bool poca_test_sh(const GeoT<T>& G, const T xi[3], const T vi[3], const T xj[3],
+                                             const T vj[3], const T sh[3], T dt, T R2, T& d2) {
+    T dr[3], dv[3];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        const T x = R<T>::sub(xi[d], xj[d]);
+        dr[d] = MINIMG ? min_image<T>(x, G.hL[d], G.L[d]) : R<T>::add(x, sh[d]);
+        dv[d] = R<T>::sub(vi[d], vj[d]);
+    }
+    T a = R<T>::mul(dr[0], dv[0]);
+    a = R<T>::fma(dr[1], dv[1], a);
+    T bb = R<T>::mul(dv[0], dv[0]);
+    bb = R<T>::fma(dv[1], dv[1], bb);
+    if (DIM == 3) {
+        a = R<T>::fma(dr[2], dv[2], a);
+        bb = R<T>::fma(dv[2], dv[2], bb);
+    }
+    if (!(bb > (T)0 && a < (T)0 && R<T>::fma(bb, dt, a) > (T)0)) return false;
+    T r2 = R<T>::mul(dr[0], dr[0]);
+    r2 = R<T>::fma(dr[1], dr[1], r2);
+    if (DIM == 3) r2 = R<T>::fma(dr[2], dr[2], r2);
+    const T disc = R<T>::fma(a, a, -R<T>::mul(bb, R<T>::sub(r2, R2)));
+    if (!(disc >= (T)0)) return false;
+    d2 = R<T>::sub(r2, R<T>::div(R<T>::mul(a, a), bb));
+    return true;
+}
+
 // Search window of one dimension in search-cell coordinates: within k cells of
-// g and inside the c-bins c-1 .. c+1.  Periodic windows are taken modulo M
-// (the full row when they would cover it); walled ones are cut at the box.
+// g and inside the c-bins c-1 .. c+1; cut at walls.  A periodic window is kept
+// unwrapped (t in (-M, 2M), image shift +L below 0, -L above M-1) when
+// M >= 2k + 3, so every candidate of a row sits at the same image; otherwise
+// the whole periodic row is searched with a per-candidate minimum image.
 struct Win {
     int lo, hi;
-    bool wrap;
+    bool full;   // whole periodic row: per-candidate minimum image
 };
 __device__ __forceinline__ Win window_1d(int g, int c, int s, int M, int k, bool wall) {
     Win w;
     w.lo = max(g - k, (c - 1) * s);
     w.hi = min(g + k, (c + 2) * s - 1);
+    w.full = false;
     if (wall) {
         w.lo = max(w.lo, 0);
         w.hi = min(w.hi, M - 1);
-        w.wrap = false;
-    } else if (w.hi - w.lo + 1 >= M) {
+    } else if (M < 2 * k + 3 || w.hi - w.lo + 1 >= M) {
         w.lo = 0;
         w.hi = M - 1;
-        w.wrap = false;
-    } else {
-        w.wrap = true;
+        w.full = true;
     }
     return w;
 }
-__device__ __forceinline__ int wrap_idx(int t, int M) {
-    t %= M;
-    return t < 0 ? t + M : t;
+
+// Scan every candidate range of one particle.  The (x row, y row, z part)
+// ranges are visited as one flat sequence per thread so that lanes with
+// short ranges move on instead of waiting for the longest range of the warp.
+template <typename T, int DIM, bool MINIMG>
+__device__ __forceinline__ void scan_ranges(const Bufs<T>& b, const GeoT<T>& G, const InstDev& I, const Win& wx,
+                                            const Win& wy, const int za[2], const int zb[2], const T zs[2],
+                                            int nz, const T xi[3], const T vi[3], T dt, T R2, T& bd,
+                                            uint32_t& bid, int32_t& bq, uint32_t& ncand) {
+    using V = typename Vec4<T>::type;
+    const uint32_t Mz = (DIM == 3) ? (uint32_t)I.M[2] : 1u;
+    const uint32_t My = (uint32_t)I.M[1];
+    const int Mx = I.M[0], Myi = I.M[1];
+    const uint32_t nmax = (uint32_t)b.n;
+    int tx = wx.lo, ty = wy.lo, zp = 0;
+    int32_t q = 0, qe = 0;
+    T sh[3] = {(T)0, (T)0, (T)0};
+    for (;;) {
+        if (q >= qe) {
+            bool more = false;
+            while (tx <= wx.hi) {
+                int gx = tx, gy = ty;
+                T sx = (T)0, sy = (T)0;
+                if (gx < 0) { gx += Mx; sx = G.L[0]; } else if (gx >= Mx) { gx -= Mx; sx = -G.L[0]; }
+                if (gy < 0) { gy += Myi; sy = G.L[1]; } else if (gy >= Myi) { gy -= Myi; sy = -G.L[1]; }
+                const uint32_t row = I.key_base + ((uint32_t)gx * My + (uint32_t)gy) * Mz;
+                // clamped so that a corrupted scan (flagged on the host) cannot read outside A
+                q = (int32_t)min(b.start[row + (uint32_t)za[zp]], nmax);
+                qe = (int32_t)min(b.start[row + (uint32_t)zb[zp] + 1u], nmax);
+                sh[0] = sx;
+                sh[1] = sy;
+                sh[2] = zs[zp];
+                if (++zp == nz) {
+                    zp = 0;
+                    if (++ty > wy.hi) { ty = wy.lo; ++tx; }
+                }
+                if (q < qe) { more = true; break; }
+            }
+            if (!more) break;
+            ncand += (uint32_t)(qe - q);
+        }
+        const V Pj = ldg_vec(b.posA + q);
+        const V Qj = ldg_vec(b.velA + q);
+        const T xj[3] = {Pj.x, Pj.y, Pj.z};
+        const T vj[3] = {Qj.x, Qj.y, Qj.z};
+        T d2;
+        // the particle itself has v_rel = 0 and fails b > 0
+        if (poca_test_sh<T, DIM, MINIMG>(G, xi, vi, xj, vj, sh, dt, R2, d2)) {
+            const uint32_t idj = R<T>::bits(Pj.w);
+            if (d2 < bd || (d2 == bd && idj < bid)) {
+                bd = d2;
+                bid = idj;
+                bq = q;
+            }
+        }
+        ++q;
+    }
 }
 
 // Closest candidate of every particle (criterion 3 over the 3^D c-bin
-// neighbourhood, restricted to search cells that can hold a candidate).
+// neighbourhood, restricted to the search cells that can hold a candidate).
 // One thread per particle in sorted order; candidates are read through L1.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads) search_kernel(Bufs<T> b) {
@@ -391,55 +524,37 @@ __global__ void __launch_bounds__(kThreads) search_kernel(Bufs<T> b) {
     int c[3] = {0, 0, 0}, g[3] = {0, 0, 0};
 #pragma unroll
     for (int d = 0; d < DIM; ++d) cell_and_search<T>(xi[d], G.lo[d], G.inv[d], G.n[d], I.s[d], c[d], g[d]);
-    Win wx = window_1d(g[0], c[0], I.s[0], I.M[0], kk[0], G.wall[0]);
-    Win wy = window_1d(g[1], c[1], I.s[1], I.M[1], kk[1], G.wall[1]);
-    Win wz = {0, 0, false};
-    if (DIM == 3) wz = window_1d(g[2], c[2], I.s[2], I.M[2], kk[2], G.wall[2]);
-    // z segments (z is the fastest key dimension, so a z window is 1 or 2 ranges)
-    int z0a = wz.lo, z1a = wz.hi, z0b = 1, z1b = 0;
-    if (DIM == 3 && wz.wrap) {
-        const int a0 = wrap_idx(wz.lo, I.M[2]), a1 = wrap_idx(wz.hi, I.M[2]);
-        if (a0 <= a1) { z0a = a0; z1a = a1; }
-        else { z0a = a0; z1a = I.M[2] - 1; z0b = 0; z1b = a1; }
+    const Win wx = window_1d(g[0], c[0], I.s[0], I.M[0], kk[0], G.wall[0]);
+    const Win wy = window_1d(g[1], c[1], I.s[1], I.M[1], kk[1], G.wall[1]);
+    // z is the fastest key dimension: its window is one or two key ranges
+    int za[2] = {0, 0}, zb[2] = {0, 0};
+    T zs[2] = {(T)0, (T)0};
+    int nz = 1;
+    bool full = wx.full || wy.full;
+    if (DIM == 3) {
+        const Win wz = window_1d(g[2], c[2], I.s[2], I.M[2], kk[2], G.wall[2]);
+        full = full || wz.full;
+        const int Mz = I.M[2];
+        if (wz.lo < 0) {
+            za[0] = wz.lo + Mz; zb[0] = Mz - 1; zs[0] = G.L[2];
+            za[1] = 0; zb[1] = wz.hi;
+            nz = 2;
+        } else if (wz.hi >= Mz) {
+            za[0] = wz.lo; zb[0] = Mz - 1;
+            za[1] = 0; zb[1] = wz.hi - Mz; zs[1] = -G.L[2];
+            nz = 2;
+        } else {
+            za[0] = wz.lo; zb[0] = wz.hi;
+        }
     }
-    const uint32_t Mz = (DIM == 3) ? (uint32_t)I.M[2] : 1u;
-    const uint32_t My = (uint32_t)I.M[1];
     T bd = R<T>::inf();
     uint32_t bid = 0xffffffffu;
     int32_t bq = -1;
     uint32_t ncand = 0;
-    for (int tx = wx.lo; tx <= wx.hi; ++tx) {
-        const int gx = wx.wrap ? wrap_idx(tx, I.M[0]) : tx;
-        for (int ty = wy.lo; ty <= wy.hi; ++ty) {
-            const int gy = wy.wrap ? wrap_idx(ty, I.M[1]) : ty;
-            const uint32_t row = I.key_base + ((uint32_t)gx * My + (uint32_t)gy) * Mz;
-            for (int seg = 0; seg < 2; ++seg) {
-                const int za = seg == 0 ? z0a : z0b;
-                const int zb = seg == 0 ? z1a : z1b;
-                if (za > zb) continue;
-                // clamped so that a corrupted scan (flagged on the host) cannot read outside A
-                const int32_t q0 = (int32_t)min(b.start[row + (uint32_t)za], (uint32_t)b.n);
-                const int32_t q1 = (int32_t)min(b.start[row + (uint32_t)zb + 1u], (uint32_t)b.n);
-                ncand += (uint32_t)(q1 - q0);
-                for (int32_t q = q0; q < q1; ++q) {
-                    if (q == (int32_t)p) continue;
-                    const V Pj = b.posA[q];
-                    const V Qj = b.velA[q];
-                    const T xj[3] = {Pj.x, Pj.y, Pj.z};
-                    const T vj[3] = {Qj.x, Qj.y, Qj.z};
-                    T d2;
-                    if (poca_test<T, DIM>(G, xi, vi, xj, vj, dt, R2, d2)) {
-                        const uint32_t idj = R<T>::bits(Pj.w);
-                        if (d2 < bd || (d2 == bd && idj < bid)) {
-                            bd = d2;
-                            bid = idj;
-                            bq = q;
-                        }
-                    }
-                }
-            }
-        }
-    }
+    if (full)
+        scan_ranges<T, DIM, true>(b, G, I, wx, wy, za, zb, zs, nz, xi, vi, dt, R2, bd, bid, bq, ncand);
+    else
+        scan_ranges<T, DIM, false>(b, G, I, wx, wy, za, zb, zs, nz, xi, vi, dt, R2, bd, bid, bq, ncand);
     b.best[p] = bq;
     if (b.record) atomicAdd(&b.st->candidates, (unsigned long long)(ncand > 0 ? ncand - 1 : 0));
 }
@@ -450,7 +565,11 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads) move_kernel(Bufs<T> b, int want_moments) {
     using V = typename Vec4<T>::type;
     __shared__ GeoT<T> G;
-    if (threadIdx.x == 0) G.load(b.geo);
+    __shared__ MomentSlots<T> S;
+    if (threadIdx.x == 0) {
+        G.load(b.geo);
+        S.n = 0;
+    }
     __syncthreads();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = p < b.n;
@@ -564,7 +683,7 @@ __global__ void __launch_bounds__(kThreads) move_kernel(Bufs<T> b, int want_mome
     }
     const T v2 = vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2];
     warp_vmax<T>(b.dyn, valid, inst, v2);
-    if (want_moments) warp_moments<T>(b.acc, valid, bin, vn, W, paired);
+    if (want_moments) block_moments<T>(S, b.acc, valid, bin, vn, W, paired);
 }
 
 // Counting-sort scatter B -> A in search-key order.
@@ -619,7 +738,11 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads) state_moments_kernel(Bufs<T> b) {
     using V = typename Vec4<T>::type;
     __shared__ GeoT<T> G;
-    if (threadIdx.x == 0) G.load(b.geo);
+    __shared__ MomentSlots<T> S;
+    if (threadIdx.x == 0) {
+        G.load(b.geo);
+        S.n = 0;
+    }
     __syncthreads();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = p < b.n;
@@ -635,7 +758,7 @@ __global__ void __launch_bounds__(kThreads) state_moments_kernel(Bufs<T> b) {
     const T v[3] = {Q.x, Q.y, Q.z};
     uint32_t skey = 0, bin = 0;
     keys_of<T, DIM>(G, I, x, skey, bin);
-    warp_moments<T>(b.acc, valid, bin, v, (T)0, false);
+    block_moments<T>(S, b.acc, valid, bin, v, (T)0, false);
 }
 
 // Particles per c-bin and largest |v|^2 per instance of the packed state in B
@@ -648,17 +771,34 @@ __global__ void __launch_bounds__(kThreads) cbin_hist_kernel(Bufs<T> b, uint32_t
     if (threadIdx.x == 0) G.load(b.geo);
     __syncthreads();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= b.n) return;
-    const V P = b.posB[p];
-    const V Q = b.velB[p];
-    const int inst = (int)R<T>::bits(Q.w);
-    const InstDev& I = b.inst[inst];
+    const bool valid = p < b.n;
+    V P = {}, Q = {};
+    int inst = 0;
+    if (valid) {
+        P = b.posB[p];
+        Q = b.velB[p];
+        inst = (int)R<T>::bits(Q.w);
+    }
+    const InstDev I = b.inst[inst];
     const T x[3] = {P.x, P.y, P.z};
-    uint32_t skey, bin;
+    uint32_t skey = 0, bin = 0;
     keys_of<T, DIM>(G, I, x, skey, bin);
-    atomicAdd(hist + bin, 1u);
+    const unsigned active = __ballot_sync(kFull, valid);
+    if (valid) {
+        const unsigned peers = __match_any_sync(active, bin);
+        if ((int)lane_id() == __ffs(peers) - 1) atomicAdd(hist + bin, (uint32_t)__popc(peers));
+    }
     const double v2 = (double)Q.x * Q.x + (double)Q.y * Q.y + (double)Q.z * Q.z;
-    atomicMax(vmax2 + inst, (unsigned long long)__double_as_longlong(v2));
+    double m = valid ? v2 : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
+    const int inst0 = __shfl_sync(kFull, inst, 0);
+    const bool same = __all_sync(kFull, !valid || inst == inst0);
+    if (same) {
+        if (lane_id() == 0 && valid) atomicMax(vmax2 + inst0, (unsigned long long)__double_as_longlong(m));
+    } else if (valid) {
+        atomicMax(vmax2 + inst, (unsigned long long)__double_as_longlong(v2));
+    }
 }
 
 // ------------------------------------------------------------- launchers
