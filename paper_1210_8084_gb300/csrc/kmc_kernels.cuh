@@ -421,25 +421,30 @@ __device__ __forceinline__ bool poca_test_sh(const GeoT<T>& G, const T xi[3], co
 
 // Search window of one dimension in search-cell coordinates: within k cells of
 // g and inside the c-bins c-1 .. c+1; cut at walls.  A periodic window is kept
-// unwrapped (t in (-M, 2M), image shift +L below 0, -L above M-1) when
-// M >= 2k + 3, so every candidate of a row sits at the same image; otherwise
-// the whole periodic row is searched with a per-candidate minimum image.
+// unwrapped (t in (-M, 2M); image shift +L below 0, -L above M-1).  When every
+// cell of the window lies less than half a box (minus half a cell) from the
+// particle's cell, all candidates of a row share one image and the shift is
+// exact; otherwise (`amb`) the candidates take the per-candidate minimum image,
+// and a window as wide as the row becomes the row itself.
 struct Win {
     int lo, hi;
-    bool full;   // whole periodic row: per-candidate minimum image
+    bool amb;   // per-candidate minimum image needed
 };
 __device__ __forceinline__ Win window_1d(int g, int c, int s, int M, int k, bool wall) {
     Win w;
     w.lo = max(g - k, (c - 1) * s);
     w.hi = min(g + k, (c + 2) * s - 1);
-    w.full = false;
+    w.amb = false;
     if (wall) {
         w.lo = max(w.lo, 0);
         w.hi = min(w.hi, M - 1);
-    } else if (M < 2 * k + 3 || w.hi - w.lo + 1 >= M) {
+    } else if (w.hi - w.lo + 1 >= M) {
         w.lo = 0;
         w.hi = M - 1;
-        w.full = true;
+        w.amb = true;
+    } else {
+        const int m = max(g - w.lo, w.hi - g) + 1;
+        w.amb = 2 * m + 1 > M;
     }
     return w;
 }
@@ -530,10 +535,10 @@ __global__ void __launch_bounds__(kThreads) search_kernel(Bufs<T> b) {
     int za[2] = {0, 0}, zb[2] = {0, 0};
     T zs[2] = {(T)0, (T)0};
     int nz = 1;
-    bool full = wx.full || wy.full;
+    bool amb = wx.amb || wy.amb;
     if (DIM == 3) {
         const Win wz = window_1d(g[2], c[2], I.s[2], I.M[2], kk[2], G.wall[2]);
-        full = full || wz.full;
+        amb = amb || wz.amb;
         const int Mz = I.M[2];
         if (wz.lo < 0) {
             za[0] = wz.lo + Mz; zb[0] = Mz - 1; zs[0] = G.L[2];
@@ -551,7 +556,7 @@ __global__ void __launch_bounds__(kThreads) search_kernel(Bufs<T> b) {
     uint32_t bid = 0xffffffffu;
     int32_t bq = -1;
     uint32_t ncand = 0;
-    if (full)
+    if (amb)
         scan_ranges<T, DIM, true>(b, G, I, wx, wy, za, zb, zs, nz, xi, vi, dt, R2, bd, bid, bq, ncand);
     else
         scan_ranges<T, DIM, false>(b, G, I, wx, wy, za, zb, zs, nz, xi, vi, dt, R2, bd, bid, bq, ncand);
