@@ -385,6 +385,8 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
         const double sigma = insts[i].sigma > 0 ? insts[i].sigma : 1.0 / (insts[i].lambda * nbar);
         I.R2 = I.n > 0 ? sigma / M_PI : 0.0;
         I.dt = insts[i].dt;
+        I.R2f = (float)I.R2;
+        I.dtf = (float)I.dt;
         I.seed_lo = (uint32_t)(insts[i].seed & 0xffffffffu);
         I.seed_hi = (uint32_t)(insts[i].seed >> 32);
         for (int d = 0; d < 3; ++d) {

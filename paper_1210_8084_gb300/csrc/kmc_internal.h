@@ -35,6 +35,7 @@ struct InstDev {
     int M[3];            // search cells per dimension = n_cells * s
     double R2;           // squared contact distance
     double dt;           // timestep
+    float R2f, dtf;      // the same rounded to binary32 (binary32 kernels use these)
     uint32_t seed_lo, seed_hi;
     double w[3];         // search-cell width per dimension
 };

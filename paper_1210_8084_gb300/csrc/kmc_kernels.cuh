@@ -55,6 +55,13 @@ struct R<double> {
     static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000LL); }
 };
 
+// Per-instance timestep and squared contact distance in the state precision
+// (binary32 copies are rounded once on the host, as the oracle rounds them).
+__device__ __forceinline__ float inst_dt(const InstDev& I, float) { return I.dtf; }
+__device__ __forceinline__ double inst_dt(const InstDev& I, double) { return I.dt; }
+__device__ __forceinline__ float inst_R2(const InstDev& I, float) { return I.R2f; }
+__device__ __forceinline__ double inst_R2(const InstDev& I, double) { return I.R2; }
+
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32 multiplies with
 // the published multipliers; the key advances by the Weyl increments.
@@ -182,25 +189,42 @@ __device__ __forceinline__ uint32_t aggregated_increment(uint32_t* count, uint32
     return base + (uint32_t)__popc(peers & lt);
 }
 
-// Largest |v|^2 per instance: warp maximum, then one atomicMax per warp and
-// instance, skipped when it cannot raise the stored value.
+// Largest |v|^2 per instance: a warp maximum on the bit patterns (non-negative
+// floats order like their bits, so the reduction is integer work), then one
+// atomicMax per warp on the binary64 bits, skipped when it cannot raise the
+// stored value.  A warp that straddles two instances falls back to one atomic
+// per lane.
+__device__ __forceinline__ unsigned long long vmax_bits(float v2) {
+    return (unsigned long long)__double_as_longlong((double)v2);
+}
+__device__ __forceinline__ unsigned long long vmax_bits(double v2) {
+    return (unsigned long long)__double_as_longlong(v2);
+}
+__device__ __forceinline__ unsigned long long warp_max_bits(float v2, bool valid) {
+    const unsigned m = __reduce_max_sync(kFull, valid ? __float_as_uint(v2) : 0u);
+    return vmax_bits(__uint_as_float(m));
+}
+__device__ __forceinline__ unsigned long long warp_max_bits(double v2, bool valid) {
+    unsigned long long m = valid ? (unsigned long long)__double_as_longlong(v2) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(kFull, m, o);
+        m = y > m ? y : m;
+    }
+    return m;
+}
+
 template <typename T>
 __device__ __forceinline__ void warp_vmax(InstDyn* dyn, bool valid, int inst, T v2) {
-    unsigned todo = __ballot_sync(kFull, valid);
-    while (todo) {
-        const int leader = __ffs(todo) - 1;
-        const int gi = __shfl_sync(kFull, inst, leader);
-        const bool mine = valid && inst == gi;
-        const unsigned grp = __ballot_sync(kFull, mine);
-        double m = mine ? (double)v2 : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
-        if ((int)lane_id() == leader) {
-            const unsigned long long bitsm = (unsigned long long)__double_as_longlong(m);
-            unsigned long long* dst = &dyn[gi].vmax2_next;
-            if (bitsm > *((volatile unsigned long long*)dst)) atomicMax(dst, bitsm);
+    const int inst0 = __shfl_sync(kFull, inst, 0);
+    if (__all_sync(kFull, !valid || inst == inst0)) {
+        const unsigned long long m = warp_max_bits(v2, valid);
+        if (lane_id() == 0) {
+            unsigned long long* dst = &dyn[inst0].vmax2_next;
+            if (m > *((volatile unsigned long long*)dst)) atomicMax(dst, m);
         }
-        todo &= ~grp;
+    } else if (valid) {
+        atomicMax(&dyn[inst].vmax2_next, vmax_bits(v2));
     }
 }
 
@@ -449,48 +473,23 @@ __device__ __forceinline__ Win window_1d(int g, int c, int s, int M, int k, bool
     return w;
 }
 
-// Scan every candidate range of one particle.  The (x row, y row, z part)
-// ranges are visited as one flat sequence per thread so that lanes with
-// short ranges move on instead of waiting for the longest range of the warp.
+// Test the candidates [q, qe) of one range and keep the closest (smaller d2,
+// ties to the lower id).  The next candidate is loaded before the current one
+// is tested.
 template <typename T, int DIM, bool MINIMG>
-__device__ __forceinline__ void scan_ranges(const Bufs<T>& b, const GeoT<T>& G, const InstDev& I, const Win& wx,
-                                            const Win& wy, const int za[2], const int zb[2], const T zs[2],
-                                            int nz, const T xi[3], const T vi[3], T dt, T R2, T& bd,
-                                            uint32_t& bid, int32_t& bq, uint32_t& ncand) {
+__device__ __forceinline__ void scan_range(const Bufs<T>& b, const GeoT<T>& G, int32_t q, int32_t qe,
+                                           const T sh[3], const T xi[3], const T vi[3], T dt, T R2, T& bd,
+                                           uint32_t& bid, int32_t& bq) {
     using V = typename Vec4<T>::type;
-    const uint32_t Mz = (DIM == 3) ? (uint32_t)I.M[2] : 1u;
-    const uint32_t My = (uint32_t)I.M[1];
-    const int Mx = I.M[0], Myi = I.M[1];
-    const uint32_t nmax = (uint32_t)b.n;
-    int tx = wx.lo, ty = wy.lo, zp = 0;
-    int32_t q = 0, qe = 0;
-    T sh[3] = {(T)0, (T)0, (T)0};
-    for (;;) {
-        if (q >= qe) {
-            bool more = false;
-            while (tx <= wx.hi) {
-                int gx = tx, gy = ty;
-                T sx = (T)0, sy = (T)0;
-                if (gx < 0) { gx += Mx; sx = G.L[0]; } else if (gx >= Mx) { gx -= Mx; sx = -G.L[0]; }
-                if (gy < 0) { gy += Myi; sy = G.L[1]; } else if (gy >= Myi) { gy -= Myi; sy = -G.L[1]; }
-                const uint32_t row = I.key_base + ((uint32_t)gx * My + (uint32_t)gy) * Mz;
-                // clamped so that a corrupted scan (flagged on the host) cannot read outside A
-                q = (int32_t)min(b.start[row + (uint32_t)za[zp]], nmax);
-                qe = (int32_t)min(b.start[row + (uint32_t)zb[zp] + 1u], nmax);
-                sh[0] = sx;
-                sh[1] = sy;
-                sh[2] = zs[zp];
-                if (++zp == nz) {
-                    zp = 0;
-                    if (++ty > wy.hi) { ty = wy.lo; ++tx; }
-                }
-                if (q < qe) { more = true; break; }
-            }
-            if (!more) break;
-            ncand += (uint32_t)(qe - q);
+    if (q >= qe) return;
+    V Pn = ldg_vec(b.posA + q);
+    V Qn = ldg_vec(b.velA + q);
+    for (; q < qe; ++q) {
+        const V Pj = Pn, Qj = Qn;
+        if (q + 1 < qe) {
+            Pn = ldg_vec(b.posA + q + 1);
+            Qn = ldg_vec(b.velA + q + 1);
         }
-        const V Pj = ldg_vec(b.posA + q);
-        const V Qj = ldg_vec(b.velA + q);
         const T xj[3] = {Pj.x, Pj.y, Pj.z};
         const T vj[3] = {Qj.x, Qj.y, Qj.z};
         T d2;
@@ -503,7 +502,103 @@ __device__ __forceinline__ void scan_ranges(const Bufs<T>& b, const GeoT<T>& G, 
                 bq = q;
             }
         }
-        ++q;
+    }
+}
+
+// Unwrapped window index -> (cell, image shift) of a periodic or walled dimension.
+template <typename T>
+__device__ __forceinline__ int unwrap(int t, int M, T L, T& shift) {
+    shift = (T)0;
+    if (t < 0) { shift = L; return t + M; }
+    if (t >= M) { shift = -L; return t - M; }
+    return t;
+}
+
+// Every candidate range of one particle.  The last position dimension is the
+// fastest of the key, so a window is a set of rows (x, or x and y) each with
+// one or two contiguous key ranges.  Common case (at most 3 cells per row
+// dimension, one range per row): all row ranges are fetched first so their
+// loads overlap, then the rows are scanned in turn.  Otherwise rows are
+// visited one at a time.
+template <typename T, int DIM, bool MINIMG>
+__device__ __forceinline__ void scan_window(const Bufs<T>& b, const GeoT<T>& G, const InstDev& I, const Win w[3],
+                                            const T xi[3], const T vi[3], T dt, T R2, T& bd, uint32_t& bid,
+                                            int32_t& bq) {
+    constexpr int F = DIM - 1;   // fast (contiguous) dimension
+    const int MF = I.M[F];
+    const uint32_t nmax = (uint32_t)b.n;
+    // fast-dimension parts: unwrapped window -> 1 or 2 key ranges with shifts
+    int fa[2], fb[2];
+    T fs[2] = {(T)0, (T)0};
+    int nf = 1;
+    if (w[F].lo < 0) {
+        fa[0] = w[F].lo + MF; fb[0] = MF - 1; fs[0] = G.L[F];
+        fa[1] = 0; fb[1] = w[F].hi;
+        nf = 2;
+    } else if (w[F].hi >= MF) {
+        fa[0] = w[F].lo; fb[0] = MF - 1;
+        fa[1] = 0; fb[1] = w[F].hi - MF; fs[1] = -G.L[F];
+        nf = 2;
+    } else {
+        fa[0] = w[F].lo; fb[0] = w[F].hi;
+    }
+    const int nx = w[0].hi - w[0].lo + 1;
+    const int ny = (DIM == 3) ? w[1].hi - w[1].lo + 1 : 1;
+    const uint32_t My = (DIM == 3) ? (uint32_t)I.M[1] : 1u;
+    const uint32_t Mf = (uint32_t)MF;
+    if (nf == 1 && nx <= 3 && ny <= 3) {
+        constexpr int NR = (DIM == 3) ? 9 : 3;
+        int32_t q0[NR], q1[NR];
+        T sx[3], sy[3];
+        int gxs[3], gys[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            gxs[i] = unwrap<T>(w[0].lo + i, I.M[0], G.L[0], sx[i]);
+            gys[i] = (DIM == 3) ? unwrap<T>(w[1].lo + i, I.M[1], G.L[1], sy[i]) : 0;
+            if (DIM != 3) sy[i] = (T)0;
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int ix = (DIM == 3) ? r / 3 : r;
+            const int iy = (DIM == 3) ? r % 3 : 0;
+            q0[r] = 0;
+            q1[r] = 0;
+            if (ix < nx && iy < ny) {
+                const uint32_t row = I.key_base + ((uint32_t)gxs[ix] * My + (uint32_t)gys[iy]) * Mf;
+                // clamped so that a corrupted scan (flagged on the host) cannot read outside A
+                q0[r] = (int32_t)min(b.start[row + (uint32_t)fa[0]], nmax);
+                q1[r] = (int32_t)min(b.start[row + (uint32_t)fb[0] + 1u], nmax);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int ix = (DIM == 3) ? r / 3 : r;
+            const int iy = (DIM == 3) ? r % 3 : 0;
+            T sh[3];
+            sh[0] = sx[ix];
+            sh[1] = (DIM == 3) ? sy[iy] : fs[0];
+            sh[2] = fs[0];
+            scan_range<T, DIM, MINIMG>(b, G, q0[r], q1[r], sh, xi, vi, dt, R2, bd, bid, bq);
+        }
+        return;
+    }
+    for (int tx = w[0].lo; tx <= w[0].hi; ++tx) {
+        T sx;
+        const int gx = unwrap<T>(tx, I.M[0], G.L[0], sx);
+        for (int ty = (DIM == 3 ? w[1].lo : 0); ty <= (DIM == 3 ? w[1].hi : 0); ++ty) {
+            T sy = (T)0;
+            const int gy = (DIM == 3) ? unwrap<T>(ty, I.M[1], G.L[1], sy) : 0;
+            const uint32_t row = I.key_base + ((uint32_t)gx * My + (uint32_t)gy) * Mf;
+            for (int part = 0; part < nf; ++part) {
+                const int32_t q = (int32_t)min(b.start[row + (uint32_t)fa[part]], nmax);
+                const int32_t qe = (int32_t)min(b.start[row + (uint32_t)fb[part] + 1u], nmax);
+                T sh[3];
+                sh[0] = sx;
+                sh[1] = (DIM == 3) ? sy : fs[part];
+                sh[2] = fs[part];
+                scan_range<T, DIM, MINIMG>(b, G, q, qe, sh, xi, vi, dt, R2, bd, bid, bq);
+            }
+        }
     }
 }
 
@@ -525,43 +620,23 @@ __global__ void __launch_bounds__(kThreads) search_kernel(Bufs<T> b) {
     const int* kk = b.dyn[inst].k;
     const T xi[3] = {P.x, P.y, P.z};
     const T vi[3] = {Q.x, Q.y, Q.z};
-    const T dt = (T)I.dt, R2 = (T)I.R2;
+    const T dt = inst_dt(I, T()), R2 = inst_R2(I, T());
     int c[3] = {0, 0, 0}, g[3] = {0, 0, 0};
 #pragma unroll
     for (int d = 0; d < DIM; ++d) cell_and_search<T>(xi[d], G.lo[d], G.inv[d], G.n[d], I.s[d], c[d], g[d]);
-    const Win wx = window_1d(g[0], c[0], I.s[0], I.M[0], kk[0], G.wall[0]);
-    const Win wy = window_1d(g[1], c[1], I.s[1], I.M[1], kk[1], G.wall[1]);
-    // z is the fastest key dimension: its window is one or two key ranges
-    int za[2] = {0, 0}, zb[2] = {0, 0};
-    T zs[2] = {(T)0, (T)0};
-    int nz = 1;
-    bool amb = wx.amb || wy.amb;
-    if (DIM == 3) {
-        const Win wz = window_1d(g[2], c[2], I.s[2], I.M[2], kk[2], G.wall[2]);
-        amb = amb || wz.amb;
-        const int Mz = I.M[2];
-        if (wz.lo < 0) {
-            za[0] = wz.lo + Mz; zb[0] = Mz - 1; zs[0] = G.L[2];
-            za[1] = 0; zb[1] = wz.hi;
-            nz = 2;
-        } else if (wz.hi >= Mz) {
-            za[0] = wz.lo; zb[0] = Mz - 1;
-            za[1] = 0; zb[1] = wz.hi - Mz; zs[1] = -G.L[2];
-            nz = 2;
-        } else {
-            za[0] = wz.lo; zb[0] = wz.hi;
-        }
+    Win w[3];
+    bool amb = false;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        w[d] = window_1d(g[d], c[d], I.s[d], I.M[d], kk[d], G.wall[d]);
+        amb = amb || w[d].amb;
     }
     T bd = R<T>::inf();
     uint32_t bid = 0xffffffffu;
     int32_t bq = -1;
-    uint32_t ncand = 0;
-    if (amb)
-        scan_ranges<T, DIM, true>(b, G, I, wx, wy, za, zb, zs, nz, xi, vi, dt, R2, bd, bid, bq, ncand);
-    else
-        scan_ranges<T, DIM, false>(b, G, I, wx, wy, za, zb, zs, nz, xi, vi, dt, R2, bd, bid, bq, ncand);
+    if (amb) scan_window<T, DIM, true>(b, G, I, w, xi, vi, dt, R2, bd, bid, bq);
+    else scan_window<T, DIM, false>(b, G, I, w, xi, vi, dt, R2, bd, bid, bq);
     b.best[p] = bq;
-    if (b.record) atomicAdd(&b.st->candidates, (unsigned long long)(ncand > 0 ? ncand - 1 : 0));
 }
 
 // Unambiguous pairs, CM-frame scattering, split free flight, walls, then the
@@ -591,7 +666,7 @@ __global__ void __launch_bounds__(kThreads) move_kernel(Bufs<T> b, int want_mome
     const uint32_t id = R<T>::bits(P.w);
     const T x[3] = {P.x, P.y, P.z};
     const T v[3] = {Q.x, Q.y, Q.z};
-    const T dt = (T)I.dt;
+    const T dt = inst_dt(I, T());
     T xn[3] = {x[0], x[1], x[2]}, vn[3] = {v[0], v[1], v[2]};
     T W = (T)0;
     bool paired = false;
