@@ -101,8 +101,10 @@ def algorithmic_bytes(n, n_keys, n_bins, frac_paired, phase):
     State of a particle: position 12 B + id 4 B, velocity 12 B + instance 4 B."""
     if phase == "search":
         return n * (32 + 4)                    # read own state once, write closest candidate
-    if phase == "move":
-        return n * (32 + 4 + 4 + 32 + 4 + 4) + n * frac_paired * 32 + n * 4 + n_bins * 72 * 2
+    if phase == "move":                        # own state, best, partner best, B, key, slot, histogram
+        return n * (32 + 4 + 4 + 32 + 4 + 4 + 4) + n * frac_paired * 32
+    if phase == "moments":                     # read A once, bin sums
+        return n * 32 + n_bins * 72 * 2
     if phase == "scan":
         return n_keys * (4 + 4 + 4)            # read count, write start, clear count
     if phase == "scatter":
@@ -200,8 +202,8 @@ def ours(args):
 
     # ---------------- roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
-    phases = {p: prof[p] / args.steps for p in ("search", "move", "scan", "scatter", "finalize", "clear")}
-    dom = max(("search", "move", "scan", "scatter"), key=lambda p: phases[p])
+    phases = {p: prof[p] / args.steps for p in ("search", "move", "scan", "scatter", "moments", "finalize")}
+    dom = max(("search", "move", "scan", "scatter", "moments"), key=lambda p: phases[p])
     ab = algorithmic_bytes(n, info.n_search_cells, info.n_bins, frac_paired, dom)
     achieved = ab / (phases[dom] * 1e-3) / 1e9
     peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -224,7 +226,7 @@ def ours(args):
         "collision_fraction": round(frac_paired, 4),
         "roofline": roof,
         "e2e": e2e,
-        "gpu_launches": 6 * args.steps,
+        "gpu_launches": 7 * args.steps,
         "clocks": clk,
     }
     if not args.no_cpu_baseline and world == 1:

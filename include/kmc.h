@@ -129,11 +129,11 @@ KMC_API int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const vo
 KMC_API int kmc_step(kmc_handle* h, int nsteps, int want_moments);
 
 /* Phases of one step, in launch order, for kmc_step_profiled. */
-#define KMC_PHASE_CLEAR 0    /* zero the moment accumulators (want_moments only) */
-#define KMC_PHASE_SEARCH 1   /* closest candidate per particle (criteria 1-3) */
-#define KMC_PHASE_MOVE 2     /* pairs, scattering, free flight, walls, next key, moment sums */
-#define KMC_PHASE_SCAN 3     /* exclusive scan of the key histogram */
-#define KMC_PHASE_SCATTER 4  /* counting-sort scatter into key order */
+#define KMC_PHASE_SEARCH 0   /* closest candidate per particle (criteria 1-3) */
+#define KMC_PHASE_MOVE 1     /* pairs, scattering, free flight, walls, next key and histogram */
+#define KMC_PHASE_SCAN 2     /* exclusive scan of the key histogram */
+#define KMC_PHASE_SCATTER 3  /* counting-sort scatter into key order */
+#define KMC_PHASE_MOMENTS 4  /* per-c-bin moment sums of the new state (want_moments only) */
 #define KMC_PHASE_FINALIZE 5 /* derived moments and per-instance totals (want_moments only) */
 #define KMC_NPHASES 6
 

@@ -34,7 +34,7 @@ KMC_MOM_RAW = 1
 KMC_MOM_DERIVED = 2
 KMC_MOM_GLOBAL = 4
 KMC_NPHASES = 6
-PHASES = ("clear", "search", "move", "scan", "scatter", "finalize")
+PHASES = ("search", "move", "scan", "scatter", "moments", "finalize")
 
 ABI_FUNCTIONS = (
     "kmc_init", "kmc_step", "kmc_moments", "kmc_moments_size", "kmc_free", "kmc_sync",

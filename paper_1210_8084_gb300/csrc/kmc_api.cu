@@ -47,6 +47,7 @@ struct kmc_handle {
     double *acc = nullptr, *mom = nullptr, *glob = nullptr;
     int32_t *rec_best = nullptr, *rec_partner = nullptr;
     uint32_t n_keys = 0, n_tiles = 0;
+    uint32_t id_bits = 32;
     int64_t n_bins = 0, bins_per_inst = 0;
     int64_t bytes = 0;
     int mom_state = 0;  // 1: acc/mom/glob describe the current state
@@ -118,6 +119,8 @@ Bufs<T> make_bufs(const kmc_handle* h) {
     b.rec_best = h->rec_best;
     b.rec_partner = h->rec_partner;
     b.record = (h->cfg.flags & KMC_FLAG_RECORD) ? 1 : 0;
+    b.id_bits = h->id_bits;
+    b.id_mask = h->id_bits >= 32 ? 0xffffffffu : ((1u << h->id_bits) - 1u);
     return b;
 }
 
@@ -129,21 +132,22 @@ cudaError_t enqueue_step(kmc_handle* h, int want_moments, cudaEvent_t* ev = null
     cudaStream_t s = h->stream;
     cudaError_t e;
     auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], s) : cudaSuccess; };
-    if ((e = mark(KMC_PHASE_CLEAR)) != cudaSuccess) return e;
-    if (want_moments) {
-        e = cudaMemsetAsync(h->acc, 0, sizeof(double) * kAccFields * (size_t)h->n_bins, s);
-        if (e != cudaSuccess) return e;
-    }
     if ((e = mark(KMC_PHASE_SEARCH)) != cudaSuccess) return e;
     if ((e = launch_search<T>(b, s)) != cudaSuccess) return e;
     if ((e = mark(KMC_PHASE_MOVE)) != cudaSuccess) return e;
-    if ((e = launch_move<T>(b, want_moments, s)) != cudaSuccess) return e;
+    if ((e = launch_move<T>(b, s)) != cudaSuccess) return e;
     if ((e = mark(KMC_PHASE_SCAN)) != cudaSuccess) return e;
     if ((e = launch_scan(h->count, h->start, h->n_keys, h->n_tiles, h->scan_status, h->dyn_d, h->inst_d,
                          h->n_inst, h->st_d, h->geo, 1, s)) != cudaSuccess)
         return e;
     if ((e = mark(KMC_PHASE_SCATTER)) != cudaSuccess) return e;
     if ((e = launch_scatter<T>(b, s)) != cudaSuccess) return e;
+    if ((e = mark(KMC_PHASE_MOMENTS)) != cudaSuccess) return e;
+    if (want_moments) {
+        e = cudaMemsetAsync(h->acc, 0, sizeof(double) * kAccFields * (size_t)h->n_bins, s);
+        if (e != cudaSuccess) return e;
+        if ((e = launch_moments<T>(b, 1, s)) != cudaSuccess) return e;
+    }
     if ((e = mark(KMC_PHASE_FINALIZE)) != cudaSuccess) return e;
     if (want_moments) {
         if ((e = launch_finalize(h->inst_d, h->n_inst, h->geo, h->acc, h->mom, h->glob, h->n_bins, s)) !=
@@ -372,6 +376,18 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
     }
     double V = 1.0;
     for (int d = 0; d < h->dim; ++d) V *= g.L[d];
+    // particle tag: instance index above the local id
+    {
+        uint32_t inst_bits = 0;
+        while ((1ll << inst_bits) < (long long)h->n_inst) ++inst_bits;
+        h->id_bits = 32 - inst_bits;
+        int64_t nmax = 0;
+        for (auto& I : insts) nmax = std::max(nmax, I.n_particles);
+        if (inst_bits > 0 && nmax > (int64_t)(1ll << h->id_bits)) {
+            delete h;
+            return fail(nullptr, KMC_ERANGE, "instance too large for the particle tag: fewer instances or particles");
+        }
+    }
 
     int64_t off = 0;
     for (int i = 0; i < h->n_inst; ++i) {
@@ -605,8 +621,8 @@ int kmc_moments(kmc_handle* h, double* out, int where, int mask) {
     if (mask & ~(KMC_MOM_RAW | KMC_MOM_DERIVED | KMC_MOM_GLOBAL)) return fail(h, KMC_EINVAL, "bad fields_mask");
     if (!h->mom_state) {
         KMC_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(double) * kAccFields * (size_t)h->n_bins, h->stream));
-        cudaError_t e = h->precision == 64 ? launch_moments_state<double>(make_bufs<double>(h), h->stream)
-                                           : launch_moments_state<float>(make_bufs<float>(h), h->stream);
+        cudaError_t e = h->precision == 64 ? launch_moments<double>(make_bufs<double>(h), 0, h->stream)
+                                           : launch_moments<float>(make_bufs<float>(h), 0, h->stream);
         KMC_CUDA(h, e);
         KMC_CUDA(h, launch_finalize(h->inst_d, h->n_inst, h->geo, h->acc, h->mom, h->glob, h->n_bins, h->stream));
         h->mom_state = 1;

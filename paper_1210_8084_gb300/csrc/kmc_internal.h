@@ -24,6 +24,8 @@ constexpr int kAccFields = 9;          // per c-bin accumulator: 8 moment sums +
 constexpr uint32_t kErrScanTimeout = 1u;
 constexpr uint32_t kErrKeyRange = 2u;
 
+constexpr int kMomItems = 4;           // moments: consecutive particles per thread
+
 // Per-instance constants.  Geometry (box, c-bins, walls) is shared; the search
 // grid subdivision s[] and the interaction constants are per instance.
 struct InstDev {
@@ -103,6 +105,9 @@ struct Bufs {
     int32_t* rec_best;       // RECORD: [n] by global id
     int32_t* rec_partner;    // RECORD: [n] by global id
     int record;
+    // particle tag = (instance << id_bits) | instance-local id
+    uint32_t id_bits;        // 32 when there is one instance
+    uint32_t id_mask;
 };
 
 // Launchers (defined in kmc_kernels.cuh, instantiated per precision).
@@ -113,7 +118,7 @@ cudaError_t launch_bin_init(const Bufs<T>& b, cudaStream_t s);
 template <typename T>
 cudaError_t launch_search(const Bufs<T>& b, cudaStream_t s);
 template <typename T>
-cudaError_t launch_move(const Bufs<T>& b, int want_moments, cudaStream_t s);
+cudaError_t launch_move(const Bufs<T>& b, cudaStream_t s);
 template <typename T>
 cudaError_t launch_scatter(const Bufs<T>& b, cudaStream_t s);
 template <typename T>
@@ -121,7 +126,7 @@ cudaError_t launch_gather_state(const Bufs<T>& b, T* pos3, T* vel3, cudaStream_t
 template <typename T>
 cudaError_t launch_cell_keys(const Bufs<T>& b, int32_t* keys, cudaStream_t s);
 template <typename T>
-cudaError_t launch_moments_state(const Bufs<T>& b, cudaStream_t s);
+cudaError_t launch_moments(const Bufs<T>& b, int use_virial, cudaStream_t s);
 template <typename T>
 cudaError_t launch_cbin_hist(const Bufs<T>& b, uint32_t* hist, unsigned long long* vmax2, cudaStream_t s);
 

@@ -9,7 +9,9 @@
 //   scatter : counting-sort scatter into search-key order
 //
 // Layout: SoA of 16-byte (binary32) or 32-byte (binary64) vectors,
-//   pos = (x, y, z, id bits), vel = (vx, vy, vz, instance bits),
+//   pos = (x, y, z, tag bits), vel = (vx, vy, vz, W),
+// tag = (instance << id_bits) | instance-local id, W = collisional virial of the
+// particle's last step (+inf when it did not collide),
 // sorted by search key = key_base + (gx * My + gy) * Mz + gz where g is the
 // search cell (a c-bin subdivided s_d times per dimension, x slowest).
 #pragma once
@@ -172,6 +174,16 @@ __device__ __forceinline__ int instance_of(const InstDev* inst, int n_inst, int6
     return lo;
 }
 
+// Instance and local id of a particle tag.
+template <typename T>
+__device__ __forceinline__ int tag_inst(const Bufs<T>& b, uint32_t tag) {
+    return b.id_bits >= 32u ? 0 : (int)(tag >> b.id_bits);
+}
+template <typename T>
+__device__ __forceinline__ uint32_t tag_id(const Bufs<T>& b, uint32_t tag) {
+    return tag & b.id_mask;
+}
+
 // ------------------------------------------------------------ warp helpers
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -232,7 +244,8 @@ __device__ __forceinline__ void warp_vmax(InstDyn* dyn, bool valid, int inst, T 
 // atomics reach any one bin: lanes with the same bin are reduced with warp
 // shuffles; each warp group's totals go to a shared-memory slot list; after a
 // block barrier the first slot of every distinct bin adds up its duplicates and
-// issues the global atomics.  All threads of the block must call this.
+// issues the global atomics.  All threads of the block must call this; a lane
+// contributes its partial sums (v, v^2, W), particle count and collided count.
 template <typename T>
 struct MomentSlots {
     uint32_t bin[kThreads];
@@ -243,35 +256,34 @@ struct MomentSlots {
 };
 
 template <typename T>
-__device__ __forceinline__ void block_moments(MomentSlots<T>& S, double* acc, bool valid, uint32_t bin,
-                                              const T v[3], T W, bool collided) {
+__device__ __forceinline__ void block_moment_partials(MomentSlots<T>& S, double* acc, bool valid, uint32_t bin,
+                                                      const T fl[7], int cnt_l, int coll_l) {
     unsigned todo = __ballot_sync(kFull, valid);
-    const unsigned coll = __ballot_sync(kFull, valid && collided);
     while (todo) {
         const int leader = __ffs(todo) - 1;
         const uint32_t gb = __shfl_sync(kFull, bin, leader);
         const bool mine = valid && bin == gb;
         const unsigned grp = __ballot_sync(kFull, mine);
         T f[7];
-        f[0] = mine ? v[0] : (T)0;
-        f[1] = mine ? v[1] : (T)0;
-        f[2] = mine ? v[2] : (T)0;
-        f[3] = f[0] * f[0];
-        f[4] = f[1] * f[1];
-        f[5] = f[2] * f[2];
-        f[6] = mine ? W : (T)0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int k = 0; k < 7; ++k) f[k] = mine ? fl[k] : (T)0;
+        int c = mine ? cnt_l : 0, cc = mine ? coll_l : 0;
+        if (grp != (1u << leader)) {
 #pragma unroll
-            for (int k = 0; k < 7; ++k) f[k] += __shfl_xor_sync(kFull, f[k], o);
+            for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                for (int k = 0; k < 7; ++k) f[k] += __shfl_xor_sync(kFull, f[k], o);
+            }
+            c = __reduce_add_sync(kFull, (unsigned)c);
+            cc = __reduce_add_sync(kFull, (unsigned)cc);
         }
         if ((int)lane_id() == leader) {
             const int slot = atomicAdd(&S.n, 1);
             S.bin[slot] = gb;
 #pragma unroll
             for (int k = 0; k < 7; ++k) S.f[k][slot] = f[k];
-            S.cnt[slot] = __popc(grp);
-            S.coll[slot] = __popc(grp & coll);
+            S.cnt[slot] = c;
+            S.coll[slot] = cc;
         }
         todo &= ~grp;
     }
@@ -329,8 +341,9 @@ __global__ void __launch_bounds__(kThreads) pack_kernel(Bufs<T> b, const T* __re
     }
     if (!ok) atomicAdd(bad, 1u);
     V P, Q;
-    P.x = x[0]; P.y = x[1]; P.z = x[2]; P.w = R<T>::from_bits(id);
-    Q.x = v[0]; Q.y = v[1]; Q.z = v[2]; Q.w = R<T>::from_bits((uint32_t)inst);
+    const uint32_t tag = (b.id_bits >= 32u ? 0u : ((uint32_t)inst << b.id_bits)) | id;
+    P.x = x[0]; P.y = x[1]; P.z = x[2]; P.w = R<T>::from_bits(tag);
+    Q.x = v[0]; Q.y = v[1]; Q.z = v[2]; Q.w = R<T>::inf();
     b.posB[p] = P;
     b.velB[p] = Q;
 }
@@ -350,7 +363,7 @@ __global__ void __launch_bounds__(kThreads) bin_kernel(Bufs<T> b) {
     if (valid) {
         P = b.posB[p];
         Q = b.velB[p];
-        inst = (int)R<T>::bits(Q.w);
+        inst = tag_inst(b, R<T>::bits(P.w));
     }
     const InstDev I = b.inst[inst];
     const T x[3] = {P.x, P.y, P.z};
@@ -615,7 +628,7 @@ __global__ void __launch_bounds__(kThreads) search_kernel(Bufs<T> b) {
     if (p >= b.n) return;
     const V P = b.posA[p];
     const V Q = b.velA[p];
-    const int inst = (int)R<T>::bits(Q.w);
+    const int inst = tag_inst(b, R<T>::bits(P.w));
     const InstDev& I = b.inst[inst];
     const int* kk = b.dyn[inst].k;
     const T xi[3] = {P.x, P.y, P.z};
@@ -640,16 +653,13 @@ __global__ void __launch_bounds__(kThreads) search_kernel(Bufs<T> b) {
 }
 
 // Unambiguous pairs, CM-frame scattering, split free flight, walls, then the
-// next step's search key / slot / histogram and the moment sums.
+// next step's search key / slot / histogram.  The particle's collisional
+// virial goes to vel.w for the moment pass.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kThreads) move_kernel(Bufs<T> b, int want_moments) {
+__global__ void __launch_bounds__(kThreads) move_kernel(Bufs<T> b) {
     using V = typename Vec4<T>::type;
     __shared__ GeoT<T> G;
-    __shared__ MomentSlots<T> S;
-    if (threadIdx.x == 0) {
-        G.load(b.geo);
-        S.n = 0;
-    }
+    if (threadIdx.x == 0) G.load(b.geo);
     __syncthreads();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = p < b.n;
@@ -659,21 +669,21 @@ __global__ void __launch_bounds__(kThreads) move_kernel(Bufs<T> b, int want_mome
     if (valid) {
         P = b.posA[p];
         Q = b.velA[p];
-        inst = (int)R<T>::bits(Q.w);
+        inst = tag_inst(b, R<T>::bits(P.w));
         j = b.best[p];
     }
     const InstDev I = b.inst[inst];
-    const uint32_t id = R<T>::bits(P.w);
+    const uint32_t tag = R<T>::bits(P.w);   // ordering of tags = ordering of local ids
     const T x[3] = {P.x, P.y, P.z};
     const T v[3] = {Q.x, Q.y, Q.z};
     const T dt = inst_dt(I, T());
     T xn[3] = {x[0], x[1], x[2]}, vn[3] = {v[0], v[1], v[2]};
     T W = (T)0;
     bool paired = false;
-    uint32_t idj = 0xffffffffu;
+    uint32_t tagj = 0xffffffffu;
     if (j >= 0) {
         paired = b.best[j] == (int32_t)p;
-        if (paired || b.record) idj = R<T>::bits(b.posA[j].w);
+        if (paired || b.record) tagj = R<T>::bits(b.posA[j].w);
     }
     if (paired) {
         const V Pj = b.posA[j];
@@ -695,8 +705,8 @@ __global__ void __launch_bounds__(kThreads) move_kernel(Bufs<T> b, int want_mome
         }
         const T b3 = (DIM == 3) ? bb : R<T>::fma(dv[2], dv[2], bb);
         const T tp = R<T>::div(-a, bb);                         // Eq. 12
-        const uint32_t lo_id = id < idj ? id : idj;
-        const T sgn = id < idj ? (T)1 : (T)-1;
+        const uint32_t lo_id = tag_id(b, tag < tagj ? tag : tagj);
+        const T sgn = tag < tagj ? (T)1 : (T)-1;
         const uint4 rnd = philox4x32_10(make_uint4(lo_id, b.st->step, 0u, 0u), I.seed_lo, I.seed_hi);
         T u1, u2;
         uniforms<T>(rnd, u1, u2);
@@ -750,20 +760,20 @@ __global__ void __launch_bounds__(kThreads) move_kernel(Bufs<T> b, int want_mome
         const uint32_t slot = aggregated_increment(b.count, skey, active);
         V Pn, Qn;
         Pn.x = xn[0]; Pn.y = xn[1]; Pn.z = xn[2]; Pn.w = P.w;
-        Qn.x = vn[0]; Qn.y = vn[1]; Qn.z = vn[2]; Qn.w = Q.w;
+        Qn.x = vn[0]; Qn.y = vn[1]; Qn.z = vn[2]; Qn.w = paired ? W : R<T>::inf();
         b.posB[p] = Pn;
         b.velB[p] = Qn;
         b.key[p] = skey;
         b.slot[p] = slot;
         if (b.record) {
-            const int64_t gid = I.p_off + (int64_t)id;
-            b.rec_best[gid] = (j >= 0) ? (int32_t)idj : -1;
-            b.rec_partner[gid] = paired ? (int32_t)idj : -1;
+            const int64_t gid = I.p_off + (int64_t)tag_id(b, tag);
+            b.rec_best[gid] = (j >= 0) ? (int32_t)tag_id(b, tagj) : -1;
+            b.rec_partner[gid] = paired ? (int32_t)tag_id(b, tagj) : -1;
         }
     }
+    (void)bin;
     const T v2 = vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2];
     warp_vmax<T>(b.dyn, valid, inst, v2);
-    if (want_moments) block_moments<T>(S, b.acc, valid, bin, vn, W, paired);
 }
 
 // Counting-sort scatter B -> A in search-key order.
@@ -788,8 +798,8 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(Bufs<T> b, T* __restri
     if (p >= b.n) return;
     const V P = b.posA[p];
     const V Q = b.velA[p];
-    const int inst = (int)R<T>::bits(Q.w);
-    const int64_t gid = b.inst[inst].p_off + (int64_t)R<T>::bits(P.w);
+    const int inst = tag_inst(b, R<T>::bits(P.w));
+    const int64_t gid = b.inst[inst].p_off + (int64_t)tag_id(b, R<T>::bits(P.w));
     if (pos3) { pos3[3 * gid] = P.x; pos3[3 * gid + 1] = P.y; pos3[3 * gid + 2] = P.z; }
     if (vel3) { vel3[3 * gid] = Q.x; vel3[3 * gid + 1] = Q.y; vel3[3 * gid + 2] = Q.z; }
 }
@@ -805,17 +815,21 @@ __global__ void __launch_bounds__(kThreads) cellkey_kernel(Bufs<T> b, int32_t* _
     if (p >= b.n) return;
     const V P = b.posA[p];
     const V Q = b.velA[p];
-    const int inst = (int)R<T>::bits(Q.w);
+    const int inst = tag_inst(b, R<T>::bits(P.w));
     const InstDev& I = b.inst[inst];
     const T x[3] = {P.x, P.y, P.z};
     uint32_t skey, bin;
     keys_of<T, DIM>(G, I, x, skey, bin);
-    keys[I.p_off + (int64_t)R<T>::bits(P.w)] = (int32_t)(bin - I.bin_base);
+    keys[I.p_off + (int64_t)tag_id(b, R<T>::bits(P.w))] = (int32_t)(bin - I.bin_base);
 }
 
-// Moment sums of the current state A (zero virial).
+// Moment sums per c-bin of the sorted state A (Eqs. vel_b, stress, 18, 19):
+// N, Sum v, Sum v^2, Sum W and the collided count.  Each thread reduces
+// kMomItems consecutive particles (consecutive particles of A share a c-bin
+// almost always), then warp and block aggregation as in block_moments.
+// use_virial = 0 ignores vel.w (state not produced by a step).
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kThreads) state_moments_kernel(Bufs<T> b) {
+__global__ void __launch_bounds__(kThreads) moments_kernel(Bufs<T> b, int use_virial) {
     using V = typename Vec4<T>::type;
     __shared__ GeoT<T> G;
     __shared__ MomentSlots<T> S;
@@ -824,21 +838,39 @@ __global__ void __launch_bounds__(kThreads) state_moments_kernel(Bufs<T> b) {
         S.n = 0;
     }
     __syncthreads();
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = p < b.n;
-    V P = {}, Q = {};
-    int inst = 0;
-    if (valid) {
-        P = b.posA[p];
-        Q = b.velA[p];
-        inst = (int)R<T>::bits(Q.w);
+    const int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kMomItems;
+    uint32_t cur = 0xffffffffu;
+    T f[7] = {0, 0, 0, 0, 0, 0, 0};
+    int cnt = 0, coll = 0;
+    for (int k = 0; k < kMomItems; ++k) {
+        const int64_t p = base + k;
+        if (p >= b.n) break;
+        const V P = b.posA[p];
+        const V Q = b.velA[p];
+        const int inst = tag_inst(b, R<T>::bits(P.w));
+        const InstDev& I = b.inst[inst];
+        const T x[3] = {P.x, P.y, P.z};
+        uint32_t skey, bin;
+        keys_of<T, DIM>(G, I, x, skey, bin);
+        if (bin != cur && cnt > 0) {   // rare: the thread's particles span two bins
+            double* a = b.acc + (size_t)cur * kAccFields;
+            atomicAdd(a + 0, (double)cnt);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) atomicAdd(a + 1 + q, (double)f[q]);
+            if (coll) atomicAdd(a + 8, (double)coll);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) f[q] = (T)0;
+            cnt = coll = 0;
+        }
+        cur = bin;
+        const bool collided = use_virial && Q.w != R<T>::inf();
+        f[0] += Q.x; f[1] += Q.y; f[2] += Q.z;
+        f[3] += Q.x * Q.x; f[4] += Q.y * Q.y; f[5] += Q.z * Q.z;
+        if (collided) f[6] += Q.w;
+        cnt += 1;
+        coll += collided ? 1 : 0;
     }
-    const InstDev I = b.inst[inst];
-    const T x[3] = {P.x, P.y, P.z};
-    const T v[3] = {Q.x, Q.y, Q.z};
-    uint32_t skey = 0, bin = 0;
-    keys_of<T, DIM>(G, I, x, skey, bin);
-    block_moments<T>(S, b.acc, valid, bin, v, (T)0, false);
+    block_moment_partials<T>(S, b.acc, cnt > 0, cur, f, cnt, coll);
 }
 
 // Particles per c-bin and largest |v|^2 per instance of the packed state in B
@@ -857,7 +889,7 @@ __global__ void __launch_bounds__(kThreads) cbin_hist_kernel(Bufs<T> b, uint32_t
     if (valid) {
         P = b.posB[p];
         Q = b.velB[p];
-        inst = (int)R<T>::bits(Q.w);
+        inst = tag_inst(b, R<T>::bits(P.w));
     }
     const InstDev I = b.inst[inst];
     const T x[3] = {P.x, P.y, P.z};
@@ -912,9 +944,9 @@ cudaError_t launch_search(const Bufs<T>& b, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t launch_move(const Bufs<T>& b, int want_moments, cudaStream_t s) {
+cudaError_t launch_move(const Bufs<T>& b, cudaStream_t s) {
     if (b.n == 0) return cudaSuccess;
-    KMC_DIM_DISPATCH(b.geo.dim, move_kernel, b, want_moments);
+    KMC_DIM_DISPATCH(b.geo.dim, move_kernel, b);
     return cudaGetLastError();
 }
 
@@ -940,9 +972,12 @@ cudaError_t launch_cell_keys(const Bufs<T>& b, int32_t* keys, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t launch_moments_state(const Bufs<T>& b, cudaStream_t s) {
+cudaError_t launch_moments(const Bufs<T>& b, int use_virial, cudaStream_t s) {
     if (b.n == 0) return cudaSuccess;
-    KMC_DIM_DISPATCH(b.geo.dim, state_moments_kernel, b);
+    const int64_t threads = (b.n + kMomItems - 1) / kMomItems;
+    const unsigned blocks = (unsigned)((threads + kThreads - 1) / kThreads);
+    if (b.geo.dim == 3) moments_kernel<T, 3><<<blocks, kThreads, 0, s>>>(b, use_virial);
+    else moments_kernel<T, 2><<<blocks, kThreads, 0, s>>>(b, use_virial);
     return cudaGetLastError();
 }
 
@@ -957,11 +992,11 @@ cudaError_t launch_cbin_hist(const Bufs<T>& b, uint32_t* hist, unsigned long lon
     template cudaError_t launch_pack<T>(const Bufs<T>&, const T*, const T*, uint32_t*, cudaStream_t); \
     template cudaError_t launch_bin_init<T>(const Bufs<T>&, cudaStream_t);                         \
     template cudaError_t launch_search<T>(const Bufs<T>&, cudaStream_t);                           \
-    template cudaError_t launch_move<T>(const Bufs<T>&, int, cudaStream_t);                        \
+    template cudaError_t launch_move<T>(const Bufs<T>&, cudaStream_t);                             \
     template cudaError_t launch_scatter<T>(const Bufs<T>&, cudaStream_t);                          \
     template cudaError_t launch_gather_state<T>(const Bufs<T>&, T*, T*, cudaStream_t);             \
     template cudaError_t launch_cell_keys<T>(const Bufs<T>&, int32_t*, cudaStream_t);              \
-    template cudaError_t launch_moments_state<T>(const Bufs<T>&, cudaStream_t);                   \
+    template cudaError_t launch_moments<T>(const Bufs<T>&, int, cudaStream_t);                     \
     template cudaError_t launch_cbin_hist<T>(const Bufs<T>&, uint32_t*, unsigned long long*, cudaStream_t);
 
 }  // namespace kmc
