@@ -48,6 +48,8 @@ struct kmc_handle {
     int32_t *rec_best = nullptr, *rec_partner = nullptr;
     uint32_t n_keys = 0, n_tiles = 0;
     uint32_t id_bits = 32;
+    uint32_t n_stage_tiles = 0;
+    int stage_cap = 0, stage_rows = 0, stage_stride = 0, any_direct = 1;
     int64_t n_bins = 0, bins_per_inst = 0;
     int64_t bytes = 0;
     int mom_state = 0;  // 1: acc/mom/glob describe the current state
@@ -119,6 +121,11 @@ Bufs<T> make_bufs(const kmc_handle* h) {
     b.rec_best = h->rec_best;
     b.rec_partner = h->rec_partner;
     b.record = (h->cfg.flags & KMC_FLAG_RECORD) ? 1 : 0;
+    b.n_stage_tiles = h->n_stage_tiles;
+    b.stage_cap = h->stage_cap;
+    b.stage_rows = h->stage_rows;
+    b.stage_stride = h->stage_stride;
+    b.any_direct = h->any_direct;
     b.id_bits = h->id_bits;
     b.id_mask = h->id_bits >= 32 ? 0xffffffffu : ((1u << h->id_bits) - 1u);
     return b;
@@ -267,6 +274,57 @@ void choose_subdivision(const kmc_handle* h, InstDev& I, double vmax, uint32_t m
     }
 }
 
+// Staged search plan (3-D only): a tile is tile_rows y-rows of one x-slab,
+// sized for about one block of home particles in the densest rows; the tile's
+// neighbourhood (3 x-slabs by tile_rows + 2 y-rows at the first step) must
+// fit the shared-memory budget, otherwise the instance is searched directly.
+void plan_staged_search(kmc_handle* h, const std::vector<uint32_t>& max_occ) {
+    const size_t vbytes = vec_size(h);
+    const size_t budget = 160 * 1024;
+    uint32_t tiles = 0;
+    int cap = 0, rows = 0, stride = 0, direct = 0;
+    for (int i = 0; i < h->n_inst; ++i) {
+        InstDev& I = h->inst_h[i];
+        I.staged = 0;
+        I.tile_rows = 1;
+        I.tiles_per_x = 1;
+        I.tile_base = tiles;
+        bool ok = h->dim == 3 && I.n > 0 && !(h->cfg.flags & KMC_FLAG_DIRECT_SEARCH);
+        double ppr = 1.0;   // particles per y-row (all z) in the densest c-bins
+        if (ok) {
+            ppr = std::max(1.0, (double)max_occ[i] * h->geo.n[2] / ((double)I.s[0] * I.s[1]));
+            int R = (int)std::floor(0.9 * kStageThreads / ppr);
+            R = std::max(1, std::min(R, I.M[1]));
+            const int nxs = std::min(3, I.M[0]);
+            const int rows_i = nxs * (R + 4);
+            const int cap_i = ((int)std::ceil(nxs * (R + 2) * ppr * 1.35) + 64 + 31) / 32 * 32;
+            const size_t bytes = (size_t)cap_i * 2 * vbytes + (size_t)rows_i * (I.M[2] + 1) * sizeof(uint32_t);
+            ok = I.s[0] == 1 && R + 4 < I.M[1] && rows_i <= 64 && bytes <= budget;
+            if (ok) {
+                I.staged = 1;
+                I.tile_rows = R;
+                I.tiles_per_x = (I.M[1] + R - 1) / R;
+                tiles += (uint32_t)(I.M[0] * I.tiles_per_x);
+                cap = std::max(cap, cap_i);
+                rows = std::max(rows, rows_i);
+                stride = std::max(stride, I.M[2] + 1);
+            }
+        }
+        if (!ok) direct = 1;
+    }
+    const size_t total = (size_t)cap * 2 * vbytes + (size_t)rows * stride * sizeof(uint32_t);
+    if (tiles > 0 && total > budget) {   // instances disagree too much: search all directly
+        for (auto& I : h->inst_h) I.staged = 0;
+        tiles = 0;
+        direct = 1;
+    }
+    h->n_stage_tiles = tiles;
+    h->stage_cap = cap;
+    h->stage_rows = rows;
+    h->stage_stride = stride;
+    h->any_direct = direct;
+}
+
 int validate_config(const kmc_config* c, int64_t n) {
     if (!c) return fail(nullptr, KMC_EINVAL, "cfg is NULL");
     if (c->dim_pos != 2 && c->dim_pos != 3) return fail(nullptr, KMC_EINVAL, "dim_pos must be 2 or 3");
@@ -283,7 +341,8 @@ int validate_config(const kmc_config* c, int64_t n) {
     }
     if (c->n_instances < 0) return fail(nullptr, KMC_EINVAL, "n_instances < 0");
     if (c->n_instances > 1 && !c->instances) return fail(nullptr, KMC_EINVAL, "instances is NULL");
-    if (c->flags & ~(KMC_FLAG_RECORD | KMC_FLAG_NO_GRAPH)) return fail(nullptr, KMC_EINVAL, "unknown flags");
+    if (c->flags & ~(KMC_FLAG_RECORD | KMC_FLAG_NO_GRAPH | KMC_FLAG_DIRECT_SEARCH))
+        return fail(nullptr, KMC_EINVAL, "unknown flags");
     return KMC_OK;
 }
 
@@ -492,9 +551,11 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
               cudaStreamSynchronize(h->stream) == cudaSuccess;
         if (!okc) return bail(fail(h, KMC_ECUDA, "search-grid statistics failed"));
         uint64_t keys = 0;
+        std::vector<uint32_t> max_occ(h->n_inst, 0u);
         for (int i = 0; i < h->n_inst; ++i) {
             uint32_t mx = 0;
             for (int64_t b = 0; b < h->bins_per_inst; ++b) mx = std::max(mx, hist_h[(size_t)(i * h->bins_per_inst + b)]);
+            max_occ[i] = mx;
             double v2;
             memcpy(&v2, &vm_h[i], sizeof(double));
             choose_subdivision(h, h->inst_h[i], sqrt(v2), mx);
@@ -505,6 +566,7 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
         }
         h->n_keys = (uint32_t)keys;
         h->n_tiles = (uint32_t)((keys + 1 + kScanTile - 1) / kScanTile);
+        plan_staged_search(h, max_occ);
         if (cudaMemcpyAsync(h->inst_d, h->inst_h.data(), sizeof(InstDev) * h->n_inst, cudaMemcpyHostToDevice,
                             h->stream) != cudaSuccess)
             return bail(fail(h, KMC_ECUDA, "upload of instance table failed"));
@@ -514,6 +576,11 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
     if ((rc = dev_alloc(h, (void**)&h->start, padded * sizeof(uint32_t)))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->scan_status, (1 + (size_t)h->n_tiles) * sizeof(unsigned long long))))
         return bail(rc);
+    if (h->n_stage_tiles > 0) {
+        const cudaError_t e = h->precision == 64 ? prepare_staged<double>(make_bufs<double>(h))
+                                                 : prepare_staged<float>(make_bufs<float>(h));
+        if (e != cudaSuccess) return bail(fail(h, KMC_ECUDA, std::string("staged search set-up: ") + cudaGetErrorString(e)));
+    }
     if ((rc = sort_packed(h, 0u))) return bail(rc);
     *out = h;
     return KMC_OK;

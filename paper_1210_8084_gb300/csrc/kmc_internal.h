@@ -25,6 +25,7 @@ constexpr uint32_t kErrScanTimeout = 1u;
 constexpr uint32_t kErrKeyRange = 2u;
 
 constexpr int kMomItems = 4;           // moments: consecutive particles per thread
+constexpr int kStageThreads = 256;     // staged search: threads per tile
 
 // Per-instance constants.  Geometry (box, c-bins, walls) is shared; the search
 // grid subdivision s[] and the interaction constants are per instance.
@@ -40,6 +41,13 @@ struct InstDev {
     float R2f, dtf;      // the same rounded to binary32 (binary32 kernels use these)
     uint32_t seed_lo, seed_hi;
     double w[3];         // search-cell width per dimension
+    // staged search (3-D, sparse search cells): tiles of tile_rows consecutive
+    // y-rows of one x-slab; the tile's neighbourhood rows are copied to
+    // shared memory before the search
+    int staged;
+    int tile_rows;
+    int tiles_per_x;     // ceil(M[1] / tile_rows)
+    uint32_t tile_base;  // first tile of the instance in the staged launch
 };
 
 // Per-instance quantities that change every step (written on the device).
@@ -105,6 +113,12 @@ struct Bufs {
     int32_t* rec_best;       // RECORD: [n] by global id
     int32_t* rec_partner;    // RECORD: [n] by global id
     int record;
+    // staged search launch
+    uint32_t n_stage_tiles;  // tiles over all staged instances (0: none)
+    int stage_cap;           // candidate vectors a tile can stage
+    int stage_rows;          // row slots of the staged start table
+    int stage_stride;        // entries per row slot (max M[2] + 1)
+    int any_direct;          // some instance uses the direct (per-thread) search
     // particle tag = (instance << id_bits) | instance-local id
     uint32_t id_bits;        // 32 when there is one instance
     uint32_t id_mask;
@@ -117,6 +131,10 @@ template <typename T>
 cudaError_t launch_bin_init(const Bufs<T>& b, cudaStream_t s);
 template <typename T>
 cudaError_t launch_search(const Bufs<T>& b, cudaStream_t s);
+template <typename T>
+cudaError_t prepare_staged(const Bufs<T>& b);
+template <typename T>
+size_t stage_smem_bytes(const Bufs<T>& b);
 template <typename T>
 cudaError_t launch_move(const Bufs<T>& b, cudaStream_t s);
 template <typename T>

@@ -630,6 +630,7 @@ __global__ void __launch_bounds__(kThreads) search_kernel(Bufs<T> b) {
     const V Q = b.velA[p];
     const int inst = tag_inst(b, R<T>::bits(P.w));
     const InstDev& I = b.inst[inst];
+    if (I.staged) return;   // searched by the staged kernel
     const int* kk = b.dyn[inst].k;
     const T xi[3] = {P.x, P.y, P.z};
     const T vi[3] = {Q.x, Q.y, Q.z};
@@ -650,6 +651,227 @@ __global__ void __launch_bounds__(kThreads) search_kernel(Bufs<T> b) {
     if (amb) scan_window<T, DIM, true>(b, G, I, w, xi, vi, dt, R2, bd, bid, bq);
     else scan_window<T, DIM, false>(b, G, I, w, xi, vi, dt, R2, bd, bid, bq);
     b.best[p] = bq;
+}
+
+// Direct search of one particle (global loads), used by the staged kernel for
+// particles whose window it cannot serve from shared memory.
+template <typename T, int DIM>
+__device__ __noinline__ int32_t search_one_direct(const Bufs<T>& b, const GeoT<T>& G, int64_t p) {
+    using V = typename Vec4<T>::type;
+    const V P = b.posA[p];
+    const V Q = b.velA[p];
+    const int inst = tag_inst(b, R<T>::bits(P.w));
+    const InstDev& I = b.inst[inst];
+    const int* kk = b.dyn[inst].k;
+    const T xi[3] = {P.x, P.y, P.z};
+    const T vi[3] = {Q.x, Q.y, Q.z};
+    const T dt = inst_dt(I, T()), R2 = inst_R2(I, T());
+    int c[3] = {0, 0, 0}, g[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) cell_and_search<T>(xi[d], G.lo[d], G.inv[d], G.n[d], I.s[d], c[d], g[d]);
+    Win w[3];
+    bool amb = false;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        w[d] = window_1d(g[d], c[d], I.s[d], I.M[d], kk[d], G.wall[d]);
+        amb = amb || w[d].amb;
+    }
+    T bd = R<T>::inf();
+    uint32_t bid = 0xffffffffu;
+    int32_t bq = -1;
+    if (amb) scan_window<T, DIM, true>(b, G, I, w, xi, vi, dt, R2, bd, bid, bq);
+    else scan_window<T, DIM, false>(b, G, I, w, xi, vi, dt, R2, bd, bid, bq);
+    return bq;
+}
+
+// Staged search (3-D, sparse search cells).  A block owns a tile: tile_rows
+// consecutive y-rows of one x-slab, i.e. one contiguous range of A.  Every
+// row of the tile's neighbourhood (x-slabs of the window, y-rows of the
+// union of the windows) is a contiguous range of A too; those rows and their
+// search-cell offsets are copied to shared memory with coalesced loads, then
+// each thread walks its own window there: same candidates, same test, same
+// tie rule as the direct search, without dependent global loads.  A tile
+// whose neighbourhood does not fit, or a particle whose window is not a plain
+// unwrapped window, takes the direct path.
+constexpr int kStageMaxRows = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(kStageThreads) search_staged_kernel(Bufs<T> b) {
+    using V = typename Vec4<T>::type;
+    extern __shared__ __align__(32) unsigned char smem[];
+    V* sp = reinterpret_cast<V*>(smem);
+    V* sv = sp + b.stage_cap;
+    uint32_t* loc = reinterpret_cast<uint32_t*>(sv + b.stage_cap);
+    __shared__ GeoT<T> G;
+    __shared__ int s_inst, s_gx, s_y0, s_y1, s_xlo, s_nx, s_ylo, s_ny, s_ok;
+    __shared__ int32_t s_h0, s_h1;
+    __shared__ int32_t s_rowA0[kStageMaxRows];
+    __shared__ int32_t s_rowL0[kStageMaxRows + 1];
+    const int tid = threadIdx.x;
+    const uint32_t tile = blockIdx.x;
+    if (tid == 0) {
+        G.load(b.geo);
+        int lo = 0, hi = b.n_inst - 1;   // last instance with tile_base <= tile
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (b.inst[mid].tile_base <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        const InstDev& I = b.inst[lo];
+        const uint32_t t = tile - I.tile_base;
+        s_inst = lo;
+        s_gx = (int)(t / (uint32_t)I.tiles_per_x);
+        s_y0 = (int)(t % (uint32_t)I.tiles_per_x) * I.tile_rows;
+        s_y1 = min(s_y0 + I.tile_rows, I.M[1]);
+        const uint32_t Mz = (uint32_t)I.M[2], My = (uint32_t)I.M[1];
+        const uint32_t k0 = I.key_base + ((uint32_t)s_gx * My + (uint32_t)s_y0) * Mz;
+        const uint32_t k1 = I.key_base + ((uint32_t)s_gx * My + (uint32_t)s_y1) * Mz;
+        s_h0 = (int32_t)min(b.start[k0], (uint32_t)b.n);
+        s_h1 = (int32_t)min(b.start[k1], (uint32_t)b.n);
+        const int* kk = b.dyn[lo].k;
+        // x-slabs of the (common) x-window, union of the y-windows
+        const Win wx = window_1d(s_gx, s_gx / I.s[0], I.s[0], I.M[0], kk[0], G.wall[0]);
+        const Win wy0 = window_1d(s_y0, s_y0 / I.s[1], I.s[1], I.M[1], kk[1], G.wall[1]);
+        const Win wy1 = window_1d(s_y1 - 1, (s_y1 - 1) / I.s[1], I.s[1], I.M[1], kk[1], G.wall[1]);
+        s_xlo = wx.lo;
+        s_nx = wx.hi - wx.lo + 1;
+        s_ylo = wy0.lo;
+        s_ny = wy1.hi - wy0.lo + 1;
+        s_ok = !wx.amb && !wy0.amb && !wy1.amb && s_ny < I.M[1] && s_nx * s_ny <= min(b.stage_rows, kStageMaxRows);
+    }
+    __syncthreads();
+    if (s_h0 >= s_h1) return;
+    const InstDev& I = b.inst[s_inst];
+    const uint32_t Mz = (uint32_t)I.M[2], My = (uint32_t)I.M[1];
+    const int nr = s_nx * s_ny;
+    if (s_ok) {
+        // row ranges of A
+        for (int r = tid; r < nr; r += blockDim.x) {
+            T sh;
+            const int gx = unwrap<T>(s_xlo + r / s_ny, I.M[0], G.L[0], sh);
+            const int gy = unwrap<T>(s_ylo + r % s_ny, I.M[1], G.L[1], sh);
+            const uint32_t rk = I.key_base + ((uint32_t)gx * My + (uint32_t)gy) * Mz;
+            const int32_t a0 = (int32_t)min(b.start[rk], (uint32_t)b.n);
+            const int32_t a1 = (int32_t)min(b.start[rk + Mz], (uint32_t)b.n);
+            s_rowA0[r] = a0;
+            s_rowL0[r + 1] = max(a1 - a0, 0);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            s_rowL0[0] = 0;
+            for (int r = 0; r < nr; ++r) s_rowL0[r + 1] += s_rowL0[r];
+            if (s_rowL0[nr] > b.stage_cap) s_ok = 0;
+        }
+        __syncthreads();
+    }
+    if (!s_ok) {   // neighbourhood too large for this tile: direct search
+        for (int64_t p = s_h0 + tid; p < s_h1; p += blockDim.x) b.best[p] = search_one_direct<T, 3>(b, G, p);
+        return;
+    }
+    // copy the rows and their search-cell offsets
+    const int total = s_rowL0[nr];
+    for (int e = tid; e < total; e += blockDim.x) {
+        int r = 0;
+        while (s_rowL0[r + 1] <= e) ++r;
+        const int32_t a = s_rowA0[r] + (e - s_rowL0[r]);
+        sp[e] = ldg_vec(b.posA + a);
+        sv[e] = ldg_vec(b.velA + a);
+    }
+    const int stride = b.stage_stride;
+    for (int e = tid; e < nr * ((int)Mz + 1); e += blockDim.x) {
+        const int r = e / ((int)Mz + 1), z = e % ((int)Mz + 1);
+        T sh;
+        const int gx = unwrap<T>(s_xlo + r / s_ny, I.M[0], G.L[0], sh);
+        const int gy = unwrap<T>(s_ylo + r % s_ny, I.M[1], G.L[1], sh);
+        const uint32_t rk = I.key_base + ((uint32_t)gx * My + (uint32_t)gy) * Mz;
+        const int32_t a = (int32_t)min(b.start[rk + (uint32_t)z], (uint32_t)b.n);
+        loc[r * stride + z] = (uint32_t)(s_rowL0[r] + (a - s_rowA0[r]));
+    }
+    __syncthreads();
+
+    const int* kk = b.dyn[s_inst].k;
+    const T dt = inst_dt(I, T()), R2 = inst_R2(I, T());
+    for (int64_t p = s_h0 + tid; p < s_h1; p += blockDim.x) {
+        const V P = b.posA[p];
+        const V Q = b.velA[p];
+        const T xi[3] = {P.x, P.y, P.z};
+        const T vi[3] = {Q.x, Q.y, Q.z};
+        int c[3], g[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) cell_and_search<T>(xi[d], G.lo[d], G.inv[d], G.n[d], I.s[d], c[d], g[d]);
+        Win w[3];
+        bool amb = false;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            w[d] = window_1d(g[d], c[d], I.s[d], I.M[d], kk[d], G.wall[d]);
+            amb = amb || w[d].amb;
+        }
+        if (amb || w[0].lo < s_xlo || w[0].hi >= s_xlo + s_nx || w[1].lo < s_ylo || w[1].hi >= s_ylo + s_ny) {
+            b.best[p] = search_one_direct<T, 3>(b, G, p);
+            continue;
+        }
+        // z parts of the window (z is the fastest key dimension)
+        const int MZ = I.M[2];
+        int fa[2], fb[2];
+        T fs[2] = {(T)0, (T)0};
+        int nf = 1;
+        if (w[2].lo < 0) {
+            fa[0] = w[2].lo + MZ; fb[0] = MZ - 1; fs[0] = G.L[2];
+            fa[1] = 0; fb[1] = w[2].hi;
+            nf = 2;
+        } else if (w[2].hi >= MZ) {
+            fa[0] = w[2].lo; fb[0] = MZ - 1;
+            fa[1] = 0; fb[1] = w[2].hi - MZ; fs[1] = -G.L[2];
+            nf = 2;
+        } else {
+            fa[0] = w[2].lo; fb[0] = w[2].hi;
+        }
+        T bd = R<T>::inf();
+        uint32_t bid = 0xffffffffu;
+        int32_t bq = -1;
+        int tx = w[0].lo, ty = w[1].lo, part = 0;
+        int32_t q = 0, qe = 0, off = 0;
+        T sh[3] = {(T)0, (T)0, (T)0};
+        for (;;) {
+            if (q >= qe) {
+                bool more = false;
+                while (tx <= w[0].hi) {
+                    T sx, sy;
+                    unwrap<T>(tx, I.M[0], G.L[0], sx);
+                    unwrap<T>(ty, I.M[1], G.L[1], sy);
+                    const int r = (tx - s_xlo) * s_ny + (ty - s_ylo);
+                    q = (int32_t)loc[r * stride + fa[part]];
+                    qe = (int32_t)loc[r * stride + fb[part] + 1];
+                    off = s_rowA0[r] - s_rowL0[r];
+                    sh[0] = sx;
+                    sh[1] = sy;
+                    sh[2] = part == 0 ? fs[0] : fs[1];
+                    if (++part == nf) {
+                        part = 0;
+                        if (++ty > w[1].hi) { ty = w[1].lo; ++tx; }
+                    }
+                    if (q < qe) { more = true; break; }
+                }
+                if (!more) break;
+            }
+            const V Pj = sp[q];
+            const V Qj = sv[q];
+            const T xj[3] = {Pj.x, Pj.y, Pj.z};
+            const T vj[3] = {Qj.x, Qj.y, Qj.z};
+            T d2;
+            // the particle itself has v_rel = 0 and fails b > 0
+            if (poca_test_sh<T, 3, false>(G, xi, vi, xj, vj, sh, dt, R2, d2)) {
+                const uint32_t idj = R<T>::bits(Pj.w);
+                if (d2 < bd || (d2 == bd && idj < bid)) {
+                    bd = d2;
+                    bid = idj;
+                    bq = q + off;
+                }
+            }
+            ++q;
+        }
+        b.best[p] = bq;
+    }
 }
 
 // Unambiguous pairs, CM-frame scattering, split free flight, walls, then the
@@ -937,10 +1159,27 @@ cudaError_t launch_bin_init(const Bufs<T>& b, cudaStream_t s) {
 }
 
 template <typename T>
+size_t stage_smem_bytes(const Bufs<T>& b) {
+    return (size_t)b.stage_cap * 2 * sizeof(typename Vec4<T>::type) +
+           (size_t)b.stage_rows * (size_t)b.stage_stride * sizeof(uint32_t);
+}
+
+template <typename T>
 cudaError_t launch_search(const Bufs<T>& b, cudaStream_t s) {
     if (b.n == 0) return cudaSuccess;
-    KMC_DIM_DISPATCH(b.geo.dim, search_kernel, b);
+    if (b.n_stage_tiles > 0) {
+        search_staged_kernel<T><<<b.n_stage_tiles, kStageThreads, stage_smem_bytes(b), s>>>(b);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (b.any_direct) KMC_DIM_DISPATCH(b.geo.dim, search_kernel, b);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t prepare_staged(const Bufs<T>& b) {
+    const size_t bytes = stage_smem_bytes(b);
+    return cudaFuncSetAttribute(search_staged_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <typename T>
@@ -992,6 +1231,8 @@ cudaError_t launch_cbin_hist(const Bufs<T>& b, uint32_t* hist, unsigned long lon
     template cudaError_t launch_pack<T>(const Bufs<T>&, const T*, const T*, uint32_t*, cudaStream_t); \
     template cudaError_t launch_bin_init<T>(const Bufs<T>&, cudaStream_t);                         \
     template cudaError_t launch_search<T>(const Bufs<T>&, cudaStream_t);                           \
+    template cudaError_t prepare_staged<T>(const Bufs<T>&);                                        \
+    template size_t stage_smem_bytes<T>(const Bufs<T>&);                                           \
     template cudaError_t launch_move<T>(const Bufs<T>&, cudaStream_t);                             \
     template cudaError_t launch_scatter<T>(const Bufs<T>&, cudaStream_t);                          \
     template cudaError_t launch_gather_state<T>(const Bufs<T>&, T*, T*, cudaStream_t);             \

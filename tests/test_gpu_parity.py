@@ -26,10 +26,11 @@ def _setup():
 
 
 def run_gpu_step(pos, vel, dim, n_cells, lo, hi, bc, lam, dt, seed, precision, step=0, sub_cells=(0, 0, 0),
-                 nsteps=1):
+                 nsteps=1, direct=False, occ=0.0):
     import paper_1210_8084_gb300 as k
+    flags = k.KMC_FLAG_RECORD | (k.KMC_FLAG_DIRECT_SEARCH if direct else 0)
     cfg = k.make_config(dim_pos=dim, n_cells=n_cells, lo=lo, hi=hi, bc=bc, lam=lam, dt=dt, seed=seed,
-                        precision=precision, flags=k.KMC_FLAG_RECORD, sub_cells=sub_cells)
+                        precision=precision, flags=flags, sub_cells=sub_cells, occupancy_target=occ)
     sim = k.Simulation(cfg, pos, vel)
     if step:
         p0, v0 = sim.state()
@@ -108,15 +109,18 @@ def make_inputs(name, n, dim, lo, hi):
     return pos, vel
 
 
+@pytest.mark.parametrize("direct", [False, True], ids=["auto", "direct"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_one_step_parity(case):
+def test_one_step_parity(case, direct):
+    """One step from the same state; the automatic search (shared-memory
+    staged tiles where they fit) and the direct search must both match."""
     _setup()
     name, n, dim, n_cells, lo, hi, bc, lam, dt, prec = case
     pos, vel = make_inputs(name, n, dim, lo, hi)
     if prec == 32:
         pos, vel = f32_state(pos, vel, lo, hi, bc)
     seed = 11
-    g = run_gpu_step(pos, vel, dim, n_cells, lo, hi, bc, lam, dt, seed, prec)
+    g = run_gpu_step(pos, vel, dim, n_cells, lo, hi, bc, lam, dt, seed, prec, direct=direct)
     o = oracle_step(pos, vel, dim, n_cells, lo, hi, bc, g["info"].R2, dt, seed, 0, prec == 32)
     assert (g["best"] >= 0).mean() > 0.02 or lam >= 1.0
     compare_step(g, o, prec, pos, vel, dim)
@@ -131,7 +135,7 @@ def test_contact_distance_matches_oracle_bitwise():
         assert g["info"].R2 == oracle.contact_R2(lam, 0.0, 5000.0)
 
 
-@pytest.mark.parametrize("sub", [(1, 1, 1), (1, 3, 2), (1, 40, 40), (0, 0, 0)])
+@pytest.mark.parametrize("sub", [(1, 1, 1), (1, 3, 2), (1, 9, 9), (1, 40, 40), (0, 0, 0)])
 def test_search_grid_subdivision_does_not_change_results(sub):
     """Any subdivision of the c-bins into search cells returns the same
     closest candidates as the plain 3^D neighbourhood (the window adapts)."""
