@@ -110,6 +110,9 @@ typedef struct kmc_info {
     double vmax;             /* instance 0: largest speed of the current state */
     int window[3];           /* instance 0: search half-width in search cells for the next step */
     int64_t bytes_device;    /* device memory held by the handle */
+    int64_t stage_tiles;     /* tiles of the shared-memory staged search (0: direct search only) */
+    int tile_rows;           /* instance 0: y-rows per staged tile (0: searched directly) */
+    int stage_cap;           /* candidates a staged tile holds in shared memory */
 } kmc_info;
 
 /* Create a simulation.  pos and vel are n x 3 row-major arrays of float

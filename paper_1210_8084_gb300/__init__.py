@@ -90,6 +90,9 @@ class KmcInfo(ctypes.Structure):
         ("vmax", ctypes.c_double),
         ("window", ctypes.c_int * 3),
         ("bytes_device", ctypes.c_int64),
+        ("stage_tiles", ctypes.c_int64),
+        ("tile_rows", ctypes.c_int),
+        ("stage_cap", ctypes.c_int),
     ]
 
 

@@ -750,6 +750,9 @@ int kmc_get_info(kmc_handle* h, kmc_info* info) {
     memcpy(&v2, &dy.vmax2_cur, sizeof(double));
     info->vmax = sqrt(v2);
     info->bytes_device = h->bytes;
+    info->stage_tiles = h->n_stage_tiles;
+    info->tile_rows = I.staged ? I.tile_rows : 0;
+    info->stage_cap = h->stage_cap;
     return KMC_OK;
 }
 
