@@ -707,6 +707,7 @@ __global__ void __launch_bounds__(kStageThreads) search_staged_kernel(Bufs<T> b)
     __shared__ int32_t s_h0, s_h1;
     __shared__ int32_t s_rowA0[kStageMaxRows];
     __shared__ int32_t s_rowL0[kStageMaxRows + 1];
+    __shared__ uint32_t s_rowK[kStageMaxRows];
     const int tid = threadIdx.x;
     const uint32_t tile = blockIdx.x;
     if (tid == 0) {
@@ -753,6 +754,7 @@ __global__ void __launch_bounds__(kStageThreads) search_staged_kernel(Bufs<T> b)
             const uint32_t rk = I.key_base + ((uint32_t)gx * My + (uint32_t)gy) * Mz;
             const int32_t a0 = (int32_t)min(b.start[rk], (uint32_t)b.n);
             const int32_t a1 = (int32_t)min(b.start[rk + Mz], (uint32_t)b.n);
+            s_rowK[r] = rk;
             s_rowA0[r] = a0;
             s_rowL0[r + 1] = max(a1 - a0, 0);
         }
@@ -768,24 +770,22 @@ __global__ void __launch_bounds__(kStageThreads) search_staged_kernel(Bufs<T> b)
         for (int64_t p = s_h0 + tid; p < s_h1; p += blockDim.x) b.best[p] = search_one_direct<T, 3>(b, G, p);
         return;
     }
-    // copy the rows and their search-cell offsets
-    const int total = s_rowL0[nr];
-    for (int e = tid; e < total; e += blockDim.x) {
-        int r = 0;
-        while (s_rowL0[r + 1] <= e) ++r;
-        const int32_t a = s_rowA0[r] + (e - s_rowL0[r]);
-        sp[e] = ldg_vec(b.posA + a);
-        sv[e] = ldg_vec(b.velA + a);
-    }
+    // copy the rows and their search-cell offsets: one warp per row, lanes
+    // along the row (coalesced)
     const int stride = b.stage_stride;
-    for (int e = tid; e < nr * ((int)Mz + 1); e += blockDim.x) {
-        const int r = e / ((int)Mz + 1), z = e % ((int)Mz + 1);
-        T sh;
-        const int gx = unwrap<T>(s_xlo + r / s_ny, I.M[0], G.L[0], sh);
-        const int gy = unwrap<T>(s_ylo + r % s_ny, I.M[1], G.L[1], sh);
-        const uint32_t rk = I.key_base + ((uint32_t)gx * My + (uint32_t)gy) * Mz;
-        const int32_t a = (int32_t)min(b.start[rk + (uint32_t)z], (uint32_t)b.n);
-        loc[r * stride + z] = (uint32_t)(s_rowL0[r] + (a - s_rowA0[r]));
+    const int lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    for (int r = warp; r < nr; r += nwarps) {
+        const int32_t a0 = s_rowA0[r], l0 = s_rowL0[r], cnt = s_rowL0[r + 1] - l0;
+        for (int t = lane; t < cnt; t += 32) {
+            sp[l0 + t] = ldg_vec(b.posA + a0 + t);
+            sv[l0 + t] = ldg_vec(b.velA + a0 + t);
+        }
+        const uint32_t rk = s_rowK[r];
+        uint32_t* lr = loc + r * stride;
+        for (int z = lane; z <= (int)Mz; z += 32) {
+            const int32_t a = (int32_t)min(b.start[rk + (uint32_t)z], (uint32_t)b.n);
+            lr[z] = (uint32_t)(l0 + (a - a0));
+        }
     }
     __syncthreads();
 
