@@ -49,7 +49,7 @@ struct kmc_handle {
     uint32_t n_keys = 0, n_tiles = 0;
     uint32_t id_bits = 32;
     uint32_t n_stage_tiles = 0;
-    int stage_cap = 0, stage_rows = 0, stage_stride = 0, any_direct = 1;
+    int stage_cap = 0, stage_rows = 0, stage_stride = 0, stage_pair_cap = 0, any_direct = 1;
     int64_t n_bins = 0, bins_per_inst = 0;
     int64_t bytes = 0;
     int mom_state = 0;  // 1: acc/mom/glob describe the current state
@@ -125,6 +125,7 @@ Bufs<T> make_bufs(const kmc_handle* h) {
     b.stage_cap = h->stage_cap;
     b.stage_rows = h->stage_rows;
     b.stage_stride = h->stage_stride;
+    b.stage_pair_cap = h->stage_pair_cap;
     b.any_direct = h->any_direct;
     b.id_bits = h->id_bits;
     b.id_mask = h->id_bits >= 32 ? 0xffffffffu : ((1u << h->id_bits) - 1u);
@@ -282,7 +283,7 @@ void plan_staged_search(kmc_handle* h, const std::vector<uint32_t>& max_occ) {
     const size_t vbytes = vec_size(h);
     const size_t budget = 160 * 1024;
     uint32_t tiles = 0;
-    int cap = 0, rows = 0, stride = 0, direct = 0;
+    int cap = 0, rows = 0, stride = 0, pcap = 0, direct = 0;
     for (int i = 0; i < h->n_inst; ++i) {
         InstDev& I = h->inst_h[i];
         I.staged = 0;
@@ -297,9 +298,14 @@ void plan_staged_search(kmc_handle* h, const std::vector<uint32_t>& max_occ) {
             R = std::max(1, std::min(R, I.M[1]));
             const int nxs = std::min(3, I.M[0]);
             const int rows_i = nxs * (R + 4);
-            const int cap_i = ((int)std::ceil(nxs * (R + 2) * ppr * 1.35) + 64 + 31) / 32 * 32;
-            const size_t bytes = (size_t)cap_i * 2 * vbytes + (size_t)rows_i * (I.M[2] + 1) * sizeof(uint32_t);
-            ok = I.s[0] == 1 && R + 4 < I.M[1] && rows_i <= 64 && bytes <= budget;
+            const int cap_i = ((int)std::ceil(nxs * (R + 2) * ppr * 1.3) + 64 + 31) / 32 * 32;
+            // pair list: home particles x candidates (27 search cells of the window)
+            const double cand = 27.0 * ppr / I.M[2];
+            const int pcap_i = h->precision == 32 ? ((int)std::ceil(R * ppr * cand * 1.5) + 512 + 31) / 32 * 32 : 0;
+            const size_t bytes = (size_t)cap_i * 2 * vbytes + (size_t)rows_i * (I.M[2] + 2) * sizeof(uint32_t) +
+                                 (size_t)pcap_i * 4 + 2 * kStageThreads * 12 + 4;
+            ok = I.s[0] == 1 && R + 4 < I.M[1] && rows_i <= 64 && bytes <= budget && cap_i < 65536 &&
+                 R * ppr * 1.3 < 2 * kStageThreads;
             if (ok) {
                 I.staged = 1;
                 I.tile_rows = R;
@@ -307,12 +313,14 @@ void plan_staged_search(kmc_handle* h, const std::vector<uint32_t>& max_occ) {
                 tiles += (uint32_t)(I.M[0] * I.tiles_per_x);
                 cap = std::max(cap, cap_i);
                 rows = std::max(rows, rows_i);
-                stride = std::max(stride, I.M[2] + 1);
+                stride = std::max(stride, (I.M[2] + 2) / 2 * 2);
+                pcap = std::max(pcap, pcap_i);
             }
         }
         if (!ok) direct = 1;
     }
-    const size_t total = (size_t)cap * 2 * vbytes + (size_t)rows * stride * sizeof(uint32_t);
+    const size_t total = (size_t)cap * 2 * vbytes + (size_t)rows * stride * sizeof(uint32_t) + (size_t)pcap * 4 +
+                         2 * kStageThreads * 12 + 4;
     if (tiles > 0 && total > budget) {   // instances disagree too much: search all directly
         for (auto& I : h->inst_h) I.staged = 0;
         tiles = 0;
@@ -322,6 +330,7 @@ void plan_staged_search(kmc_handle* h, const std::vector<uint32_t>& max_occ) {
     h->stage_cap = cap;
     h->stage_rows = rows;
     h->stage_stride = stride;
+    h->stage_pair_cap = pcap;
     h->any_direct = direct;
 }
 

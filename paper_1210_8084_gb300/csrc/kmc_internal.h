@@ -117,7 +117,8 @@ struct Bufs {
     uint32_t n_stage_tiles;  // tiles over all staged instances (0: none)
     int stage_cap;           // candidate vectors a tile can stage
     int stage_rows;          // row slots of the staged start table
-    int stage_stride;        // entries per row slot (max M[2] + 1)
+    int stage_stride;        // entries per row slot (max M[2] + 1, even)
+    int stage_pair_cap;      // entries of the binary32 pair list
     int any_direct;          // some instance uses the direct (per-thread) search
     // particle tag = (instance << id_bits) | instance-local id
     uint32_t id_bits;        // 32 when there is one instance

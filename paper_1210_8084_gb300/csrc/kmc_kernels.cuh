@@ -694,6 +694,189 @@ __device__ __noinline__ int32_t search_one_direct(const Bufs<T>& b, const GeoT<T
 // whose neighbourhood does not fit, or a particle whose window is not a plain
 // unwrapped window, takes the direct path.
 constexpr int kStageMaxRows = 64;
+constexpr int kStageMaxHome = 2 * kStageThreads;
+
+// Order-preserving 32-bit image of a binary32 distance (-0 folded into +0):
+// unsigned comparison of the images is the floating-point comparison.
+__device__ __forceinline__ uint32_t ordered_bits(float d2) {
+    const uint32_t u = __float_as_uint(d2 + 0.0f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// Ranges [q0, q1) (shared-memory indices) of one home particle's window
+// inside the staged rows; calls f(q0, q1) for each.  Returns false when the
+// window is not a plain unwrapped window inside the staged union.
+template <typename T, typename F>
+__device__ __forceinline__ bool for_each_staged_range(const GeoT<T>& G, const InstDev& I, const int* kk,
+                                                      const uint32_t* loc, int stride, int xlo, int nx, int ylo,
+                                                      int ny, const T xi[3], F&& f) {
+    int c[3], g[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) cell_and_search<T>(xi[d], G.lo[d], G.inv[d], G.n[d], I.s[d], c[d], g[d]);
+    Win w[3];
+    bool amb = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        w[d] = window_1d(g[d], c[d], I.s[d], I.M[d], kk[d], G.wall[d]);
+        amb = amb || w[d].amb;
+    }
+    if (amb || w[0].lo < xlo || w[0].hi >= xlo + nx || w[1].lo < ylo || w[1].hi >= ylo + ny) return false;
+    const int MZ = I.M[2];
+    int fa0 = w[2].lo, fb0 = w[2].hi, fa1 = 1, fb1 = 0;
+    if (w[2].lo < 0) { fa0 = w[2].lo + MZ; fb0 = MZ - 1; fa1 = 0; fb1 = w[2].hi; }
+    else if (w[2].hi >= MZ) { fb0 = MZ - 1; fa1 = 0; fb1 = w[2].hi - MZ; }
+    for (int tx = w[0].lo; tx <= w[0].hi; ++tx) {
+        for (int ty = w[1].lo; ty <= w[1].hi; ++ty) {
+            const uint32_t* lr = loc + ((tx - xlo) * ny + (ty - ylo)) * stride;
+            f((int)lr[fa0], (int)lr[fb0 + 1]);
+            if (fa1 <= fb1) f((int)lr[fa1], (int)lr[fb1 + 1]);
+        }
+    }
+    return true;
+}
+
+// Pair-list search over the staged rows (binary32).  Phase A: every home
+// particle writes its candidates as (home ordinal, staged index) entries at
+// its offset of a block-wide exclusive scan.  Phase B: the block tests the
+// entries round-robin, so every lane has work whatever the window sizes; a
+// passing candidate lowers the home particle's 64-bit key (ordered d2, tag)
+// with a shared-memory atomicMin, which keeps the smaller distance and, on a
+// tie, the lower id.  Phase C: each home particle finds the staged index of
+// the winning tag among its own entries.  Periodic images come from the
+// per-candidate minimum image, equal to the row image inside these windows.
+template <typename T>
+__device__ __noinline__ void staged_pairs(const Bufs<T>& b, const GeoT<T>& G, const InstDev& I, const int* kk,
+                                          const typename Vec4<T>::type* sp, const typename Vec4<T>::type* sv,
+                                          unsigned char* scratch, const int32_t* rowA0, const int32_t* rowL0,
+                                          int nr, int xlo, int nx, int ylo, int ny, int32_t h0, int32_t h1,
+                                          int stride, T dt, T R2) {
+    using V = typename Vec4<T>::type;
+    __shared__ int s_total;
+    __shared__ int s_warp[kStageThreads / 32];
+    unsigned long long* bkey = reinterpret_cast<unsigned long long*>(scratch);
+    int* hoff = reinterpret_cast<int*>(bkey + kStageMaxHome);            // [kStageMaxHome + 1]
+    uint32_t* pairs = reinterpret_cast<uint32_t*>(hoff + kStageMaxHome + 1);
+    const uint32_t* ltab = reinterpret_cast<const uint32_t*>(sv + b.stage_cap);
+    const int tid = threadIdx.x;
+    const int H = h1 - h0;
+    // home particles sit contiguously in the staged rows, in A order, from
+    // the staged row holding h0
+    int hbase = 0;
+    for (int r = 0; r < nr; ++r) {
+        if (rowA0[r] <= h0 && h0 < rowA0[r] + (rowL0[r + 1] - rowL0[r])) {
+            hbase = rowL0[r] + (h0 - rowA0[r]);
+            break;
+        }
+    }
+    const bool fits = H <= kStageMaxHome;
+    // phase A1: candidate counts
+    int cnt[2] = {0, 0};
+    bool direct[2] = {!fits, !fits};
+    if (fits) {
+        for (int k = 0; k < 2; ++k) {
+            const int i = tid + k * kStageThreads;
+            if (i >= H) break;
+            const V P = sp[hbase + i];
+            const T xi[3] = {P.x, P.y, P.z};
+            int c = 0;
+            const bool ok = for_each_staged_range<T>(G, I, kk, ltab, stride, xlo, nx, ylo, ny, xi,
+                                                     [&](int q0, int q1) { c += max(q1 - q0, 0); });
+            cnt[k] = ok ? c : 0;
+            direct[k] = !ok;
+        }
+    }
+    // block exclusive scan of the per-thread totals
+    int mine = cnt[0] + cnt[1];
+    int inc = mine;
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < kStageThreads / 32 ? s_warp[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < kStageThreads / 32) s_warp[lane] = wi - w;
+        if (lane == kStageThreads / 32 - 1) s_total = wi;
+    }
+    __syncthreads();
+    const int base = s_warp[warp] + inc - mine;
+    const bool list_ok = fits && s_total <= b.stage_pair_cap;
+    // phase A2: write the entries, reset the keys
+    if (list_ok) {
+        int off = base;
+        for (int k = 0; k < 2; ++k) {
+            const int i = tid + k * kStageThreads;
+            if (i >= H) break;
+            hoff[i] = off;
+            bkey[i] = ~0ull;
+            if (direct[k]) continue;
+            const V P = sp[hbase + i];
+            const T xi[3] = {P.x, P.y, P.z};
+            const uint32_t hi16 = (uint32_t)i << 16;
+            for_each_staged_range<T>(G, I, kk, ltab, stride, xlo, nx, ylo, ny, xi, [&](int q0, int q1) {
+                for (int q = q0; q < q1; ++q) pairs[off++] = hi16 | (uint32_t)q;
+            });
+        }
+        if (tid == 0) hoff[min(H, kStageMaxHome)] = s_total;
+    }
+    __syncthreads();
+    if (!list_ok) {   // too many entries for the list: direct search for the whole tile
+        for (int64_t p = h0 + tid; p < h1; p += blockDim.x) b.best[p] = search_one_direct<T, 3>(b, G, p);
+        return;
+    }
+    // phase B: balanced pair tests
+    const T sh0[3] = {(T)0, (T)0, (T)0};
+    for (int t = tid; t < s_total; t += blockDim.x) {
+        const uint32_t e = pairs[t];
+        const int i = (int)(e >> 16);
+        const int q = (int)(e & 0xffffu);
+        const V Pi = sp[hbase + i], Qi = sv[hbase + i];
+        const V Pj = sp[q], Qj = sv[q];
+        const T xi[3] = {Pi.x, Pi.y, Pi.z}, vi[3] = {Qi.x, Qi.y, Qi.z};
+        const T xj[3] = {Pj.x, Pj.y, Pj.z}, vj[3] = {Qj.x, Qj.y, Qj.z};
+        T d2;
+        if (poca_test_sh<T, 3, true>(G, xi, vi, xj, vj, sh0, dt, R2, d2)) {
+            const unsigned long long key = ((unsigned long long)ordered_bits((float)d2) << 32) |
+                                           (unsigned long long)R<T>::bits(Pj.w);
+            atomicMin(&bkey[i], key);
+        }
+    }
+    __syncthreads();
+    // phase C: staged index of the winning tag, back to a sorted position
+    for (int k = 0; k < 2; ++k) {
+        const int i = tid + k * kStageThreads;
+        if (i >= H) break;
+        const int64_t p = h0 + i;
+        if (direct[k]) {
+            b.best[p] = search_one_direct<T, 3>(b, G, p);
+            continue;
+        }
+        const unsigned long long key = bkey[i];
+        int32_t bq = -1;
+        if (key != ~0ull) {
+            const uint32_t tag = (uint32_t)key;
+            for (int t = hoff[i]; t < hoff[i + 1]; ++t) {
+                const int q = (int)(pairs[t] & 0xffffu);
+                if (R<T>::bits(sp[q].w) == tag) {
+                    int r = 0;
+                    while (r + 1 < nr && rowL0[r + 1] <= q) ++r;
+                    bq = rowA0[r] + (q - rowL0[r]);
+                    break;
+                }
+            }
+        }
+        b.best[p] = bq;
+    }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kStageThreads) search_staged_kernel(Bufs<T> b) {
@@ -791,86 +974,91 @@ __global__ void __launch_bounds__(kStageThreads) search_staged_kernel(Bufs<T> b)
 
     const int* kk = b.dyn[s_inst].k;
     const T dt = inst_dt(I, T()), R2 = inst_R2(I, T());
-    for (int64_t p = s_h0 + tid; p < s_h1; p += blockDim.x) {
-        const V P = b.posA[p];
-        const V Q = b.velA[p];
-        const T xi[3] = {P.x, P.y, P.z};
-        const T vi[3] = {Q.x, Q.y, Q.z};
-        int c[3], g[3];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) cell_and_search<T>(xi[d], G.lo[d], G.inv[d], G.n[d], I.s[d], c[d], g[d]);
-        Win w[3];
-        bool amb = false;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            w[d] = window_1d(g[d], c[d], I.s[d], I.M[d], kk[d], G.wall[d]);
-            amb = amb || w[d].amb;
-        }
-        if (amb || w[0].lo < s_xlo || w[0].hi >= s_xlo + s_nx || w[1].lo < s_ylo || w[1].hi >= s_ylo + s_ny) {
-            b.best[p] = search_one_direct<T, 3>(b, G, p);
-            continue;
-        }
-        // z parts of the window (z is the fastest key dimension)
-        const int MZ = I.M[2];
-        int fa[2], fb[2];
-        T fs[2] = {(T)0, (T)0};
-        int nf = 1;
-        if (w[2].lo < 0) {
-            fa[0] = w[2].lo + MZ; fb[0] = MZ - 1; fs[0] = G.L[2];
-            fa[1] = 0; fb[1] = w[2].hi;
-            nf = 2;
-        } else if (w[2].hi >= MZ) {
-            fa[0] = w[2].lo; fb[0] = MZ - 1;
-            fa[1] = 0; fb[1] = w[2].hi - MZ; fs[1] = -G.L[2];
-            nf = 2;
-        } else {
-            fa[0] = w[2].lo; fb[0] = w[2].hi;
-        }
-        T bd = R<T>::inf();
-        uint32_t bid = 0xffffffffu;
-        int32_t bq = -1;
-        int tx = w[0].lo, ty = w[1].lo, part = 0;
-        int32_t q = 0, qe = 0, off = 0;
-        T sh[3] = {(T)0, (T)0, (T)0};
-        for (;;) {
-            if (q >= qe) {
-                bool more = false;
-                while (tx <= w[0].hi) {
-                    T sx, sy;
-                    unwrap<T>(tx, I.M[0], G.L[0], sx);
-                    unwrap<T>(ty, I.M[1], G.L[1], sy);
-                    const int r = (tx - s_xlo) * s_ny + (ty - s_ylo);
-                    q = (int32_t)loc[r * stride + fa[part]];
-                    qe = (int32_t)loc[r * stride + fb[part] + 1];
-                    off = s_rowA0[r] - s_rowL0[r];
-                    sh[0] = sx;
-                    sh[1] = sy;
-                    sh[2] = part == 0 ? fs[0] : fs[1];
-                    if (++part == nf) {
-                        part = 0;
-                        if (++ty > w[1].hi) { ty = w[1].lo; ++tx; }
+    if constexpr (sizeof(T) == 4) {
+        staged_pairs(b, G, I, kk, sp, sv, reinterpret_cast<unsigned char*>(loc + (size_t)b.stage_rows * stride),
+                     s_rowA0, s_rowL0, nr, s_xlo, s_nx, s_ylo, s_ny, s_h0, s_h1, stride, dt, R2);
+    } else {
+        for (int64_t p = s_h0 + tid; p < s_h1; p += blockDim.x) {
+            const V P = b.posA[p];
+            const V Q = b.velA[p];
+            const T xi[3] = {P.x, P.y, P.z};
+            const T vi[3] = {Q.x, Q.y, Q.z};
+            int c[3], g[3];
+    #pragma unroll
+            for (int d = 0; d < 3; ++d) cell_and_search<T>(xi[d], G.lo[d], G.inv[d], G.n[d], I.s[d], c[d], g[d]);
+            Win w[3];
+            bool amb = false;
+    #pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                w[d] = window_1d(g[d], c[d], I.s[d], I.M[d], kk[d], G.wall[d]);
+                amb = amb || w[d].amb;
+            }
+            if (amb || w[0].lo < s_xlo || w[0].hi >= s_xlo + s_nx || w[1].lo < s_ylo || w[1].hi >= s_ylo + s_ny) {
+                b.best[p] = search_one_direct<T, 3>(b, G, p);
+                continue;
+            }
+            // z parts of the window (z is the fastest key dimension)
+            const int MZ = I.M[2];
+            int fa[2], fb[2];
+            T fs[2] = {(T)0, (T)0};
+            int nf = 1;
+            if (w[2].lo < 0) {
+                fa[0] = w[2].lo + MZ; fb[0] = MZ - 1; fs[0] = G.L[2];
+                fa[1] = 0; fb[1] = w[2].hi;
+                nf = 2;
+            } else if (w[2].hi >= MZ) {
+                fa[0] = w[2].lo; fb[0] = MZ - 1;
+                fa[1] = 0; fb[1] = w[2].hi - MZ; fs[1] = -G.L[2];
+                nf = 2;
+            } else {
+                fa[0] = w[2].lo; fb[0] = w[2].hi;
+            }
+            T bd = R<T>::inf();
+            uint32_t bid = 0xffffffffu;
+            int32_t bq = -1;
+            int tx = w[0].lo, ty = w[1].lo, part = 0;
+            int32_t q = 0, qe = 0, off = 0;
+            T sh[3] = {(T)0, (T)0, (T)0};
+            for (;;) {
+                if (q >= qe) {
+                    bool more = false;
+                    while (tx <= w[0].hi) {
+                        T sx, sy;
+                        unwrap<T>(tx, I.M[0], G.L[0], sx);
+                        unwrap<T>(ty, I.M[1], G.L[1], sy);
+                        const int r = (tx - s_xlo) * s_ny + (ty - s_ylo);
+                        q = (int32_t)loc[r * stride + fa[part]];
+                        qe = (int32_t)loc[r * stride + fb[part] + 1];
+                        off = s_rowA0[r] - s_rowL0[r];
+                        sh[0] = sx;
+                        sh[1] = sy;
+                        sh[2] = part == 0 ? fs[0] : fs[1];
+                        if (++part == nf) {
+                            part = 0;
+                            if (++ty > w[1].hi) { ty = w[1].lo; ++tx; }
+                        }
+                        if (q < qe) { more = true; break; }
                     }
-                    if (q < qe) { more = true; break; }
+                    if (!more) break;
                 }
-                if (!more) break;
-            }
-            const V Pj = sp[q];
-            const V Qj = sv[q];
-            const T xj[3] = {Pj.x, Pj.y, Pj.z};
-            const T vj[3] = {Qj.x, Qj.y, Qj.z};
-            T d2;
-            // the particle itself has v_rel = 0 and fails b > 0
-            if (poca_test_sh<T, 3, false>(G, xi, vi, xj, vj, sh, dt, R2, d2)) {
-                const uint32_t idj = R<T>::bits(Pj.w);
-                if (d2 < bd || (d2 == bd && idj < bid)) {
-                    bd = d2;
-                    bid = idj;
-                    bq = q + off;
+                const V Pj = sp[q];
+                const V Qj = sv[q];
+                const T xj[3] = {Pj.x, Pj.y, Pj.z};
+                const T vj[3] = {Qj.x, Qj.y, Qj.z};
+                T d2;
+                // the particle itself has v_rel = 0 and fails b > 0
+                if (poca_test_sh<T, 3, false>(G, xi, vi, xj, vj, sh, dt, R2, d2)) {
+                    const uint32_t idj = R<T>::bits(Pj.w);
+                    if (d2 < bd || (d2 == bd && idj < bid)) {
+                        bd = d2;
+                        bid = idj;
+                        bq = q + off;
+                    }
                 }
+                ++q;
             }
-            ++q;
+            b.best[p] = bq;
         }
-        b.best[p] = bq;
     }
 }
 
@@ -1160,8 +1348,11 @@ cudaError_t launch_bin_init(const Bufs<T>& b, cudaStream_t s) {
 
 template <typename T>
 size_t stage_smem_bytes(const Bufs<T>& b) {
-    return (size_t)b.stage_cap * 2 * sizeof(typename Vec4<T>::type) +
-           (size_t)b.stage_rows * (size_t)b.stage_stride * sizeof(uint32_t);
+    size_t bytes = (size_t)b.stage_cap * 2 * sizeof(typename Vec4<T>::type) +
+                   (size_t)b.stage_rows * (size_t)b.stage_stride * sizeof(uint32_t);
+    if (sizeof(T) == 4)   // pair list: keys, offsets, entries
+        bytes += (size_t)kStageMaxHome * 8 + (size_t)(kStageMaxHome + 1) * 4 + (size_t)b.stage_pair_cap * 4;
+    return bytes;
 }
 
 template <typename T>
