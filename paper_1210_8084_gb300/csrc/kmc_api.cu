@@ -234,7 +234,9 @@ void choose_subdivision(const kmc_handle* h, InstDev& I, double vmax, uint32_t m
     int nsub = 0;
     for (int d = 0; d < h->dim; ++d) {
         const double dx = h->geo.L[d] / h->geo.n[d];
-        const double Dp = D * 1.001 + 1e-5 * h->geo.L[d];
+        // cells 10% wider than the step-0 reach, so the window stays +-1 cell
+        // while v_max drifts up with the sampled Maxwell tail
+        const double Dp = 1.1 * (D * 1.001 + 1e-5 * h->geo.L[d]);
         double r = dx / Dp;
         if (!(r >= 1.0)) r = 1.0;
         if (r > 4096.0) r = 4096.0;
@@ -290,7 +292,7 @@ void plan_staged_search(kmc_handle* h, const std::vector<uint32_t>& max_occ) {
         I.tile_rows = 1;
         I.tiles_per_x = 1;
         I.tile_base = tiles;
-        bool ok = h->dim == 3 && I.n > 0 && !(h->cfg.flags & KMC_FLAG_DIRECT_SEARCH);
+        bool ok = h->dim == 3 && I.n > 0 && (h->cfg.flags & KMC_FLAG_STAGED_SEARCH);
         double ppr = 1.0;   // particles per y-row (all z) in the densest c-bins
         if (ok) {
             ppr = std::max(1.0, (double)max_occ[i] * h->geo.n[2] / ((double)I.s[0] * I.s[1]));
@@ -350,7 +352,7 @@ int validate_config(const kmc_config* c, int64_t n) {
     }
     if (c->n_instances < 0) return fail(nullptr, KMC_EINVAL, "n_instances < 0");
     if (c->n_instances > 1 && !c->instances) return fail(nullptr, KMC_EINVAL, "instances is NULL");
-    if (c->flags & ~(KMC_FLAG_RECORD | KMC_FLAG_NO_GRAPH | KMC_FLAG_DIRECT_SEARCH))
+    if (c->flags & ~(KMC_FLAG_RECORD | KMC_FLAG_NO_GRAPH | KMC_FLAG_STAGED_SEARCH))
         return fail(nullptr, KMC_EINVAL, "unknown flags");
     return KMC_OK;
 }

@@ -26,9 +26,9 @@ def _setup():
 
 
 def run_gpu_step(pos, vel, dim, n_cells, lo, hi, bc, lam, dt, seed, precision, step=0, sub_cells=(0, 0, 0),
-                 nsteps=1, direct=False, occ=0.0):
+                 nsteps=1, staged=False, occ=0.0):
     import paper_1210_8084_gb300 as k
-    flags = k.KMC_FLAG_RECORD | (k.KMC_FLAG_DIRECT_SEARCH if direct else 0)
+    flags = k.KMC_FLAG_RECORD | (k.KMC_FLAG_STAGED_SEARCH if staged else 0)
     cfg = k.make_config(dim_pos=dim, n_cells=n_cells, lo=lo, hi=hi, bc=bc, lam=lam, dt=dt, seed=seed,
                         precision=precision, flags=flags, sub_cells=sub_cells, occupancy_target=occ)
     sim = k.Simulation(cfg, pos, vel)
@@ -109,18 +109,18 @@ def make_inputs(name, n, dim, lo, hi):
     return pos, vel
 
 
-@pytest.mark.parametrize("direct", [False, True], ids=["auto", "direct"])
+@pytest.mark.parametrize("staged", [False, True], ids=["direct", "staged"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_one_step_parity(case, direct):
-    """One step from the same state; the automatic search (shared-memory
-    staged tiles where they fit) and the direct search must both match."""
+def test_one_step_parity(case, staged):
+    """One step from the same state; the direct search and the shared-memory
+    staged search (3-D tiles where they fit) must both match."""
     _setup()
     name, n, dim, n_cells, lo, hi, bc, lam, dt, prec = case
     pos, vel = make_inputs(name, n, dim, lo, hi)
     if prec == 32:
         pos, vel = f32_state(pos, vel, lo, hi, bc)
     seed = 11
-    g = run_gpu_step(pos, vel, dim, n_cells, lo, hi, bc, lam, dt, seed, prec, direct=direct)
+    g = run_gpu_step(pos, vel, dim, n_cells, lo, hi, bc, lam, dt, seed, prec, staged=staged)
     o = oracle_step(pos, vel, dim, n_cells, lo, hi, bc, g["info"].R2, dt, seed, 0, prec == 32)
     assert (g["best"] >= 0).mean() > 0.02 or lam >= 1.0
     compare_step(g, o, prec, pos, vel, dim)
