@@ -187,6 +187,36 @@ KMC_API int kmc_get_cell_keys(kmc_handle* h, int32_t* keys, int where);
  * last step (mutually closest), -1 if none.  Either pointer may be NULL. */
 KMC_API int kmc_get_partners(kmc_handle* h, int32_t* best, int32_t* partner, int where);
 
+/* Closest-candidate search without any allocation.  The paper has no
+ * counterpart: this entry point exists for callers that may not allocate
+ * device memory themselves or through this library, e.g. a host framework
+ * that owns all device memory through its own pool, code under a fixed
+ * device-memory budget, or a loop where cudaMalloc's implicit device
+ * synchronisation is not acceptable.  It computes, for one state, the
+ * same closest candidate per particle (criteria 1-3) as the first step of a
+ * kmc_init handle, writing best[id] = instance-local id of the candidate or -1.
+ *
+ * cfg: single instance only (n_instances <= 1; lambda/sigma, dt, box, cells,
+ * walls, precision used; sub_cells > 0 selects the search subdivision, 0 means
+ * plain c-bins; stream as in kmc_init, NULL = legacy default stream).
+ * pos, vel: device arrays n x 3 of float/double per cfg.precision; best:
+ * device int32[n].  All scratch (packed state, keys, histogram, scan tiles)
+ * lives in one file-scope __device__ array of KMC_STATIC_SCRATCH_BYTES that
+ * every GPU loading the library holds until exit; n above
+ * KMC_STATIC_MAX_PARTICLES or a search grid above KMC_STATIC_MAX_CELLS gives
+ * KMC_ERANGE.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Calls share the array and keep the last call's
+ * contents: calls whose work overlaps on the GPU race, so issue them in order
+ * on one stream.  Asynchronous on the stream; returns KMC_EINVAL / KMC_ERANGE /
+ * KMC_ECUDA for argument, size or launch errors.  Validity of the particles is
+ * not checked (unlike kmc_init). */
+#define KMC_STATIC_MAX_PARTICLES 262144
+#define KMC_STATIC_MAX_CELLS 1048576
+#define KMC_STATIC_SCRATCH_BYTES (48u << 20)
+KMC_API int kmc_find_partners_noalloc(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
+                                      int32_t* best);
+
 #ifdef __cplusplus
 }
 #endif

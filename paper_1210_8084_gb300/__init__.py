@@ -40,8 +40,9 @@ PHASES = ("search", "move", "scan", "scatter", "moments", "finalize")
 ABI_FUNCTIONS = (
     "kmc_init", "kmc_step", "kmc_moments", "kmc_moments_size", "kmc_free", "kmc_sync",
     "kmc_last_error", "kmc_get_info", "kmc_get_state", "kmc_set_state", "kmc_get_cell_keys",
-    "kmc_get_partners", "kmc_step_profiled",
+    "kmc_get_partners", "kmc_step_profiled", "kmc_find_partners_noalloc",
 )
+KMC_STATIC_MAX_PARTICLES = 262144
 
 
 class KmcInstance(ctypes.Structure):
@@ -136,6 +137,8 @@ def _load():
     L.kmc_get_partners.restype = ctypes.c_int
     L.kmc_step_profiled.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     L.kmc_step_profiled.restype = ctypes.c_int
+    L.kmc_find_partners_noalloc.argtypes = [ctypes.POINTER(KmcConfig), ctypes.c_int64, vp, vp, vp]
+    L.kmc_find_partners_noalloc.restype = ctypes.c_int
     return L
 
 
@@ -227,6 +230,13 @@ def kmc_step_profiled(h, nsteps=1, want_moments=1):
     out = {name: ms[i] for i, name in enumerate(PHASES)}
     out["total"] = ms[KMC_NPHASES]
     return out
+
+
+def kmc_find_partners_noalloc(cfg, n, pos, vel, best):
+    """Closest candidate of every particle of a device-resident state, with no
+    allocation (scratch in the library's fixed device array).  pos, vel, best
+    are device arrays; returns the C status code (KMC_OK on success)."""
+    return int(lib.kmc_find_partners_noalloc(ctypes.byref(cfg), int(n), _ptr(pos), _ptr(vel), _ptr(best)))
 
 
 def kmc_moments_size(h, fields_mask):

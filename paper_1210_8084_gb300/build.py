@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libkmc.so")
-SOURCES = ["kmc_api.cu", "kmc_scan.cu", "kmc_f32.cu", "kmc_f64.cu"]
+SOURCES = ["kmc_api.cu", "kmc_scan.cu", "kmc_f32.cu", "kmc_f64.cu", "kmc_noalloc.cu"]
 HEADERS = ["kmc_internal.h", "kmc_kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
