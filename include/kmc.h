@@ -91,7 +91,7 @@ typedef struct kmc_config {
     const kmc_instance* instances; /* n_instances entries when batched; read during kmc_init only */
     void* stream;       /* cudaStream_t; NULL = a stream owned by the handle */
     int sub_cells[3];   /* search-grid subdivision of each c-bin per dimension; 0 = automatic */
-    double occupancy_target; /* automatic subdivision: particles per search cell aimed at (0 = 2.0) */
+    double occupancy_target; /* automatic subdivision: particles per search cell aimed at (0 = 0.5) */
     int flags;          /* KMC_FLAG_* */
 } kmc_config;
 

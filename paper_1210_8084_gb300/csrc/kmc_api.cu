@@ -244,7 +244,7 @@ void choose_subdivision(const kmc_handle* h, InstDev& I, double vmax, uint32_t m
         if (smax[d] >= 2) ++nsub;
     }
     int s[3] = {1, 1, 1};
-    const double target = h->cfg.occupancy_target > 0 ? h->cfg.occupancy_target : 2.0;
+    const double target = h->cfg.occupancy_target > 0 ? h->cfg.occupancy_target : 0.5;
     if (nsub > 0 && max_bin_occ > 0) {
         const double m = (double)max_bin_occ / target;  // search cells wanted per c-bin
         const double per_dim = pow(m > 1.0 ? m : 1.0, 1.0 / nsub);
