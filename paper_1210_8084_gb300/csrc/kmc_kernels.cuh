@@ -537,7 +537,6 @@ template <typename T, int DIM, bool MINIMG>
 __device__ __forceinline__ void scan_window(const Bufs<T>& b, const GeoT<T>& G, const InstDev& I, const Win w[3],
                                             const T xi[3], const T vi[3], T dt, T R2, T& bd, uint32_t& bid,
                                             int32_t& bq) {
-    using V = typename Vec4<T>::type;
     constexpr int F = DIM - 1;   // fast (contiguous) dimension
     const int MF = I.M[F];
     const uint32_t nmax = (uint32_t)b.n;
@@ -584,47 +583,15 @@ __device__ __forceinline__ void scan_window(const Bufs<T>& b, const GeoT<T>& G, 
                 q1[r] = (int32_t)min(b.start[row + (uint32_t)fb[0] + 1u], nmax);
             }
         }
-        // Walk the row ranges as one flat sequence per thread: the ranges sit in
-        // registers and move down one slot whenever the current one is used
-        // up, so a lane with short rows goes on to its next row instead of
-        // waiting for the longest row of the warp.
-        int r = 0;
-        int32_t q = q0[0], qe = q1[0];
-        T sh[3];
-        sh[0] = sx[0];
-        sh[1] = (DIM == 3) ? sy[0] : fs[0];
-        sh[2] = fs[0];
-        for (;;) {
-            while (q >= qe) {
-                if (++r >= NR) break;
 #pragma unroll
-                for (int k = 0; k < NR - 1; ++k) {
-                    q0[k] = q0[k + 1];
-                    q1[k] = q1[k + 1];
-                }
-                q = q0[0];
-                qe = q1[0];
-                const int ix = (DIM == 3) ? r / 3 : r;
-                const int iy = (DIM == 3) ? r - 3 * ix : 0;
-                sh[0] = ix == 0 ? sx[0] : (ix == 1 ? sx[1] : sx[2]);
-                if (DIM == 3) sh[1] = iy == 0 ? sy[0] : (iy == 1 ? sy[1] : sy[2]);
-            }
-            if (r >= NR) break;
-            const V Pj = ldg_vec(b.posA + q);
-            const V Qj = ldg_vec(b.velA + q);
-            const T xj[3] = {Pj.x, Pj.y, Pj.z};
-            const T vj[3] = {Qj.x, Qj.y, Qj.z};
-            T d2;
-            // the particle itself has v_rel = 0 and fails b > 0
-            if (poca_test_sh<T, DIM, MINIMG>(G, xi, vi, xj, vj, sh, dt, R2, d2)) {
-                const uint32_t idj = R<T>::bits(Pj.w);
-                if (d2 < bd || (d2 == bd && idj < bid)) {
-                    bd = d2;
-                    bid = idj;
-                    bq = q;
-                }
-            }
-            ++q;
+        for (int r = 0; r < NR; ++r) {
+            const int ix = (DIM == 3) ? r / 3 : r;
+            const int iy = (DIM == 3) ? r % 3 : 0;
+            T sh[3];
+            sh[0] = sx[ix];
+            sh[1] = (DIM == 3) ? sy[iy] : fs[0];
+            sh[2] = fs[0];
+            scan_range<T, DIM, MINIMG>(b, G, q0[r], q1[r], sh, xi, vi, dt, R2, bd, bid, bq);
         }
         return;
     }
