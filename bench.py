@@ -96,6 +96,30 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+FLOPS_PER_TEST = 25          # binary32 operations per candidate test
+FP32_LANES = 152 * 128       # GB300: SMs x FP32 lanes per SM
+B_ALG_F32 = 72               # algorithmic bytes per particle-step (binary32 state)
+
+
+def profiled_traffic(kernel):
+    """dram bytes per launch of `kernel` from the committed ncu summary, if that
+    summary was taken on the current kernel source (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel}_kernel_sod1d_16M.md")
+    src = os.path.join(ROOT, "paper_1210_8084_gb300", "csrc", "kmc_kernels.cuh")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    fields = dict(ln.split(":", 1) for ln in text.splitlines() if ln.startswith(("source_sha256:", "traffic_bytes_per_launch:")))
+    if fields.get("source_sha256", "").strip() != sha:
+        return None
+    try:
+        return int(fields["traffic_bytes_per_launch"].strip())
+    except (KeyError, ValueError):
+        return None
+
+
 def algorithmic_bytes(n, n_keys, n_bins, frac_paired, phase):
     """Bytes each kernel must move at least (binary32 state), per launch.
     State of a particle: position 12 B + id 4 B, velocity 12 B + instance 4 B."""
@@ -151,6 +175,7 @@ def ours(args):
     # ---------------- device-resident throughput (inputs already in HBM)
     sim = k.Simulation(cfg, pos, vel)
     info = sim.info()
+    e_start = sim.moments()[2][0, 1]
     sim.step_profiled(args.warmup, want_moments=1)
     clocks = ClockSampler(local)
     barrier()
@@ -168,6 +193,8 @@ def ours(args):
     raw, der, glob = sim.moments()
     pairs = float(glob[0, 6])
     frac_paired = 2 * pairs / n
+    energy_drift = float(glob[0, 1] / e_start - 1.0)
+    cand = sim.window_size()
     sim.close()
 
     # ---------------- end to end through the C ABI with host buffers
@@ -204,12 +231,32 @@ def ours(args):
     peaks, peak_src = measured_peaks()
     phases = {p: prof[p] / args.steps for p in ("search", "move", "scan", "scatter", "moments", "finalize")}
     dom = max(("search", "move", "scan", "scatter", "moments"), key=lambda p: phases[p])
-    ab = algorithmic_bytes(n, info.n_search_cells, info.n_bins, frac_paired, dom)
-    achieved = ab / (phases[dom] * 1e-3) / 1e9
-    peak = float(peaks.get("hbm_gbs", 6800.0))
-    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_src,
-            "ms_per_launch": round(phases[dom], 4), "algorithmic_bytes_per_launch": int(ab)}
+    t_dom = phases[dom] * 1e-3
+    traffic = profiled_traffic(dom)
+    if dom == "search":
+        # arithmetic-bound: 25 binary32 operations per candidate test (PoCA test
+        # with its early outs), C_p candidates examined per particle
+        flops = FLOPS_PER_TEST * cand * n
+        sm_clock = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        peak = FP32_LANES * 2 * sm_clock / 1e12
+        achieved = flops / t_dom / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": "fp32 lanes x 2 x max SM clock (derived)", "ms_per_launch": round(phases[dom], 4),
+                "algorithmic_flops_per_launch": int(flops), "candidates_per_particle": round(cand, 3)}
+    else:
+        ab = algorithmic_bytes(n, info.n_search_cells, info.n_bins, frac_paired, dom)
+        achieved = ab / t_dom / 1e9
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": f"{peak_src} hbm_gbs", "ms_per_launch": round(phases[dom], 4),
+                "algorithmic_bytes_per_launch": int(ab)}
+    step_bytes = B_ALG_F32 * n
+    step_hbm = {"algorithmic_bytes_per_step": int(step_bytes),
+                "achieved_gbs": round(step_bytes / (elapsed_ms / args.steps * 1e-3) / 1e9, 1),
+                "frac_of_measured_hbm": round(step_bytes / (elapsed_ms / args.steps * 1e-3) / 1e9 /
+                                              float(peaks.get("hbm_gbs", 6800.0)), 4)}
     value = n * world * args.steps / (elapsed_ms * 1e-3)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -225,6 +272,8 @@ def ours(args):
         "phase_ms_per_step": {p: round(v, 4) for p, v in phases.items()},
         "collision_fraction": round(frac_paired, 4),
         "roofline": roof,
+        "step_hbm": step_hbm,
+        "energy_drift_rel": energy_drift,
         "e2e": e2e,
         "gpu_launches": 7 * args.steps,
         "clocks": clk,

@@ -95,6 +95,11 @@ typedef struct kmc_config {
     int flags;          /* KMC_FLAG_* */
 } kmc_config;
 
+/* Mean number of candidates a particle of the current state examines in the
+ * search (the size of its search window; the paper's 3^D c-bin neighbourhood
+ * restricted to the search cells that can hold a candidate).  Synchronises. */
+KMC_API int kmc_window_size(kmc_handle* h, double* mean_candidates);
+
 /* Read-only description of a handle (kmc_get_info). */
 typedef struct kmc_info {
     int64_t n_particles;     /* total over instances */

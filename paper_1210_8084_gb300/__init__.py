@@ -40,7 +40,7 @@ PHASES = ("search", "move", "scan", "scatter", "moments", "finalize")
 ABI_FUNCTIONS = (
     "kmc_init", "kmc_step", "kmc_moments", "kmc_moments_size", "kmc_free", "kmc_sync",
     "kmc_last_error", "kmc_get_info", "kmc_get_state", "kmc_set_state", "kmc_get_cell_keys",
-    "kmc_get_partners", "kmc_step_profiled", "kmc_find_partners_noalloc",
+    "kmc_get_partners", "kmc_step_profiled", "kmc_find_partners_noalloc", "kmc_window_size",
 )
 KMC_STATIC_MAX_PARTICLES = 262144
 
@@ -137,6 +137,8 @@ def _load():
     L.kmc_get_partners.restype = ctypes.c_int
     L.kmc_step_profiled.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     L.kmc_step_profiled.restype = ctypes.c_int
+    L.kmc_window_size.argtypes = [H, ctypes.POINTER(ctypes.c_double)]
+    L.kmc_window_size.restype = ctypes.c_int
     L.kmc_find_partners_noalloc.argtypes = [ctypes.POINTER(KmcConfig), ctypes.c_int64, vp, vp, vp]
     L.kmc_find_partners_noalloc.restype = ctypes.c_int
     return L
@@ -232,6 +234,13 @@ def kmc_step_profiled(h, nsteps=1, want_moments=1):
     return out
 
 
+def kmc_window_size(h):
+    """Mean candidates examined per particle by the search of the current state."""
+    v = ctypes.c_double()
+    _check(lib.kmc_window_size(h, ctypes.byref(v)), h)
+    return v.value
+
+
 def kmc_find_partners_noalloc(cfg, n, pos, vel, best):
     """Closest candidate of every particle of a device-resident state, with no
     allocation (scratch in the library's fixed device array).  pos, vel, best
@@ -320,6 +329,9 @@ class Simulation:
 
     def info(self):
         return kmc_get_info(self.h)
+
+    def window_size(self):
+        return kmc_window_size(self.h)
 
     def state(self):
         pos = np.zeros((self.n, 3), dtype=self.dtype)

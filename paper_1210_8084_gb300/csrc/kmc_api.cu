@@ -767,6 +767,23 @@ int kmc_get_info(kmc_handle* h, kmc_info* info) {
     return KMC_OK;
 }
 
+int kmc_window_size(kmc_handle* h, double* mean_candidates) {
+    if (!h || !mean_candidates) return fail(h, KMC_EINVAL, "NULL argument");
+    *mean_candidates = 0.0;
+    if (h->n == 0) return KMC_OK;
+    // the scan-status words are free between steps: use one as the counter
+    unsigned long long* total = h->scan_status;
+    KMC_CUDA(h, cudaMemsetAsync(total, 0, sizeof(unsigned long long), h->stream));
+    cudaError_t e = h->precision == 64 ? launch_window_count<double>(make_bufs<double>(h), total, h->stream)
+                                       : launch_window_count<float>(make_bufs<float>(h), total, h->stream);
+    KMC_CUDA(h, e);
+    unsigned long long t = 0;
+    KMC_CUDA(h, cudaMemcpyAsync(&t, total, sizeof(t), cudaMemcpyDeviceToHost, h->stream));
+    KMC_CUDA(h, cudaStreamSynchronize(h->stream));
+    *mean_candidates = (double)t / (double)h->n;
+    return KMC_OK;
+}
+
 int kmc_get_state(kmc_handle* h, void* pos, void* vel, int where) {
     if (!h) return fail(nullptr, KMC_EINVAL, "handle is NULL");
     if (where != KMC_WHERE_HOST && where != KMC_WHERE_DEVICE) return fail(h, KMC_EINVAL, "bad where");

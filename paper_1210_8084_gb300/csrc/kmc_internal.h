@@ -147,6 +147,8 @@ cudaError_t launch_cell_keys(const Bufs<T>& b, int32_t* keys, cudaStream_t s);
 template <typename T>
 cudaError_t launch_moments(const Bufs<T>& b, int use_virial, cudaStream_t s);
 template <typename T>
+cudaError_t launch_window_count(const Bufs<T>& b, unsigned long long* total, cudaStream_t s);
+template <typename T>
 cudaError_t launch_cbin_hist(const Bufs<T>& b, uint32_t* hist, unsigned long long* vmax2, cudaStream_t s);
 
 // precision-independent

@@ -619,7 +619,7 @@ __device__ __forceinline__ void scan_window(const Bufs<T>& b, const GeoT<T>& G, 
 // neighbourhood, restricted to the search cells that can hold a candidate).
 // One thread per particle in sorted order; candidates are read through L1.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kThreads) search_kernel(Bufs<T> b) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) search_kernel(Bufs<T> b) {
     using V = typename Vec4<T>::type;
     __shared__ GeoT<T> G;
     if (threadIdx.x == 0) G.load(b.geo);
@@ -1283,6 +1283,50 @@ __global__ void __launch_bounds__(kThreads) moments_kernel(Bufs<T> b, int use_vi
     block_moment_partials<T>(S, b.acc, cnt > 0, cur, f, cnt, coll);
 }
 
+// Candidates each particle of A examines (the sizes of its search window), summed
+// over the particles: a diagnostic for the arithmetic roofline of the search.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kThreads) window_count_kernel(Bufs<T> b, unsigned long long* total) {
+    using V = typename Vec4<T>::type;
+    __shared__ GeoT<T> G;
+    if (threadIdx.x == 0) G.load(b.geo);
+    __syncthreads();
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long cnt = 0;
+    if (p < b.n) {
+        const V P = b.posA[p];
+        const int inst = tag_inst(b, R<T>::bits(P.w));
+        const InstDev& I = b.inst[inst];
+        const int* kk = b.dyn[inst].k;
+        const T xi[3] = {P.x, P.y, P.z};
+        int c[3] = {0, 0, 0}, g[3] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) cell_and_search<T>(xi[d], G.lo[d], G.inv[d], G.n[d], I.s[d], c[d], g[d]);
+        Win w[3] = {{0, 0, false}, {0, 0, false}, {0, 0, false}};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) w[d] = window_1d(g[d], c[d], I.s[d], I.M[d], kk[d], G.wall[d]);
+        constexpr int F = DIM - 1;
+        const int MF = I.M[F];
+        const uint32_t My = (DIM == 3) ? (uint32_t)I.M[1] : 1u, Mf = (uint32_t)MF;
+        for (int tx = w[0].lo; tx <= w[0].hi; ++tx) {
+            T s0;
+            const int gx = unwrap<T>(tx, I.M[0], G.L[0], s0);
+            for (int ty = (DIM == 3 ? w[1].lo : 0); ty <= (DIM == 3 ? w[1].hi : 0); ++ty) {
+                T s1;
+                const int gy = (DIM == 3) ? unwrap<T>(ty, I.M[1], G.L[1], s1) : 0;
+                const uint32_t row = I.key_base + ((uint32_t)gx * My + (uint32_t)gy) * Mf;
+                for (int tz = w[F].lo; tz <= w[F].hi; ++tz) {
+                    T s2;
+                    const int gz = unwrap<T>(tz, MF, G.L[F], s2);
+                    cnt += b.start[row + (uint32_t)gz + 1u] - b.start[row + (uint32_t)gz];
+                }
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(kFull, cnt, o);
+    if (lane_id() == 0 && cnt) atomicAdd(total, cnt);
+}
+
 // Particles per c-bin and largest |v|^2 per instance of the packed state in B
 // (statistics for the host's choice of search grid at init).
 template <typename T, int DIM>
@@ -1418,6 +1462,13 @@ cudaError_t launch_cbin_hist(const Bufs<T>& b, uint32_t* hist, unsigned long lon
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_window_count(const Bufs<T>& b, unsigned long long* total, cudaStream_t s) {
+    if (b.n == 0) return cudaSuccess;
+    KMC_DIM_DISPATCH(b.geo.dim, window_count_kernel, b, total);
+    return cudaGetLastError();
+}
+
 #define KMC_INSTANTIATE(T)                                                                        \
     template cudaError_t launch_pack<T>(const Bufs<T>&, const T*, const T*, uint32_t*, cudaStream_t); \
     template cudaError_t launch_bin_init<T>(const Bufs<T>&, cudaStream_t);                         \
@@ -1429,6 +1480,7 @@ cudaError_t launch_cbin_hist(const Bufs<T>& b, uint32_t* hist, unsigned long lon
     template cudaError_t launch_gather_state<T>(const Bufs<T>&, T*, T*, cudaStream_t);             \
     template cudaError_t launch_cell_keys<T>(const Bufs<T>&, int32_t*, cudaStream_t);              \
     template cudaError_t launch_moments<T>(const Bufs<T>&, int, cudaStream_t);                     \
-    template cudaError_t launch_cbin_hist<T>(const Bufs<T>&, uint32_t*, unsigned long long*, cudaStream_t);
+    template cudaError_t launch_cbin_hist<T>(const Bufs<T>&, uint32_t*, unsigned long long*, cudaStream_t); \
+    template cudaError_t launch_window_count<T>(const Bufs<T>&, unsigned long long*, cudaStream_t);
 
 }  // namespace kmc
