@@ -1,6 +1,11 @@
 """Physics of the device path over full runs.
 
-* Sod shock tube at 16M particles (2000 c-bins, lambda/L = 1e-3, t = 0.1):
+* Sod shock tube in the paper's geometry (Sect. "Sod test": cubic c-bins,
+  about 20 particles per c-bin): 1024 x 32 x 32 c-bins over 1 x 1/32 x 1/32,
+  21M particles, lambda/L = 1e-3, t = 0.1.  Relative L1 distance of n, p, T to
+  the exact Riemann solution (gamma = 5/3) within 2 %; the star state (the
+  plateau between rarefaction and contact) within 2 %.
+* Sod shock tube with slab c-bins at 16M particles (2000 c-bins, lambda/L = 1e-3, t = 0.1):
   relative L1 distance of n, p, T to the exact Riemann solution (Sect. "Sod
   test"; gamma = 5/3).  Measured 3.4 %, 4.0 %, 4.9 % (the 2 % aimed at is not
   reached: with one c-bin across y and z the candidates of a particle lie
@@ -40,6 +45,50 @@ def _profiles(raw, nb, n_left_density):
     T = c2 / 3.0
     dens = N * nb
     return dens / n_left_density, u, dens * T / n_left_density, T
+
+
+def _profiles_x(raw, ncx, nb, n_left_density):
+    """As _profiles, after summing c-bins over y and z (c-bin rows are x fastest)."""
+    rx = raw.reshape(raw.shape[0] // ncx, ncx, 8).sum(0)
+    return _profiles(rx, nb, n_left_density)
+
+
+def test_sod_3d_cubic_bins_within_two_percent():
+    _setup()
+    import paper_1210_8084_gb300 as k
+    from paper_1210_8084_gb300 import inputs
+    from oracle import riemann
+    ncx, ppc, steps = 1024, 20, 512
+    n_cells = (ncx, 32, 32)
+    hi = (1.0, 1 / 32, 1 / 32)
+    n = ppc * ncx * 32 * 32
+    dt = 0.2 / ncx
+    bc = (WALL, PER, PER)
+    pos, vel = inputs.sod_tube(n, seed=5, hi=hi)
+    pos, vel = inputs.cast_state(pos, vel, np.float32, (0, 0, 0), hi, bc)
+    sim = k.Simulation(k.make_config(dim_pos=3, n_cells=n_cells, hi=hi, bc=bc, lam=1e-3, dt=dt, seed=5,
+                                     precision=32), pos, vel)
+    e0 = sim.moments()[2][0, 1]
+    sim.step(steps, want_moments=1)
+    raw, der, glob = sim.moments()
+    sim.close()
+    t = steps * dt
+    nb = 256
+    n_l = n * 8 / 9 / 0.5
+    dn, u, p, T = _profiles_x(raw, ncx, nb, n_l)
+    ex = riemann.sod_profile(np.linspace(0, 1, nb + 1), t, 0.5, 1.0, 1.0)
+    l1 = {name: float(np.abs(q - qe).sum() / np.abs(qe).sum())
+          for name, q, qe in (("n", dn, ex[:, 0]), ("u", u, ex[:, 1]), ("p", p, ex[:, 2]), ("T", T, ex[:, 3]))}
+    print("Sod (cubic c-bins) L1:", l1)
+    assert l1["n"] <= 0.02 and l1["p"] <= 0.02 and l1["T"] <= 0.02, l1
+    assert l1["u"] <= 0.08, l1
+    # star state on the left of the contact: x in [0.51, 0.54]
+    xc = (np.arange(nb) + 0.5) / nb
+    star = (xc > 0.51) & (xc < 0.54)
+    for q, qe in ((dn, ex[:, 0]), (u, ex[:, 1]), (p, ex[:, 2]), (T, ex[:, 3])):
+        assert abs(q[star].mean() / qe[star].mean() - 1) < 0.02
+    assert abs(glob[0, 1] / e0 - 1) < 1e-6
+    assert glob[0, 0] == n
 
 
 def test_sod_tube_l1_against_exact_riemann():
