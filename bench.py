@@ -97,6 +97,12 @@ class ClockSampler:
 
 
 FLOPS_PER_TEST = 25          # binary32 operations per candidate test
+
+
+def kernels_per_step(precision):
+    """Kernels of one step with moments: search, move, scan, scatter, moments,
+    two finalize kernels."""
+    return 7
 FP32_LANES = 152 * 128       # GB300: SMs x FP32 lanes per SM
 B_ALG_F32 = 72               # algorithmic bytes per particle-step (binary32 state)
 
@@ -234,16 +240,20 @@ def ours(args):
     t_dom = phases[dom] * 1e-3
     traffic = profiled_traffic(dom)
     if dom == "search":
-        # arithmetic-bound: 25 binary32 operations per candidate test (PoCA test
-        # with its early outs), C_p candidates examined per particle
-        flops = FLOPS_PER_TEST * cand * n
+        # arithmetic-bound: 25 binary32 operations per pair test (PoCA test with
+        # its early outs).  The window of a particle holds C_p candidates (itself
+        # included); binary32 tests every unordered pair once, (C_p - 1) / 2 per
+        # particle, binary64 tests all C_p.
+        tests = (cand - 1.0) / 2.0 if w["precision"] == 32 else cand
+        flops = FLOPS_PER_TEST * tests * n
         sm_clock = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
         peak = FP32_LANES * 2 * sm_clock / 1e12
         achieved = flops / t_dom / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": "fp32 lanes x 2 x max SM clock (derived)", "ms_per_launch": round(phases[dom], 4),
-                "algorithmic_flops_per_launch": int(flops), "candidates_per_particle": round(cand, 3)}
+                "algorithmic_flops_per_launch": int(flops), "candidates_per_particle": round(cand, 3),
+                "pair_tests_per_particle": round(tests, 3)}
     else:
         ab = algorithmic_bytes(n, info.n_search_cells, info.n_bins, frac_paired, dom)
         achieved = ab / t_dom / 1e9
@@ -275,7 +285,7 @@ def ours(args):
         "step_hbm": step_hbm,
         "energy_drift_rel": energy_drift,
         "e2e": e2e,
-        "gpu_launches": 7 * args.steps,
+        "gpu_launches": kernels_per_step(w["precision"]) * args.steps,
         "clocks": clk,
     }
     if not args.no_cpu_baseline and world == 1:
@@ -360,7 +370,7 @@ def batched(args):
         "batched_vs_plain": {"batched": value, "plain_sequential": plain, "speedup": value / plain,
                              "ms_per_step_plain": ms_plain / args.steps,
                              "l1_error": "identical (per-instance states bit-identical)"},
-        "gpu_launches": 7 * args.steps,
+        "gpu_launches": kernels_per_step(w["precision"]) * args.steps,
         "clocks": clk,
     }
 

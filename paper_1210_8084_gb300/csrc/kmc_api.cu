@@ -38,7 +38,8 @@ struct kmc_handle {
     // device memory
     std::vector<DevBuf> allocs;
     void *posA = nullptr, *velA = nullptr, *posB = nullptr, *velB = nullptr;
-    int32_t* best = nullptr;
+    unsigned long long* bkey = nullptr;
+    uint32_t* slot_of = nullptr;
     uint32_t *key = nullptr, *slot = nullptr, *count = nullptr, *start = nullptr, *bad = nullptr;
     unsigned long long* scan_status = nullptr;
     InstDev* inst_d = nullptr;
@@ -106,7 +107,8 @@ Bufs<T> make_bufs(const kmc_handle* h) {
     b.velA = (V*)h->velA;
     b.posB = (V*)h->posB;
     b.velB = (V*)h->velB;
-    b.best = h->best;
+    b.bkey = h->bkey;
+    b.slot_of = h->slot_of;
     b.key = h->key;
     b.slot = h->slot;
     b.count = h->count;
@@ -510,7 +512,8 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
     if ((rc = dev_alloc(h, &h->velA, nv * vec_size(h)))) return bail(rc);
     if ((rc = dev_alloc(h, &h->posB, nv * vec_size(h)))) return bail(rc);
     if ((rc = dev_alloc(h, &h->velB, nv * vec_size(h)))) return bail(rc);
-    if ((rc = dev_alloc(h, (void**)&h->best, nv * sizeof(int32_t)))) return bail(rc);
+    if ((rc = dev_alloc(h, (void**)&h->bkey, nv * sizeof(unsigned long long)))) return bail(rc);
+    if ((rc = dev_alloc(h, (void**)&h->slot_of, nv * sizeof(uint32_t)))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->key, nv * sizeof(uint32_t)))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->slot, nv * sizeof(uint32_t)))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->inst_d, sizeof(InstDev) * h->n_inst))) return bail(rc);

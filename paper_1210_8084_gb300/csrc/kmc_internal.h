@@ -24,6 +24,7 @@ constexpr int kAccFields = 9;          // per c-bin accumulator: 8 moment sums +
 constexpr uint32_t kErrScanTimeout = 1u;
 constexpr uint32_t kErrKeyRange = 2u;
 
+constexpr unsigned long long kNoPartner = ~0ull;  // partner key of a particle without candidate
 constexpr int kMomItems = 4;           // moments: consecutive particles per thread
 constexpr int kStageThreads = 256;     // staged search: threads per tile
 
@@ -98,7 +99,8 @@ struct Bufs {
     Geo geo;
     V* posA; V* velA;        // sorted state (search-grid key order)
     V* posB; V* velB;        // staging / unsorted end-of-step state
-    int32_t* best;           // [n] sorted position of the closest candidate or -1
+    unsigned long long* bkey;  // [n] partner key of A[p] (tag of the closest candidate, kNoPartner)
+    uint32_t* slot_of;       // [n] by global id: sorted position in A (written by the search)
     uint32_t* key;           // [n] search key of B
     uint32_t* slot;          // [n] rank of B[p] within its search cell
     uint32_t* count;         // [n_keys + 1] histogram (zero outside the step)

@@ -422,6 +422,25 @@ __device__ __forceinline__ dvec4 ldg_vec(const dvec4* p) {
     return r;
 }
 
+// Order-preserving 32-bit image of a binary32 distance (-0 folded into +0):
+// unsigned comparison of the images is the floating-point comparison.
+__device__ __forceinline__ uint32_t ordered_bits(float d2) {
+    const uint32_t u = __float_as_uint(d2 + 0.0f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+// Partner key of a particle: the tag of its closest candidate in the low 32
+// bits; in binary32 the high 32 bits hold the ordered image of d2, so that
+// the minimum key is the closest candidate with ties to the lower id (tags of
+// one instance order as their ids); the symmetric search combines keys with
+// atomicMin.  Binary64 searches store the key of a full window directly and
+// leave the high bits zero.
+template <typename T>
+__device__ __forceinline__ unsigned long long partner_key(T d2, uint32_t tag) {
+    if (sizeof(T) == 4) return ((unsigned long long)ordered_bits((float)d2) << 32) | (unsigned long long)tag;
+    return (unsigned long long)tag;
+}
+
 // The acceptance test with the separation r_i - r_j formed as
 // (x_i - x_j) + shift_d: the shift is the periodic image of the candidate's
 // row (0, +L or -L) when MINIMG is false, and the per-candidate minimum image
@@ -489,11 +508,12 @@ __device__ __forceinline__ Win window_1d(int g, int c, int s, int M, int k, bool
 // Test the candidates [q, qe) of one range and keep the closest (smaller d2,
 // ties to the lower id).  The next candidate is loaded before the current one
 // is tested.
-template <typename T, int DIM, bool MINIMG>
+template <typename T, int DIM, bool MINIMG, bool SYM = false>
 __device__ __forceinline__ void scan_range(const Bufs<T>& b, const GeoT<T>& G, int32_t q, int32_t qe,
                                            const T sh[3], const T xi[3], const T vi[3], T dt, T R2, T& bd,
-                                           uint32_t& bid, int32_t& bq) {
+                                           uint32_t& bid, int32_t& bq, int32_t self = 0, uint32_t tag = 0) {
     using V = typename Vec4<T>::type;
+    if (SYM) q = max(q, self + 1);
     if (q >= qe) return;
     V Pn = ldg_vec(b.posA + q);
     V Qn = ldg_vec(b.velA + q);
@@ -514,6 +534,7 @@ __device__ __forceinline__ void scan_range(const Bufs<T>& b, const GeoT<T>& G, i
                 bid = idj;
                 bq = q;
             }
+            if (SYM) atomicMin(&b.bkey[q], partner_key<T>(d2, tag));
         }
     }
 }
@@ -533,10 +554,84 @@ __device__ __forceinline__ int unwrap(int t, int M, T L, T& shift) {
 // dimension, one range per row): all row ranges are fetched first so their
 // loads overlap, then the rows are scanned in turn.  Otherwise rows are
 // visited one at a time.
-template <typename T, int DIM, bool MINIMG>
+// Walk the non-empty row ranges of one particle as one sequence: the ranges
+// sit in shared memory (`rng`, one slot per row, stride kThreads), `mask`
+// marks the non-empty rows, and the next candidate is loaded while the current
+// one is tested.  A lane with short rows goes on to its next row instead of
+// idling until the longest row of its warp is done.  `code` holds the periodic
+// image of every row: two bits per x row (bits 0-5) and per y row (bits 6-11),
+// 1 = +L, 2 = -L; `sf` is the image of the fast dimension.
+template <typename T>
+__device__ __forceinline__ T image_of(uint32_t c, T L) {
+    return c == 1u ? L : (c == 2u ? -L : (T)0);
+}
+
+template <typename T, int DIM, bool MINIMG, bool SYM>
+__device__ __forceinline__ void walk_rows(const Bufs<T>& b, const GeoT<T>& G, const int2* rng, uint32_t mask,
+                                          uint32_t code, T sf, const T xi[3], const T vi[3], T dt, T R2, T& bd,
+                                          uint32_t& bid, int32_t& bq, uint32_t tag) {
+    using V = typename Vec4<T>::type;
+    if (mask == 0u) return;
+    int r = __ffs(mask) - 1;
+    mask &= mask - 1u;
+    int2 rg = rng[r * kThreads];
+    int32_t q = rg.x, qe = rg.y;
+    auto row_shift = [&](int row, T& s0, T& s1) {
+        const int ix = (DIM == 3) ? row / 3 : row;
+        const int iy = (DIM == 3) ? row - 3 * ix : 0;
+        s0 = image_of<T>((code >> (2 * ix)) & 3u, G.L[0]);
+        s1 = (DIM == 3) ? image_of<T>((code >> (6 + 2 * iy)) & 3u, G.L[1]) : sf;
+    };
+    T s0, s1;
+    row_shift(r, s0, s1);
+    V Pn = ldg_vec(b.posA + q);
+    V Qn = ldg_vec(b.velA + q);
+    for (;;) {
+        const V Pj = Pn, Qj = Qn;
+        const int32_t qj = q;
+        T sh[3];
+        sh[0] = s0;
+        sh[1] = s1;
+        sh[2] = sf;
+        bool more = true;
+        if (++q >= qe) {
+            if (mask != 0u) {
+                r = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                rg = rng[r * kThreads];
+                q = rg.x;
+                qe = rg.y;
+                row_shift(r, s0, s1);
+            } else {
+                more = false;
+            }
+        }
+        if (more) {
+            Pn = ldg_vec(b.posA + q);
+            Qn = ldg_vec(b.velA + q);
+        }
+        const T xj[3] = {Pj.x, Pj.y, Pj.z};
+        const T vj[3] = {Qj.x, Qj.y, Qj.z};
+        T d2;
+        // the particle itself has v_rel = 0 and fails b > 0
+        if (poca_test_sh<T, DIM, MINIMG>(G, xi, vi, xj, vj, sh, dt, R2, d2)) {
+            const uint32_t idj = R<T>::bits(Pj.w);
+            if (d2 < bd || (d2 == bd && idj < bid)) {
+                bd = d2;
+                bid = idj;
+                bq = qj;
+            }
+            if (SYM) atomicMin(&b.bkey[qj], partner_key<T>(d2, tag));
+        }
+        if (!more) break;
+    }
+}
+
+template <typename T, int DIM, bool MINIMG, bool WALK = false, bool SYM = false>
 __device__ __forceinline__ void scan_window(const Bufs<T>& b, const GeoT<T>& G, const InstDev& I, const Win w[3],
                                             const T xi[3], const T vi[3], T dt, T R2, T& bd, uint32_t& bid,
-                                            int32_t& bq) {
+                                            int32_t& bq, int2* rng = nullptr, int32_t self = 0,
+                                            uint32_t tag = 0, uint32_t self_key = 0) {
     constexpr int F = DIM - 1;   // fast (contiguous) dimension
     const int MF = I.M[F];
     const uint32_t nmax = (uint32_t)b.n;
@@ -578,20 +673,41 @@ __device__ __forceinline__ void scan_window(const Bufs<T>& b, const GeoT<T>& G, 
             q1[r] = 0;
             if (ix < nx && iy < ny) {
                 const uint32_t row = I.key_base + ((uint32_t)gxs[ix] * My + (uint32_t)gys[iy]) * Mf;
+                // symmetric search: a row that ends before the particle's own cell
+                // holds only lower positions, whose particles test this one
+                if (SYM && row + (uint32_t)fb[0] < self_key) continue;
                 // clamped so that a corrupted scan (flagged on the host) cannot read outside A
                 q0[r] = (int32_t)min(b.start[row + (uint32_t)fa[0]], nmax);
                 q1[r] = (int32_t)min(b.start[row + (uint32_t)fb[0] + 1u], nmax);
             }
         }
+        if constexpr (WALK) {
+            uint32_t mask = 0u, code = 0u;
 #pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            const int ix = (DIM == 3) ? r / 3 : r;
-            const int iy = (DIM == 3) ? r % 3 : 0;
-            T sh[3];
-            sh[0] = sx[ix];
-            sh[1] = (DIM == 3) ? sy[iy] : fs[0];
-            sh[2] = fs[0];
-            scan_range<T, DIM, MINIMG>(b, G, q0[r], q1[r], sh, xi, vi, dt, R2, bd, bid, bq);
+            for (int r = 0; r < NR; ++r) {
+                if (SYM) q0[r] = max(q0[r], self + 1);
+                if (q1[r] > q0[r]) {
+                    rng[r * kThreads] = make_int2(q0[r], q1[r]);
+                    mask |= 1u << r;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                code |= (sx[i] > (T)0 ? 1u : (sx[i] < (T)0 ? 2u : 0u)) << (2 * i);
+                if (DIM == 3) code |= (sy[i] > (T)0 ? 1u : (sy[i] < (T)0 ? 2u : 0u)) << (6 + 2 * i);
+            }
+            walk_rows<T, DIM, MINIMG, SYM>(b, G, rng, mask, code, fs[0], xi, vi, dt, R2, bd, bid, bq, tag);
+        } else {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int ix = (DIM == 3) ? r / 3 : r;
+                const int iy = (DIM == 3) ? r % 3 : 0;
+                T sh[3];
+                sh[0] = sx[ix];
+                sh[1] = (DIM == 3) ? sy[iy] : fs[0];
+                sh[2] = fs[0];
+                scan_range<T, DIM, MINIMG, SYM>(b, G, q0[r], q1[r], sh, xi, vi, dt, R2, bd, bid, bq, self, tag);
+            }
         }
         return;
     }
@@ -609,7 +725,7 @@ __device__ __forceinline__ void scan_window(const Bufs<T>& b, const GeoT<T>& G, 
                 sh[0] = sx;
                 sh[1] = (DIM == 3) ? sy : fs[part];
                 sh[2] = fs[part];
-                scan_range<T, DIM, MINIMG>(b, G, q, qe, sh, xi, vi, dt, R2, bd, bid, bq);
+                scan_range<T, DIM, MINIMG, SYM>(b, G, q, qe, sh, xi, vi, dt, R2, bd, bid, bq, self, tag);
             }
         }
     }
@@ -618,18 +734,30 @@ __device__ __forceinline__ void scan_window(const Bufs<T>& b, const GeoT<T>& G, 
 // Closest candidate of every particle (criterion 3 over the 3^D c-bin
 // neighbourhood, restricted to the search cells that can hold a candidate).
 // One thread per particle in sorted order; candidates are read through L1.
+// Binary32: the pair test is symmetric (swapping i and j negates dr and dv
+// exactly, which leaves a, b, |r|^2, disc and d2 bit for bit unchanged), so
+// every pair is tested once, by its lower sorted position, and the outcome
+// goes to both partners: to the tester's running minimum and, with
+// atomicMin, to the candidate's key.  Keys start at kNoPartner.  Binary64
+// tests every candidate of a full window and stores its key.  Every particle
+// records its sorted position by id (slot_of) for the move kernel.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) search_kernel(Bufs<T> b) {
     using V = typename Vec4<T>::type;
+    constexpr bool kSym = sizeof(T) == 4;
     __shared__ GeoT<T> G;
+    __shared__ int2 rng[(DIM == 3 ? 9 : 3) * kThreads];
     if (threadIdx.x == 0) G.load(b.geo);
     __syncthreads();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= b.n) return;
     const V P = b.posA[p];
     const V Q = b.velA[p];
-    const int inst = tag_inst(b, R<T>::bits(P.w));
+    const uint32_t tag = R<T>::bits(P.w);
+    const int inst = tag_inst(b, tag);
     const InstDev& I = b.inst[inst];
+    // sorted position by id, read by the move kernel to find a partner
+    b.slot_of[I.p_off + (int64_t)tag_id(b, tag)] = (uint32_t)p;
     if (I.staged) return;   // searched by the staged kernel
     const int* kk = b.dyn[inst].k;
     const T xi[3] = {P.x, P.y, P.z};
@@ -648,15 +776,29 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) search_kerne
     T bd = R<T>::inf();
     uint32_t bid = 0xffffffffu;
     int32_t bq = -1;
-    if (amb) scan_window<T, DIM, true>(b, G, I, w, xi, vi, dt, R2, bd, bid, bq);
-    else scan_window<T, DIM, false>(b, G, I, w, xi, vi, dt, R2, bd, bid, bq);
-    b.best[p] = bq;
+    uint32_t self_key = 0;
+    if (kSym) {
+        self_key = (DIM == 3) ? I.key_base + ((uint32_t)g[0] * (uint32_t)I.M[1] + (uint32_t)g[1]) * (uint32_t)I.M[2] +
+                                    (uint32_t)g[2]
+                              : I.key_base + (uint32_t)g[0] * (uint32_t)I.M[1] + (uint32_t)g[1];
+    }
+    if (amb)
+        scan_window<T, DIM, true, true, kSym>(b, G, I, w, xi, vi, dt, R2, bd, bid, bq, rng + threadIdx.x,
+                                              (int32_t)p, tag, self_key);
+    else
+        scan_window<T, DIM, false, true, kSym>(b, G, I, w, xi, vi, dt, R2, bd, bid, bq, rng + threadIdx.x,
+                                               (int32_t)p, tag, self_key);
+    if (kSym) {
+        if (bq >= 0) atomicMin(&b.bkey[p], partner_key<T>(bd, bid));
+    } else {
+        b.bkey[p] = bq >= 0 ? partner_key<T>(bd, bid) : kNoPartner;
+    }
 }
 
 // Direct search of one particle (global loads), used by the staged kernel for
 // particles whose window it cannot serve from shared memory.
 template <typename T, int DIM>
-__device__ __noinline__ int32_t search_one_direct(const Bufs<T>& b, const GeoT<T>& G, int64_t p) {
+__device__ __noinline__ unsigned long long search_one_direct(const Bufs<T>& b, const GeoT<T>& G, int64_t p) {
     using V = typename Vec4<T>::type;
     const V P = b.posA[p];
     const V Q = b.velA[p];
@@ -681,7 +823,7 @@ __device__ __noinline__ int32_t search_one_direct(const Bufs<T>& b, const GeoT<T
     int32_t bq = -1;
     if (amb) scan_window<T, DIM, true>(b, G, I, w, xi, vi, dt, R2, bd, bid, bq);
     else scan_window<T, DIM, false>(b, G, I, w, xi, vi, dt, R2, bd, bid, bq);
-    return bq;
+    return bq >= 0 ? partner_key<T>(bd, bid) : kNoPartner;
 }
 
 // Staged search (3-D, sparse search cells).  A block owns a tile: tile_rows
@@ -695,13 +837,6 @@ __device__ __noinline__ int32_t search_one_direct(const Bufs<T>& b, const GeoT<T
 // unwrapped window, takes the direct path.
 constexpr int kStageMaxRows = 64;
 constexpr int kStageMaxHome = 2 * kStageThreads;
-
-// Order-preserving 32-bit image of a binary32 distance (-0 folded into +0):
-// unsigned comparison of the images is the floating-point comparison.
-__device__ __forceinline__ uint32_t ordered_bits(float d2) {
-    const uint32_t u = __float_as_uint(d2 + 0.0f);
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
 
 // Ranges [q0, q1) (shared-memory indices) of one home particle's window
 // inside the staged rows; calls f(q0, q1) for each.  Returns false when the
@@ -741,8 +876,8 @@ __device__ __forceinline__ bool for_each_staged_range(const GeoT<T>& G, const In
 // entries round-robin, so every lane has work whatever the window sizes; a
 // passing candidate lowers the home particle's 64-bit key (ordered d2, tag)
 // with a shared-memory atomicMin, which keeps the smaller distance and, on a
-// tie, the lower id.  Phase C: each home particle finds the staged index of
-// the winning tag among its own entries.  Periodic images come from the
+// tie, the lower id.  Phase C: each home particle stores its key (the same
+// format as the direct search).  Periodic images come from the
 // per-candidate minimum image, equal to the row image inside these windows.
 template <typename T>
 __device__ __noinline__ void staged_pairs(const Bufs<T>& b, const GeoT<T>& G, const InstDev& I, const int* kk,
@@ -830,7 +965,7 @@ __device__ __noinline__ void staged_pairs(const Bufs<T>& b, const GeoT<T>& G, co
     }
     __syncthreads();
     if (!list_ok) {   // too many entries for the list: direct search for the whole tile
-        for (int64_t p = h0 + tid; p < h1; p += blockDim.x) b.best[p] = search_one_direct<T, 3>(b, G, p);
+        for (int64_t p = h0 + tid; p < h1; p += blockDim.x) b.bkey[p] = search_one_direct<T, 3>(b, G, p);
         return;
     }
     // phase B: balanced pair tests
@@ -851,30 +986,16 @@ __device__ __noinline__ void staged_pairs(const Bufs<T>& b, const GeoT<T>& G, co
         }
     }
     __syncthreads();
-    // phase C: staged index of the winning tag, back to a sorted position
+    // phase C: the keys to global memory
     for (int k = 0; k < 2; ++k) {
         const int i = tid + k * kStageThreads;
         if (i >= H) break;
         const int64_t p = h0 + i;
         if (direct[k]) {
-            b.best[p] = search_one_direct<T, 3>(b, G, p);
+            b.bkey[p] = search_one_direct<T, 3>(b, G, p);
             continue;
         }
-        const unsigned long long key = bkey[i];
-        int32_t bq = -1;
-        if (key != ~0ull) {
-            const uint32_t tag = (uint32_t)key;
-            for (int t = hoff[i]; t < hoff[i + 1]; ++t) {
-                const int q = (int)(pairs[t] & 0xffffu);
-                if (R<T>::bits(sp[q].w) == tag) {
-                    int r = 0;
-                    while (r + 1 < nr && rowL0[r + 1] <= q) ++r;
-                    bq = rowA0[r] + (q - rowL0[r]);
-                    break;
-                }
-            }
-        }
-        b.best[p] = bq;
+        b.bkey[p] = bkey[i];
     }
 }
 
@@ -950,7 +1071,7 @@ __global__ void __launch_bounds__(kStageThreads) search_staged_kernel(Bufs<T> b)
         __syncthreads();
     }
     if (!s_ok) {   // neighbourhood too large for this tile: direct search
-        for (int64_t p = s_h0 + tid; p < s_h1; p += blockDim.x) b.best[p] = search_one_direct<T, 3>(b, G, p);
+        for (int64_t p = s_h0 + tid; p < s_h1; p += blockDim.x) b.bkey[p] = search_one_direct<T, 3>(b, G, p);
         return;
     }
     // copy the rows and their search-cell offsets: one warp per row, lanes
@@ -994,7 +1115,7 @@ __global__ void __launch_bounds__(kStageThreads) search_staged_kernel(Bufs<T> b)
                 amb = amb || w[d].amb;
             }
             if (amb || w[0].lo < s_xlo || w[0].hi >= s_xlo + s_nx || w[1].lo < s_ylo || w[1].hi >= s_ylo + s_ny) {
-                b.best[p] = search_one_direct<T, 3>(b, G, p);
+                b.bkey[p] = search_one_direct<T, 3>(b, G, p);
                 continue;
             }
             // z parts of the window (z is the fastest key dimension)
@@ -1057,7 +1178,7 @@ __global__ void __launch_bounds__(kStageThreads) search_staged_kernel(Bufs<T> b)
                 }
                 ++q;
             }
-            b.best[p] = bq;
+            b.bkey[p] = bq >= 0 ? partner_key<T>(bd, bid) : kNoPartner;
         }
     }
 }
@@ -1066,7 +1187,7 @@ __global__ void __launch_bounds__(kStageThreads) search_staged_kernel(Bufs<T> b)
 // next step's search key / slot / histogram.  The particle's collisional
 // virial goes to vel.w for the moment pass.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kThreads) move_kernel(Bufs<T> b) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 1) move_kernel(Bufs<T> b) {
     using V = typename Vec4<T>::type;
     __shared__ GeoT<T> G;
     if (threadIdx.x == 0) G.load(b.geo);
@@ -1075,12 +1196,12 @@ __global__ void __launch_bounds__(kThreads) move_kernel(Bufs<T> b) {
     const bool valid = p < b.n;
     V P = {}, Q = {};
     int inst = 0;
-    int32_t j = -1;
+    unsigned long long kp = kNoPartner;
     if (valid) {
         P = b.posA[p];
         Q = b.velA[p];
         inst = tag_inst(b, R<T>::bits(P.w));
-        j = b.best[p];
+        kp = b.bkey[p];
     }
     const InstDev I = b.inst[inst];
     const uint32_t tag = R<T>::bits(P.w);   // ordering of tags = ordering of local ids
@@ -1091,9 +1212,12 @@ __global__ void __launch_bounds__(kThreads) move_kernel(Bufs<T> b) {
     T W = (T)0;
     bool paired = false;
     uint32_t tagj = 0xffffffffu;
-    if (j >= 0) {
-        paired = b.best[j] == (int32_t)p;
-        if (paired || b.record) tagj = R<T>::bits(b.posA[j].w);
+    int64_t j = -1;
+    if (kp != kNoPartner) {
+        tagj = (uint32_t)kp;
+        j = b.slot_of[I.p_off + (int64_t)tag_id(b, tagj)];
+        const unsigned long long kj = b.bkey[j];
+        paired = kj != kNoPartner && (uint32_t)kj == tag;
     }
     if (paired) {
         const V Pj = b.posA[j];
@@ -1177,7 +1301,7 @@ __global__ void __launch_bounds__(kThreads) move_kernel(Bufs<T> b) {
         b.slot[p] = slot;
         if (b.record) {
             const int64_t gid = I.p_off + (int64_t)tag_id(b, tag);
-            b.rec_best[gid] = (j >= 0) ? (int32_t)tag_id(b, tagj) : -1;
+            b.rec_best[gid] = (kp != kNoPartner) ? (int32_t)tag_id(b, tagj) : -1;
             b.rec_partner[gid] = paired ? (int32_t)tag_id(b, tagj) : -1;
         }
     }
@@ -1198,6 +1322,7 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(Bufs<T> b) {
     }
     b.posA[dst] = b.posB[p];
     b.velA[dst] = b.velB[p];
+    b.bkey[dst] = kNoPartner;   // the next search starts from no partner
 }
 
 // State of A in id order.
@@ -1407,7 +1532,8 @@ cudaError_t launch_search(const Bufs<T>& b, cudaStream_t s) {
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    if (b.any_direct) KMC_DIM_DISPATCH(b.geo.dim, search_kernel, b);
+    // always launched: besides the direct search it records slot_of for every particle
+    KMC_DIM_DISPATCH(b.geo.dim, search_kernel, b);
     return cudaGetLastError();
 }
 

@@ -52,14 +52,15 @@ __device__ __forceinline__ uint32_t tag_of(double w) {
     return (uint32_t)(unsigned long long)__double_as_longlong(w);
 }
 
-// Closest candidate per particle: sorted position -> instance-local id, by id.
+// Closest candidate per particle (its tag is the low half of the partner
+// key; one instance, so tag = id), by id.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) best_by_id(Bufs<T> b, int32_t* __restrict__ out) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= b.n) return;
     const uint32_t id = tag_of(b.posA[p].w);
-    const int32_t q = b.best[p];
-    out[id] = q >= 0 ? (int32_t)tag_of(b.posA[q].w) : -1;
+    const unsigned long long k = b.bkey[p];
+    out[id] = k != kNoPartner ? (int32_t)(uint32_t)k : -1;
 }
 
 template <typename T>
@@ -122,7 +123,8 @@ int run(const kmc_config* cfg, int64_t n, const void* pos, const void* vel, int3
     b.velA = (V*)take(nv * sizeof(V));
     b.posB = (V*)take(nv * sizeof(V));
     b.velB = (V*)take(nv * sizeof(V));
-    b.best = (int32_t*)take(nv * sizeof(int32_t));
+    b.bkey = (unsigned long long*)take(nv * sizeof(unsigned long long));
+    b.slot_of = (uint32_t*)take(nv * sizeof(uint32_t));
     b.key = (uint32_t*)take(nv * sizeof(uint32_t));
     b.slot = (uint32_t*)take(nv * sizeof(uint32_t));
     b.count = (uint32_t*)take((size_t)n_tiles * kScanTile * sizeof(uint32_t));

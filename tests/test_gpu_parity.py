@@ -293,3 +293,39 @@ def test_energy_conservation_fp32():
     e1 = sim.moments()[2][0, 1]
     sim.close()
     assert abs(e1 - e0) <= 1e-6 * e0, (e0, e1)
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+@pytest.mark.parametrize("staged", [False, True])
+def test_exact_tie_in_d2_goes_to_lower_id(precision, staged):
+    """Two candidates at exactly the same distance of closest approach (mirror
+    images in y of each other relative to particle 2).  Candidate 1 sorts
+    before candidate 0 (lower y cell) but has the higher id: the closest
+    candidate of particle 2 must be id 0 (R4), as in the oracle, and the
+    following step must start from a clean tie list."""
+    _setup()
+    import oracle
+    import paper_1210_8084_gb300 as k
+    dt = 1e-3
+    pos = np.array([[0.45, 0.5625, 0.5], [0.45, 0.4375, 0.5], [0.55, 0.5, 0.5]])
+    vel = np.array([[200.0, -1.0, 0.0], [200.0, 1.0, 0.0], [0.0, 0.0, 0.0]])
+    dtype = np.float32 if precision == 32 else np.float64
+    pos, vel = pos.astype(dtype), vel.astype(dtype)
+    flags = k.KMC_FLAG_RECORD | (k.KMC_FLAG_STAGED_SEARCH if staged else 0)
+    cfg = k.make_config(dim_pos=3, n_cells=(4, 4, 4), bc=(PER, PER, PER), sigma=math.pi * 0.01, dt=dt, seed=3,
+                        precision=precision, flags=flags)
+    sim = k.Simulation(cfg, pos, vel)
+    R2 = sim.info().R2
+    sim.step(1)
+    best, partner = sim.partners()
+    p1, v1 = sim.state()
+    sim.step(1)
+    best2, partner2 = sim.partners()
+    sim.close()
+    assert list(best) == [2, 2, 0]
+    assert list(partner) == [2, -1, 0]
+    P = oracle.make_params(3, (4, 4, 4), (0, 0, 0), (1, 1, 1), (PER, PER, PER), R2=R2, dt=dt, seed=3, step=0,
+                           decide32=precision == 32)
+    assert list(oracle.best_partners(P, pos.astype(np.float64), vel.astype(np.float64))) == [2, 2, 0]
+    P.step = 1
+    assert np.array_equal(best2, oracle.best_partners(P, p1.astype(np.float64), v1.astype(np.float64)))
