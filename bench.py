@@ -99,6 +99,29 @@ class ClockSampler:
 FLOPS_PER_TEST = 25          # binary32 operations per candidate test
 
 
+def max_over_ranks(values, world, device):
+    """Elementwise maximum of per-rank timings over all ranks (the job is as
+    slow as its slowest replica); unchanged on one rank."""
+    values = [float(v) for v in values]
+    if world == 1:
+        return values
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def job_rate(units_per_rank, world, steps, seconds):
+    """Whole-job throughput: units of every rank over the slowest rank's time."""
+    return units_per_rank * world * steps / seconds
+
+
+def replica_seed(seed, rank):
+    """Independent replicas: rank r draws its state and its scattering with seed + r."""
+    return seed + rank
+
+
 def kernels_per_step(precision):
     """Kernels of one step with moments: search, move, scan, scatter, moments,
     two finalize kernels."""
@@ -130,15 +153,15 @@ def algorithmic_bytes(n, n_keys, n_bins, frac_paired, phase):
     """Bytes each kernel must move at least (binary32 state), per launch.
     State of a particle: position 12 B + id 4 B, velocity 12 B + instance 4 B."""
     if phase == "search":
-        return n * (32 + 4)                    # read own state once, write closest candidate
-    if phase == "move":                        # own state, best, partner best, B, key, slot, histogram
-        return n * (32 + 4 + 4 + 32 + 4 + 4 + 4) + n * frac_paired * 32
+        return n * (32 + 8)                    # read own state once, write the partner key
+    if phase == "move":                        # own state, partner key, partner's key, B, key, slot, histogram
+        return n * (32 + 8 + 8 + 32 + 4 + 4 + 4) + n * frac_paired * 32
     if phase == "moments":                     # read A once, bin sums
         return n * 32 + n_bins * 72 * 2
     if phase == "scan":
         return n_keys * (4 + 4 + 4)            # read count, write start, clear count
-    if phase == "scatter":
-        return n * (4 + 4 + 4 + 32 + 32)       # key, slot, start[key], read B, write A
+    if phase == "scatter":                     # key, slot, start[key], read B, write A, clear key
+        return n * (4 + 4 + 4 + 32 + 32 + 8)
     return 0
 
 
@@ -164,12 +187,12 @@ def ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     w = make_workload(args)
     n = w["n"]
-    pos, vel = inputs.make_state(w, seed=w["seed"] + rank)
+    pos, vel = inputs.make_state(w, seed=replica_seed(w["seed"], rank))
     dtype = np.float32 if w["precision"] == 32 else np.float64
     pos, vel = inputs.cast_state(pos, vel, dtype, w["lo"], w["hi"], w["bc"])
     stream = torch.cuda.Stream()
     cfg = k.make_config(dim_pos=w["dim_pos"], n_cells=w["n_cells"], lo=w["lo"], hi=w["hi"], bc=w["bc"],
-                        lam=w["lam"], dt=w["dt"], seed=w["seed"] + rank, precision=w["precision"],
+                        lam=w["lam"], dt=w["dt"], seed=replica_seed(w["seed"], rank), precision=w["precision"],
                         stream=stream.cuda_stream, occupancy_target=args.occ)
 
     def barrier():
@@ -190,12 +213,7 @@ def ours(args):
     prof = sim.step_profiled(args.steps, want_moments=1)
     barrier()
     clk = clocks.stop()
-    elapsed_ms = prof["total"]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks([prof["total"]], world, "cuda")[0]
     raw, der, glob = sim.moments()
     pairs = float(glob[0, 6])
     frac_paired = 2 * pairs / n
@@ -219,14 +237,9 @@ def ours(args):
         k.kmc_get_state(h, pin_pos.numpy(), pin_vel.numpy(), k.KMC_WHERE_HOST)
         k.kmc_free(h)
         barrier()
-        e2e_s = time.perf_counter() - t0
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks([time.perf_counter() - t0], world, "cuda")[0]
         state_bytes = pos.nbytes + vel.nbytes
-        e2e = {"value": n * world * args.steps / e2e_s, "unit": UNIT,
+        e2e = {"value": job_rate(n, world, args.steps, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": int(state_bytes / args.steps),
                "d2h_bytes_per_step": int(mom.numel() * 8 + state_bytes / args.steps)}
 
@@ -267,7 +280,7 @@ def ours(args):
                 "achieved_gbs": round(step_bytes / (elapsed_ms / args.steps * 1e-3) / 1e9, 1),
                 "frac_of_measured_hbm": round(step_bytes / (elapsed_ms / args.steps * 1e-3) / 1e9 /
                                               float(peaks.get("hbm_gbs", 6800.0)), 4)}
-    value = n * world * args.steps / (elapsed_ms * 1e-3)
+    value = job_rate(n, world, args.steps, elapsed_ms * 1e-3)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
@@ -309,7 +322,7 @@ def batched(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     w = dict(inputs.WORKLOADS["sod1d_batched_256"])
     n_inst = args.instances or w["n_instances"]
-    ns, lams = inputs.log_uniform_instances(n_inst, seed=w["seed"] + rank, n_range=w["n_range"],
+    ns, lams = inputs.log_uniform_instances(n_inst, seed=replica_seed(w["seed"], rank), n_range=w["n_range"],
                                             lam_range=w["lam_range"])
     P, V, insts = [], [], []
     for i in range(n_inst):
@@ -350,15 +363,11 @@ def batched(args):
         torch.cuda.synchronize()
         ms_plain += timed(s1.h, args.steps)
         s1.close()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_batched, ms_plain], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_batched, ms_plain = float(t[0]), float(t[1])
+    ms_batched, ms_plain = max_over_ranks([ms_batched, ms_plain], world, "cuda")
     if rank != 0:
         return None
-    value = n_total * world * args.steps / (ms_batched * 1e-3)
-    plain = n_total * world * args.steps / (ms_plain * 1e-3)
+    value = job_rate(n_total, world, args.steps, ms_batched * 1e-3)
+    plain = job_rate(n_total, world, args.steps, ms_plain * 1e-3)
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_batched / args.steps, "higher_is_better": True,

@@ -134,8 +134,9 @@ Bufs<T> make_bufs(const kmc_handle* h) {
     return b;
 }
 
-// One step: search, move (+ key, histogram, moments), scan, scatter.  When
-// `ev` is given, ev[k] is recorded before phase k and ev[KMC_NPHASES] at the end.
+// One step: search, move (+ key, histogram), scan, scatter, moments and
+// finalize (when wanted).  When `ev` is given, ev[k] is recorded before phase k
+// and ev[KMC_NPHASES] at the end.
 template <typename T>
 cudaError_t enqueue_step(kmc_handle* h, int want_moments, cudaEvent_t* ev = nullptr) {
     const Bufs<T> b = make_bufs<T>(h);

@@ -1377,11 +1377,20 @@ __global__ void __launch_bounds__(kThreads) moments_kernel(Bufs<T> b, int use_vi
     uint32_t cur = 0xffffffffu;
     T f[7] = {0, 0, 0, 0, 0, 0, 0};
     int cnt = 0, coll = 0;
+    V Ps[kMomItems], Qs[kMomItems];   // all loads in flight before the sums
+#pragma unroll
+    for (int k = 0; k < kMomItems; ++k) {
+        if (base + k < b.n) {
+            Ps[k] = b.posA[base + k];
+            Qs[k] = b.velA[base + k];
+        }
+    }
+#pragma unroll
     for (int k = 0; k < kMomItems; ++k) {
         const int64_t p = base + k;
         if (p >= b.n) break;
-        const V P = b.posA[p];
-        const V Q = b.velA[p];
+        const V P = Ps[k];
+        const V Q = Qs[k];
         const int inst = tag_inst(b, R<T>::bits(P.w));
         const InstDev& I = b.inst[inst];
         const T x[3] = {P.x, P.y, P.z};
