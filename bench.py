@@ -130,10 +130,12 @@ FP32_LANES = 152 * 128       # GB300: SMs x FP32 lanes per SM
 B_ALG_F32 = 72               # algorithmic bytes per particle-step (binary32 state)
 
 
-def profiled_traffic(kernel):
+def profiled_traffic(kernel, workload, lam):
     """dram bytes per launch of `kernel` from the committed ncu summary, if that
-    summary was taken on the current kernel source (else None)."""
+    summary was taken on this workload and the current kernel source (else None)."""
     import hashlib
+    if workload != "sod1d_fp32_16M" or lam != 1e-3:
+        return None
     path = os.path.join(ROOT, "profiles", f"{kernel}_kernel_sod1d_16M.md")
     src = os.path.join(ROOT, "paper_1210_8084_gb300", "csrc", "kmc_kernels.cuh")
     if not os.path.exists(path):
@@ -251,7 +253,7 @@ def ours(args):
     phases = {p: prof[p] / args.steps for p in ("search", "move", "scan", "scatter", "moments", "finalize")}
     dom = max(("search", "move", "scan", "scatter", "moments"), key=lambda p: phases[p])
     t_dom = phases[dom] * 1e-3
-    traffic = profiled_traffic(dom)
+    traffic = profiled_traffic(dom, args.workload, w["lam"])
     if dom == "search":
         # arithmetic-bound: 25 binary32 operations per pair test (PoCA test with
         # its early outs).  The window of a particle holds C_p candidates (itself

@@ -58,6 +58,7 @@ extern "C" {
 #define KMC_FLAG_RECORD 1   /* keep each particle's closest candidate and partner of the last step */
 #define KMC_FLAG_NO_GRAPH 2 /* launch kernels directly instead of replaying a captured CUDA graph */
 #define KMC_FLAG_STAGED_SEARCH 4 /* stage tile neighbourhoods in shared memory (3-D; same results as the direct search) */
+#define KMC_FLAG_NO_TILE_SEARCH 8 /* search unsubdivided grids per particle too (default: one block per c-bin; same results) */
 
 #define KMC_MOM_RAW 1       /* per c-bin: N, Sum vx, Sum vy, Sum vz, Sum vx^2, Sum vy^2, Sum vz^2, Sum W */
 #define KMC_MOM_DERIVED 2   /* per c-bin: n, ux, uy, uz, T, p_kin, p_vir, p */

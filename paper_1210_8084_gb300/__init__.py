@@ -31,6 +31,7 @@ KMC_BC_WALL = 1
 KMC_FLAG_RECORD = 1
 KMC_FLAG_NO_GRAPH = 2
 KMC_FLAG_STAGED_SEARCH = 4
+KMC_FLAG_NO_TILE_SEARCH = 8
 KMC_MOM_RAW = 1
 KMC_MOM_DERIVED = 2
 KMC_MOM_GLOBAL = 4

@@ -50,7 +50,7 @@ struct kmc_handle {
     uint32_t n_keys = 0, n_tiles = 0;
     uint32_t id_bits = 32;
     uint32_t n_stage_tiles = 0;
-    int stage_cap = 0, stage_rows = 0, stage_stride = 0, stage_pair_cap = 0, any_direct = 1;
+    int stage_cap = 0, stage_rows = 0, stage_stride = 0, stage_pair_cap = 0, any_direct = 1, any_tiled = 0;
     int64_t n_bins = 0, bins_per_inst = 0;
     int64_t bytes = 0;
     int mom_state = 0;  // 1: acc/mom/glob describe the current state
@@ -129,6 +129,7 @@ Bufs<T> make_bufs(const kmc_handle* h) {
     b.stage_stride = h->stage_stride;
     b.stage_pair_cap = h->stage_pair_cap;
     b.any_direct = h->any_direct;
+    b.any_tiled = h->any_tiled;
     b.id_bits = h->id_bits;
     b.id_mask = h->id_bits >= 32 ? 0xffffffffu : ((1u << h->id_bits) - 1u);
     return b;
@@ -355,7 +356,7 @@ int validate_config(const kmc_config* c, int64_t n) {
     }
     if (c->n_instances < 0) return fail(nullptr, KMC_EINVAL, "n_instances < 0");
     if (c->n_instances > 1 && !c->instances) return fail(nullptr, KMC_EINVAL, "instances is NULL");
-    if (c->flags & ~(KMC_FLAG_RECORD | KMC_FLAG_NO_GRAPH | KMC_FLAG_STAGED_SEARCH))
+    if (c->flags & ~(KMC_FLAG_RECORD | KMC_FLAG_NO_GRAPH | KMC_FLAG_STAGED_SEARCH | KMC_FLAG_NO_TILE_SEARCH))
         return fail(nullptr, KMC_EINVAL, "unknown flags");
     return KMC_OK;
 }
@@ -582,6 +583,13 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
         h->n_keys = (uint32_t)keys;
         h->n_tiles = (uint32_t)((keys + 1 + kScanTile - 1) / kScanTile);
         plan_staged_search(h, max_occ);
+        // search cells that are the c-bins themselves: one block per cell
+        h->any_tiled = 0;
+        for (auto& I : h->inst_h) {
+            I.tiled = !I.staged && I.n > 0 && I.s[0] == 1 && I.s[1] == 1 && I.s[2] == 1 &&
+                      !(h->cfg.flags & KMC_FLAG_NO_TILE_SEARCH);
+            h->any_tiled |= I.tiled;
+        }
         if (cudaMemcpyAsync(h->inst_d, h->inst_h.data(), sizeof(InstDev) * h->n_inst, cudaMemcpyHostToDevice,
                             h->stream) != cudaSuccess)
             return bail(fail(h, KMC_ECUDA, "upload of instance table failed"));

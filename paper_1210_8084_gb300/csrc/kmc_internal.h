@@ -46,6 +46,7 @@ struct InstDev {
     // y-rows of one x-slab; the tile's neighbourhood rows are copied to
     // shared memory before the search
     int staged;
+    int tiled;           // search cells are the c-bins: one block per cell (tile_search_kernel)
     int tile_rows;
     int tiles_per_x;     // ceil(M[1] / tile_rows)
     uint32_t tile_base;  // first tile of the instance in the staged launch
@@ -122,6 +123,7 @@ struct Bufs {
     int stage_stride;        // entries per row slot (max M[2] + 1, even)
     int stage_pair_cap;      // entries of the binary32 pair list
     int any_direct;          // some instance uses the direct (per-thread) search
+    int any_tiled;           // some instance uses the tile search (one block per c-bin)
     // particle tag = (instance << id_bits) | instance-local id
     uint32_t id_bits;        // 32 when there is one instance
     uint32_t id_mask;

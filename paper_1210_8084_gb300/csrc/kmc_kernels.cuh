@@ -19,6 +19,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "kmc_internal.h"
 
 namespace kmc {
@@ -447,14 +449,15 @@ __device__ __forceinline__ unsigned long long partner_key(T d2, uint32_t tag) {
 // of every periodic dimension when MINIMG is true.  Both give the same bits as
 // the oracle's minimum image: inside a window narrower than half the box the
 // image of a row is the same for all its candidates.
-template <typename T, int DIM, bool MINIMG>
+template <typename T, int DIM, bool MINIMG, bool SHIFT = true>
 __device__ __forceinline__ bool poca_test_sh(const GeoT<T>& G, const T xi[3], const T vi[3], const T xj[3],
                                              const T vj[3], const T sh[3], T dt, T R2, T& d2) {
     T dr[3], dv[3];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         const T x = R<T>::sub(xi[d], xj[d]);
-        dr[d] = MINIMG ? min_image<T>(x, G.hL[d], G.L[d]) : R<T>::add(x, sh[d]);
+        // SHIFT = false: a row without periodic image (x + 0 = x)
+        dr[d] = MINIMG ? min_image<T>(x, G.hL[d], G.L[d]) : (SHIFT ? R<T>::add(x, sh[d]) : x);
         dv[d] = R<T>::sub(vi[d], vj[d]);
     }
     T a = R<T>::mul(dr[0], dv[0]);
@@ -758,7 +761,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) search_kerne
     const InstDev& I = b.inst[inst];
     // sorted position by id, read by the move kernel to find a partner
     b.slot_of[I.p_off + (int64_t)tag_id(b, tag)] = (uint32_t)p;
-    if (I.staged) return;   // searched by the staged kernel
+    if (I.staged || I.tiled) return;   // searched by the staged or the tile kernel
     const int* kk = b.dyn[inst].k;
     const T xi[3] = {P.x, P.y, P.z};
     const T vi[3] = {Q.x, Q.y, Q.z};
@@ -793,6 +796,240 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) search_kerne
     } else {
         b.bkey[p] = bq >= 0 ? partner_key<T>(bd, bid) : kNoPartner;
     }
+}
+
+// ------------------------------------------------------ tile search
+// Instances whose search cells are the c-bins themselves (no subdivision):
+// every particle of a cell has the same window, the 3^D c-bin neighbourhood
+// (criterion 3), so one block per cell reads the window's candidates once
+// into shared memory and every home particle of the cell runs the same loop
+// over them (broadcast reads, no divergence between lanes).  Same decisions as
+// the direct search: rows of the window as key ranges with their periodic
+// images, binary32 symmetric (a home tests only candidates at higher sorted
+// positions and offers the outcome to both keys), binary64 full window.
+constexpr int kTileThreads = 256;
+constexpr int kTileRanges = 18;   // 3 x 3 rows x 2 parts (a periodic fast dimension may split)
+
+template <typename T>
+struct TileCap {
+    static constexpr int value = 1536;   // staged candidates (pos + vel): 48 KiB in binary32
+};
+template <>
+struct TileCap<double> {
+    static constexpr int value = 768;    // 48 KiB in binary64
+};
+
+template <typename T, int DIM, bool MINIMG>
+__device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>& G, const InstDev& I, int inst,
+                                                 uint32_t kc, int64_t h0, int64_t h1, typename Vec4<T>::type* sp,
+                                                 typename Vec4<T>::type* sv, int* rq0, int* rlen, int* rpre,
+                                                 T (*rsh)[3], int& nr_s, int& tot_s) {
+    using V = typename Vec4<T>::type;
+    constexpr bool kSym = sizeof(T) == 4;
+    constexpr int CAP = TileCap<T>::value;
+    const int tid = threadIdx.x;
+    // cell coordinates from the key (x slowest)
+    uint32_t rel = kc - I.key_base;
+    int g[3] = {0, 0, 0};
+    if (DIM == 3) {
+        g[2] = (int)(rel % (uint32_t)I.M[2]);
+        rel /= (uint32_t)I.M[2];
+    }
+    g[1] = (int)(rel % (uint32_t)I.M[1]);
+    g[0] = (int)(rel / (uint32_t)I.M[1]);
+    const int* kk = b.dyn[inst].k;
+    Win w[3];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) w[d] = window_1d(g[d], g[d], 1, I.M[d], kk[d], G.wall[d]);
+    constexpr int F = DIM - 1;
+    const int MF = I.M[F];
+    // fast-dimension parts of the window
+    int fa[2], fb[2];
+    T fs[2] = {(T)0, (T)0};
+    int nf = 1;
+    if (w[F].lo < 0) {
+        fa[0] = w[F].lo + MF; fb[0] = MF - 1; fs[0] = G.L[F];
+        fa[1] = 0; fb[1] = w[F].hi;
+        nf = 2;
+    } else if (w[F].hi >= MF) {
+        fa[0] = w[F].lo; fb[0] = MF - 1;
+        fa[1] = 0; fb[1] = w[F].hi - MF; fs[1] = -G.L[F];
+        nf = 2;
+    } else {
+        fa[0] = w[F].lo; fb[0] = w[F].hi;
+    }
+    const int nx = w[0].hi - w[0].lo + 1;
+    const int ny = (DIM == 3) ? w[1].hi - w[1].lo + 1 : 1;
+    // one range per (row, part); thread r fills entry r
+    const int nrange = nx * ny * nf;
+    if (tid < kTileRanges) {
+        rq0[tid] = 0;
+        rlen[tid] = 0;
+    }
+    if (tid < nrange) {
+        const int part = tid % nf;
+        const int row = tid / nf;
+        const int ix = (DIM == 3) ? row / ny : row;
+        const int iy = (DIM == 3) ? row % ny : 0;
+        T sx, sy = (T)0;
+        const int gx = unwrap<T>(w[0].lo + ix, I.M[0], G.L[0], sx);
+        const int gy = (DIM == 3) ? unwrap<T>(w[1].lo + iy, I.M[1], G.L[1], sy) : 0;
+        const uint32_t My = (DIM == 3) ? (uint32_t)I.M[1] : 1u;
+        const uint32_t rk = I.key_base + ((uint32_t)gx * My + (uint32_t)gy) * (uint32_t)MF;
+        const uint32_t nmax = (uint32_t)b.n;
+        int32_t q0 = (int32_t)min(b.start[rk + (uint32_t)fa[part]], nmax);
+        const int32_t q1 = (int32_t)min(b.start[rk + (uint32_t)fb[part] + 1u], nmax);
+        if (kSym) q0 = max(q0, (int32_t)h0);   // lower positions test this cell's particles
+        rq0[tid] = q0;
+        rlen[tid] = max(q1 - q0, 0);
+        rsh[tid][0] = sx;
+        rsh[tid][1] = (DIM == 3) ? sy : fs[part];
+        rsh[tid][2] = fs[part];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int r = 0; r < nrange; ++r) {
+            rpre[r] = acc;
+            acc += rlen[r];
+        }
+        nr_s = nrange;
+        tot_s = acc;
+    }
+    __syncthreads();
+    const int nr = nr_s, total = tot_s;
+    const bool once = total <= CAP;   // the whole window fits: stage it once for all home chunks
+    auto stage = [&](int c0) {
+        const int cn = min(CAP, total - c0);
+        for (int e = tid; e < cn; e += blockDim.x) {
+            const int ge = c0 + e;
+            int r = 0;
+            while (r + 1 < nr && rpre[r + 1] <= ge) ++r;
+            const int64_t q = (int64_t)rq0[r] + (ge - rpre[r]);
+            sp[e] = ldg_vec(b.posA + q);
+            sv[e] = ldg_vec(b.velA + q);
+        }
+    };
+    if (once) {
+        stage(0);
+        __syncthreads();
+    }
+    const T dt = inst_dt(I, T()), R2 = inst_R2(I, T());
+    for (int32_t hc = (int32_t)h0; hc < (int32_t)h1; hc += (int32_t)blockDim.x) {
+        const int32_t p = hc + tid;
+        const bool home = p < (int32_t)h1;
+        V P = {}, Q = {};
+        if (home) {
+            P = b.posA[p];
+            Q = b.velA[p];
+        }
+        const T xi[3] = {P.x, P.y, P.z};
+        const T vi[3] = {Q.x, Q.y, Q.z};
+        const uint32_t tag = R<T>::bits(P.w);
+        T bd = R<T>::inf();
+        uint32_t bid = 0xffffffffu;
+        // binary32: a home tests only higher positions; binary64: the whole
+        // window (the particle itself fails b > 0)
+        const int32_t lim = kSym ? p : -1;
+        // the candidates [e0, e1) of one range; SH: the range has a periodic image
+        auto scan = [&](auto has_shift, int e0, int e1, int c0, int32_t qoff, const T sh[3]) {
+            constexpr bool SH = decltype(has_shift)::value;
+            for (int e = e0; e < e1; ++e) {
+                const int32_t q = qoff + e;
+                if (q <= lim) continue;
+                const V Pj = sp[e - c0];
+                const V Qj = sv[e - c0];
+                const T xj[3] = {Pj.x, Pj.y, Pj.z};
+                const T vj[3] = {Qj.x, Qj.y, Qj.z};
+                T d2;
+                const bool pass = SH || MINIMG ? poca_test_sh<T, DIM, MINIMG>(G, xi, vi, xj, vj, sh, dt, R2, d2)
+                                               : poca_test_sh<T, DIM, false, false>(G, xi, vi, xj, vj, sh, dt, R2, d2);
+                if (pass) {
+                    const uint32_t idj = R<T>::bits(Pj.w);
+                    if (d2 < bd || (d2 == bd && idj < bid)) {
+                        bd = d2;
+                        bid = idj;
+                    }
+                    if (kSym) atomicMin(&b.bkey[q], partner_key<T>(d2, tag));
+                }
+            }
+        };
+        for (int c0 = 0; c0 < total; c0 += CAP) {
+            if (!once) {
+                __syncthreads();
+                stage(c0);
+                __syncthreads();
+            }
+            if (!home) continue;
+            const int c1 = min(total, c0 + CAP);
+            for (int r = 0; r < nr; ++r) {
+                const int e0 = max(rpre[r], c0), e1 = min(rpre[r] + rlen[r], c1);
+                if (e0 >= e1) continue;
+                const T sh[3] = {rsh[r][0], rsh[r][1], rsh[r][2]};
+                const int32_t qoff = rq0[r] - rpre[r];
+                if (sh[0] != (T)0 || sh[1] != (T)0 || sh[2] != (T)0)
+                    scan(std::true_type{}, e0, e1, c0, qoff, sh);
+                else
+                    scan(std::false_type{}, e0, e1, c0, qoff, sh);
+            }
+        }
+        if (home) {
+            if (kSym) {
+                if (bid != 0xffffffffu) atomicMin(&b.bkey[p], partner_key<T>(bd, bid));
+            } else {
+                b.bkey[p] = bid != 0xffffffffu ? partner_key<T>(bd, bid) : kNoPartner;
+            }
+        }
+    }
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kTileThreads) tile_search_kernel(Bufs<T> b) {
+    using V = typename Vec4<T>::type;
+    constexpr int CAP = TileCap<T>::value;
+    __shared__ GeoT<T> G;
+    __shared__ V sp[CAP];
+    __shared__ V sv[CAP];
+    __shared__ int rq0[kTileRanges], rlen[kTileRanges], rpre[kTileRanges];
+    __shared__ T rsh[kTileRanges][3];
+    __shared__ int nr_s, tot_s, inst_s;
+    __shared__ int64_t h0_s, h1_s;
+    const uint32_t kc = blockIdx.x;
+    if (threadIdx.x == 0) {
+        G.load(b.geo);
+        // instance of the key (instances own consecutive key ranges)
+        int lo = 0, hi = b.n_inst - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (b.inst[mid].key_base <= kc) lo = mid;
+            else hi = mid - 1;
+        }
+        inst_s = lo;
+        h0_s = min(b.start[kc], (uint32_t)b.n);
+        h1_s = min(b.start[kc + 1], (uint32_t)b.n);
+    }
+    __syncthreads();
+    const InstDev& I = b.inst[inst_s];
+    if (!I.tiled || h0_s >= h1_s) return;   // block-uniform
+    bool amb = false;
+    {
+        // ambiguity of the periodic images is a property of the cell's window
+        uint32_t rel = kc - I.key_base;
+        int g[3] = {0, 0, 0};
+        if (DIM == 3) {
+            g[2] = (int)(rel % (uint32_t)I.M[2]);
+            rel /= (uint32_t)I.M[2];
+        }
+        g[1] = (int)(rel % (uint32_t)I.M[1]);
+        g[0] = (int)(rel / (uint32_t)I.M[1]);
+        const int* kk = b.dyn[inst_s].k;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) amb = amb || window_1d(g[d], g[d], 1, I.M[d], kk[d], G.wall[d]).amb;
+    }
+    if (amb)
+        tile_search_cell<T, DIM, true>(b, G, I, inst_s, kc, h0_s, h1_s, sp, sv, rq0, rlen, rpre, rsh, nr_s, tot_s);
+    else
+        tile_search_cell<T, DIM, false>(b, G, I, inst_s, kc, h0_s, h1_s, sp, sv, rq0, rlen, rpre, rsh, nr_s, tot_s);
 }
 
 // Direct search of one particle (global loads), used by the staged kernel for
@@ -1543,6 +1780,10 @@ cudaError_t launch_search(const Bufs<T>& b, cudaStream_t s) {
     }
     // always launched: besides the direct search it records slot_of for every particle
     KMC_DIM_DISPATCH(b.geo.dim, search_kernel, b);
+    if (b.any_tiled && b.n_keys > 0) {
+        if (b.geo.dim == 3) tile_search_kernel<T, 3><<<b.n_keys, kTileThreads, 0, s>>>(b);
+        else tile_search_kernel<T, 2><<<b.n_keys, kTileThreads, 0, s>>>(b);
+    }
     return cudaGetLastError();
 }
 

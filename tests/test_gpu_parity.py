@@ -26,9 +26,10 @@ def _setup():
 
 
 def run_gpu_step(pos, vel, dim, n_cells, lo, hi, bc, lam, dt, seed, precision, step=0, sub_cells=(0, 0, 0),
-                 nsteps=1, staged=False, occ=0.0):
+                 nsteps=1, staged=False, occ=0.0, per_particle=False):
     import paper_1210_8084_gb300 as k
-    flags = k.KMC_FLAG_RECORD | (k.KMC_FLAG_STAGED_SEARCH if staged else 0)
+    flags = k.KMC_FLAG_RECORD | (k.KMC_FLAG_STAGED_SEARCH if staged else 0) | \
+        (k.KMC_FLAG_NO_TILE_SEARCH if per_particle else 0)
     cfg = k.make_config(dim_pos=dim, n_cells=n_cells, lo=lo, hi=hi, bc=bc, lam=lam, dt=dt, seed=seed,
                         precision=precision, flags=flags, sub_cells=sub_cells, occupancy_target=occ)
     sim = k.Simulation(cfg, pos, vel)
@@ -109,18 +110,21 @@ def make_inputs(name, n, dim, lo, hi):
     return pos, vel
 
 
-@pytest.mark.parametrize("staged", [False, True], ids=["direct", "staged"])
+@pytest.mark.parametrize("mode", ["default", "per_particle", "staged"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_one_step_parity(case, staged):
-    """One step from the same state; the direct search and the shared-memory
-    staged search (3-D tiles where they fit) must both match."""
+def test_one_step_parity(case, mode):
+    """One step from the same state.  default: one block per c-bin where the
+    search grid is not subdivided, per-thread search elsewhere; per_particle:
+    per-thread search everywhere; staged: shared-memory staged tiles (3-D
+    subdivided grids where they fit).  All must match the oracle."""
     _setup()
     name, n, dim, n_cells, lo, hi, bc, lam, dt, prec = case
     pos, vel = make_inputs(name, n, dim, lo, hi)
     if prec == 32:
         pos, vel = f32_state(pos, vel, lo, hi, bc)
     seed = 11
-    g = run_gpu_step(pos, vel, dim, n_cells, lo, hi, bc, lam, dt, seed, prec, staged=staged)
+    g = run_gpu_step(pos, vel, dim, n_cells, lo, hi, bc, lam, dt, seed, prec, staged=mode == "staged",
+                     per_particle=mode == "per_particle")
     o = oracle_step(pos, vel, dim, n_cells, lo, hi, bc, g["info"].R2, dt, seed, 0, prec == 32)
     assert (g["best"] >= 0).mean() > 0.02 or lam >= 1.0
     compare_step(g, o, prec, pos, vel, dim)
@@ -329,3 +333,36 @@ def test_exact_tie_in_d2_goes_to_lower_id(precision, staged):
     assert list(oracle.best_partners(P, pos.astype(np.float64), vel.astype(np.float64))) == [2, 2, 0]
     P.step = 1
     assert np.array_equal(best2, oracle.best_partners(P, p1.astype(np.float64), v1.astype(np.float64)))
+
+
+TILE_CASES = [
+    # name, n, dim, n_cells, lo, hi, bc, lam, dt, precision (unsubdivided grids: the tile search)
+    ("cubic3d_fp32_walls", 60_000, 3, (20, 6, 6), (0, 0, 0), (1, 0.3, 0.3), (WALL, PER, PER), 1e-3, 0.01, 32),
+    ("cubic3d_fp64", 30_000, 3, (16, 5, 5), (0, 0, 0), (1, 5 / 16, 5 / 16), (WALL, PER, PER), 1e-3, 0.0125, 64),
+    ("square2d_fp32_dense", 200_000, 2, (40, 40, 1), (0, 0, 0), (1, 1, 1), (WALL, WALL, PER), 5e-4, 0.005, 32),
+    ("periodic3d_fp32_3cells", 20_000, 3, (3, 3, 4), (0, 0, 0), (1, 1, 1), (PER, PER, PER), 1e-3, 0.02, 32),
+    ("tiny_cells_fp32", 7_777, 3, (30, 30, 4), (0, 0, 0), (1, 1, 0.2), (PER, PER, WALL), 1e-3, 0.003, 32),
+]
+
+
+@pytest.mark.parametrize("case", TILE_CASES, ids=[c[0] for c in TILE_CASES])
+def test_tile_search_matches_oracle_and_per_particle_search(case):
+    """Grids whose search cells are the c-bins (forced with sub_cells = 1):
+    the one-block-per-cell search gives the oracle's closest candidates and
+    pairs bit for bit, and the same keys as the per-thread search, for dense
+    and nearly empty cells, periodic windows that wrap (3 cells) and walls."""
+    _setup()
+    name, n, dim, n_cells, lo, hi, bc, lam, dt, prec = case
+    pos, vel = make_inputs(name, n, dim, lo, hi)
+    if prec == 32:
+        pos, vel = f32_state(pos, vel, lo, hi, bc)
+    seed = 5
+    sub = (1, 1, 1)
+    g = run_gpu_step(pos, vel, dim, n_cells, lo, hi, bc, lam, dt, seed, prec, sub_cells=sub)
+    d = run_gpu_step(pos, vel, dim, n_cells, lo, hi, bc, lam, dt, seed, prec, sub_cells=sub, per_particle=True)
+    o = oracle_step(pos, vel, dim, n_cells, lo, hi, bc, g["info"].R2, dt, seed, 0, prec == 32)
+    assert list(g["info"].sub_cells) == [1, 1, 1]
+    assert (g["best"] >= 0).mean() > 0.05
+    compare_step(g, o, prec, pos, vel, dim)
+    assert np.array_equal(g["best"], d["best"]) and np.array_equal(g["partner"], d["partner"])
+    assert np.array_equal(g["pos"], d["pos"]) and np.array_equal(g["vel"], d["vel"])
