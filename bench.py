@@ -127,6 +127,7 @@ def kernels_per_step(precision):
     two finalize kernels."""
     return 7
 FP32_LANES = 152 * 128       # GB300: SMs x FP32 lanes per SM
+FP64_TFLOPS_NOMINAL = 1.25   # GB300 dense binary64 (nominal)
 B_ALG_F32 = 72               # algorithmic bytes per particle-step (binary32 state)
 
 
@@ -261,12 +262,17 @@ def ours(args):
         # particle, binary64 tests all C_p.
         tests = (cand - 1.0) / 2.0 if w["precision"] == 32 else cand
         flops = FLOPS_PER_TEST * tests * n
-        sm_clock = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-        peak = FP32_LANES * 2 * sm_clock / 1e12
+        if w["precision"] == 32:
+            sm_clock = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+            peak = FP32_LANES * 2 * sm_clock / 1e12
+            peak_src = "fp32 lanes x 2 x max SM clock (derived)"
+        else:
+            peak = FP64_TFLOPS_NOMINAL
+            peak_src = "nominal GB300 binary64 rate"
         achieved = flops / t_dom / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_source": "fp32 lanes x 2 x max SM clock (derived)", "ms_per_launch": round(phases[dom], 4),
+                "peak_source": peak_src, "ms_per_launch": round(phases[dom], 4),
                 "algorithmic_flops_per_launch": int(flops), "candidates_per_particle": round(cand, 3),
                 "pair_tests_per_particle": round(tests, 3)}
     else:
