@@ -193,6 +193,22 @@ KMC_API int kmc_get_cell_keys(kmc_handle* h, int32_t* keys, int where);
  * last step (mutually closest), -1 if none.  Either pointer may be NULL. */
 KMC_API int kmc_get_partners(kmc_handle* h, int32_t* best, int32_t* partner, int where);
 
+/* Pick the implementation parameters of the search for a configuration by
+ * measurement (the paper has no counterpart: these parameters change speed
+ * only, never results).  For each candidate setting -- automatic subdivision
+ * at several occupancy targets, the per-c-bin tile search or the per-particle
+ * search where the grid is not subdivided, and the shared-memory staged search
+ * for 3-D grids -- a handle is created from (cfg, n, pos, vel, where) as in
+ * kmc_init, warmed up for one step and timed over trial_steps >= 1 steps with
+ * CUDA events on its stream, then freed; the caller's data are only read.
+ * *best receives a copy of *cfg with occupancy_target and flags (the
+ * KMC_FLAG_NO_TILE_SEARCH / KMC_FLAG_STAGED_SEARCH bits) of the fastest
+ * setting and sub_cells = 0 (automatic); *ms_per_step (may be NULL) its time.
+ * Device memory: one handle at a time.  Synchronises cfg->stream.  Returns the
+ * first error of kmc_init for an invalid configuration. */
+KMC_API int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, const void* vel, int where,
+                         int trial_steps, kmc_config* best, double* ms_per_step);
+
 /* Closest-candidate search without any allocation.  The paper has no
  * counterpart: this entry point exists for callers that may not allocate
  * device memory themselves or through this library, e.g. a host framework

@@ -41,7 +41,7 @@ PHASES = ("search", "move", "scan", "scatter", "moments", "finalize")
 ABI_FUNCTIONS = (
     "kmc_init", "kmc_step", "kmc_moments", "kmc_moments_size", "kmc_free", "kmc_sync",
     "kmc_last_error", "kmc_get_info", "kmc_get_state", "kmc_set_state", "kmc_get_cell_keys",
-    "kmc_get_partners", "kmc_step_profiled", "kmc_find_partners_noalloc", "kmc_window_size",
+    "kmc_get_partners", "kmc_step_profiled", "kmc_find_partners_noalloc", "kmc_window_size", "kmc_autotune",
 )
 KMC_STATIC_MAX_PARTICLES = 262144
 
@@ -142,6 +142,9 @@ def _load():
     L.kmc_window_size.restype = ctypes.c_int
     L.kmc_find_partners_noalloc.argtypes = [ctypes.POINTER(KmcConfig), ctypes.c_int64, vp, vp, vp]
     L.kmc_find_partners_noalloc.restype = ctypes.c_int
+    L.kmc_autotune.argtypes = [ctypes.POINTER(KmcConfig), ctypes.c_int64, vp, vp, ctypes.c_int, ctypes.c_int,
+                               ctypes.POINTER(KmcConfig), ctypes.POINTER(ctypes.c_double)]
+    L.kmc_autotune.restype = ctypes.c_int
     return L
 
 
@@ -247,6 +250,18 @@ def kmc_find_partners_noalloc(cfg, n, pos, vel, best):
     allocation (scratch in the library's fixed device array).  pos, vel, best
     are device arrays; returns the C status code (KMC_OK on success)."""
     return int(lib.kmc_find_partners_noalloc(ctypes.byref(cfg), int(n), _ptr(pos), _ptr(vel), _ptr(best)))
+
+
+def kmc_autotune(cfg, n, pos, vel, where=KMC_WHERE_HOST, trial_steps=3):
+    """Fastest search set-up for cfg on this state (same results for every
+    set-up): returns (config to pass to kmc_init, milliseconds per step)."""
+    best = KmcConfig()
+    ms = ctypes.c_double()
+    _check(lib.kmc_autotune(ctypes.byref(cfg), int(n), _ptr(pos), _ptr(vel), int(where), int(trial_steps),
+                            ctypes.byref(best), ctypes.byref(ms)))
+    if hasattr(cfg, "_keep"):
+        best._keep = cfg._keep   # the instance array the copy points to
+    return best, ms.value
 
 
 def kmc_moments_size(h, fields_mask):

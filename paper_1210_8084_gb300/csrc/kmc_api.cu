@@ -736,6 +736,63 @@ int kmc_moments(kmc_handle* h, double* out, int where, int mask) {
     return KMC_OK;
 }
 
+int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, const void* vel, int where, int trial_steps,
+                 kmc_config* best, double* ms_per_step) {
+    if (!cfg || !best) return fail(nullptr, KMC_EINVAL, "NULL argument");
+    if (trial_steps < 1) return fail(nullptr, KMC_EINVAL, "trial_steps < 1");
+    struct Trial {
+        double occ;
+        int flags;
+    };
+    const int keep = cfg->flags & ~(KMC_FLAG_NO_TILE_SEARCH | KMC_FLAG_STAGED_SEARCH);
+    std::vector<Trial> trials;
+    for (double occ : {0.25, 0.35, 0.5, 0.7, 1.0, 1.5}) trials.push_back({occ, keep});
+    trials.push_back({0.0, keep | KMC_FLAG_NO_TILE_SEARCH});
+    if (cfg->dim_pos == 3) trials.push_back({0.0, keep | KMC_FLAG_STAGED_SEARCH});
+    double best_ms = -1.0;
+    kmc_config pick = *cfg;
+    std::vector<std::vector<int>> tried;   // search set-up of every timed trial
+    for (const Trial& t : trials) {
+        kmc_config c = *cfg;
+        c.sub_cells[0] = c.sub_cells[1] = c.sub_cells[2] = 0;
+        c.occupancy_target = t.occ;
+        c.flags = t.flags;
+        kmc_handle* h = nullptr;
+        int rc = kmc_init(&c, n, pos, vel, where, &h);
+        if (rc != KMC_OK) {
+            if (best_ms < 0.0) return rc;   // the configuration itself is invalid
+            continue;                       // e.g. out of memory for this subdivision
+        }
+        // settings that end in an already timed set-up (same subdivision and
+        // search kernel for every instance) are not timed again
+        std::vector<int> setup;
+        for (const InstDev& I : h->inst_h) setup.insert(setup.end(), {I.s[0], I.s[1], I.s[2], I.tiled, I.staged});
+        if (std::find(tried.begin(), tried.end(), setup) != tried.end()) {
+            kmc_free(h);
+            continue;
+        }
+        tried.push_back(setup);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        float ms = 0.f;
+        bool ok = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+        ok = ok && kmc_step(h, 1, 1) == KMC_OK && cudaEventRecord(e0, h->stream) == cudaSuccess &&
+             kmc_step(h, trial_steps, 1) == KMC_OK && cudaEventRecord(e1, h->stream) == cudaSuccess &&
+             kmc_sync(h) == KMC_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        kmc_free(h);
+        if (!ok) return fail(nullptr, KMC_ECUDA, "autotune trial failed");
+        const double per = (double)ms / trial_steps;
+        if (best_ms < 0.0 || per < best_ms) {
+            best_ms = per;
+            pick = c;
+        }
+    }
+    *best = pick;
+    if (ms_per_step) *ms_per_step = best_ms;
+    return KMC_OK;
+}
+
 void kmc_free(kmc_handle* h) {
     if (!h) return;
     release(h);

@@ -366,3 +366,29 @@ def test_tile_search_matches_oracle_and_per_particle_search(case):
     compare_step(g, o, prec, pos, vel, dim)
     assert np.array_equal(g["best"], d["best"]) and np.array_equal(g["partner"], d["partner"])
     assert np.array_equal(g["pos"], d["pos"]) and np.array_equal(g["vel"], d["vel"])
+
+
+def test_autotune_picks_a_setup_with_identical_results():
+    """kmc_autotune only times set-ups (subdivision, tile or per-particle
+    search, staged tiles); a handle built from its choice gives the same
+    closest candidates, pairs and state as the default handle."""
+    _setup()
+    import paper_1210_8084_gb300 as k
+    from paper_1210_8084_gb300 import inputs
+    for n_cells, hi in (((200, 1, 1), (1, 1, 1)), ((40, 8, 8), (1, 0.2, 0.2))):
+        pos, vel = inputs.sod_tube(100_000, seed=4, hi=hi)
+        pos, vel = inputs.cast_state(pos, vel, np.float32, (0, 0, 0), hi, (WALL, PER, PER))
+        cfg = k.make_config(dim_pos=3, n_cells=n_cells, hi=hi, bc=(WALL, PER, PER), lam=1e-3, dt=0.2 / n_cells[0],
+                            seed=9, precision=32, flags=k.KMC_FLAG_RECORD)
+        best, ms = k.kmc_autotune(cfg, len(pos), pos, vel, k.KMC_WHERE_HOST, 2)
+        assert ms > 0 and best.flags & k.KMC_FLAG_RECORD
+        out = []
+        for c in (cfg, best):
+            sim = k.Simulation(c, pos, vel)
+            sim.step(3)
+            out.append((sim.partners(), sim.state()))
+            sim.close()
+        (b0, p0), (s0, v0) = out[0]
+        (b1, p1), (s1, v1) = out[1]
+        assert np.array_equal(b0, b1) and np.array_equal(p0, p1)
+        assert np.array_equal(s0, s1) and np.array_equal(v0, v1)
