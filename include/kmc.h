@@ -59,6 +59,11 @@ extern "C" {
 #define KMC_FLAG_NO_GRAPH 2 /* launch kernels directly instead of replaying a captured CUDA graph */
 #define KMC_FLAG_STAGED_SEARCH 4 /* stage tile neighbourhoods in shared memory (3-D; same results as the direct search) */
 #define KMC_FLAG_NO_TILE_SEARCH 8 /* search unsubdivided grids per particle too (default: one block per c-bin; same results) */
+#define KMC_FLAG_ADAPTIVE_DT 16  /* timestep dt(t) = dx_min / v_max(t) of each step's start state (Sect. "Simulation
+                                  * setup"; dx_min the smallest c-bin width, v_max the largest speed of the instance,
+                                  * |v|^2 = fma(vz, vz, fma(vy, vy, vx vx)) in the state precision, the quotient in
+                                  * binary64, rounded to binary32 for binary32 state); the configured dt is used only
+                                  * while every particle is at rest */
 
 #define KMC_MOM_RAW 1       /* per c-bin: N, Sum vx, Sum vy, Sum vz, Sum vx^2, Sum vy^2, Sum vz^2, Sum W */
 #define KMC_MOM_DERIVED 2   /* per c-bin: n, ux, uy, uz, T, p_kin, p_vir, p */
@@ -112,13 +117,14 @@ typedef struct kmc_info {
     int sub_cells[3];        /* subdivision of instance 0 */
     double R2;               /* instance 0: squared contact distance (2 r_eff)^2 = sigma / pi */
     double sigma;            /* instance 0 */
-    double dt;               /* instance 0 */
+    double dt;               /* instance 0: timestep of the next step */
     double vmax;             /* instance 0: largest speed of the current state */
     int window[3];           /* instance 0: search half-width in search cells for the next step */
     int64_t bytes_device;    /* device memory held by the handle */
     int64_t stage_tiles;     /* tiles of the shared-memory staged search (0: direct search only) */
     int tile_rows;           /* instance 0: y-rows per staged tile (0: searched directly) */
     int stage_cap;           /* candidates a staged tile holds in shared memory */
+    double time;             /* instance 0: simulated time since kmc_init or the last kmc_set_state */
 } kmc_info;
 
 /* Create a simulation.  pos and vel are n x 3 row-major arrays of float

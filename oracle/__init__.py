@@ -45,6 +45,8 @@ def lib():
         L.orc_philox4x32_10.restype = None
         L.orc_contact_R2.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.orc_contact_R2.restype = ctypes.c_double
+        L.orc_adaptive_dt.argtypes = [P, i64, dp, ctypes.c_double]
+        L.orc_adaptive_dt.restype = ctypes.c_double
         L.orc_cell_keys.argtypes = [P, i64, dp, ip, ip]
         L.orc_cell_keys.restype = None
         L.orc_pair_test.argtypes = [P, dp, dp, dp, dp, dp]
@@ -102,6 +104,12 @@ def philox4x32_10(ctr, key):
 
 def contact_R2(lam, sigma, nbar):
     return lib().orc_contact_R2(float(lam), float(sigma), float(nbar))
+
+
+def adaptive_dt(P, vel, dt_rest=0.0):
+    """dx_min / v_max of the state (Sect. "Simulation setup"); dt_rest when at rest."""
+    vel = np.ascontiguousarray(vel, dtype=np.float64).reshape(-1, 3)
+    return lib().orc_adaptive_dt(ctypes.byref(P), vel.shape[0], _d(vel), float(dt_rest))
 
 
 def _state(pos, vel=None):

@@ -9,6 +9,7 @@
  * Which passage each function follows:
  *   orc_philox4x32_10   Philox4x32-10 (Salmon et al., SC'11, Sect. 4.2 and Table 2)
  *   orc_contact_R2      Eq. 7 (lambda = 1/(sigma n)) and Eq. reff_lambda
+ *   orc_adaptive_dt     Sect. "Simulation setup": dt(t) = dx / v_max(t)
  *   orc_cell_keys       Sect. "Simulation setup": spatial binning into c-bins
  *   orc_pair_test       Sect. "Point of Closest Approach Method", Eqs. 5-6
  *                       (crossing number chi), Eqs. collision_time/collision_time2
@@ -76,6 +77,33 @@ double orc_contact_R2(double lambda, double sigma, double nbar)
      * Contact distance r_eff,A + r_eff,B = 2 r_eff  =>  R^2 = 4 r_eff^2 = sigma/pi. */
     double s = sigma > 0.0 ? sigma : 1.0 / (lambda * nbar);
     return s / M_PI;
+}
+
+/* Sect. "Simulation setup": the timestep follows the fastest particle,
+ * dt(t) = dx / v_max(t), so that no particle leaves its scattering
+ * neighbourhood within a step.  dx: the smallest c-bin width. */
+double orc_adaptive_dt(const orc_params* P, int64_t n, const double* vel, double dt_rest)
+{
+    double v2max = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        const double* v = vel + 3 * i;
+        double v2;
+        if (P->decide32) {
+            float x = (float)v[0], y = (float)v[1], z = (float)v[2];
+            float xx = x * x;
+            v2 = (double)fmaf(z, z, fmaf(y, y, xx));
+        } else {
+            v2 = fma(v[2], v[2], fma(v[1], v[1], v[0] * v[0]));
+        }
+        if (v2 > v2max) v2max = v2;
+    }
+    if (!(v2max > 0.0)) return dt_rest;
+    double dx = INFINITY;
+    for (int d = 0; d < P->dim; ++d) {
+        double w = (P->hi[d] - P->lo[d]) / P->n_cells[d];
+        if (w < dx) dx = w;
+    }
+    return dx / sqrt(v2max);
 }
 
 /* ------------------------------------------------------------------- keys */

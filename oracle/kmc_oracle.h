@@ -47,6 +47,13 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
  * (Eq. reff_lambda), i.e. R2 = sigma / pi.  nbar = N / V. */
 double orc_contact_R2(double lambda, double sigma, double nbar);
 
+/* Adaptive timestep (Sect. "Simulation setup"): dt = dx / v_max with dx the
+ * smallest c-bin width over the position dimensions and v_max the largest
+ * speed of the state.  |v|^2 = fma(vz, vz, fma(vy, vy, vx * vx)) in the
+ * decision precision, the root and the quotient in binary64.  Returns dt_rest
+ * when every particle is at rest. */
+double orc_adaptive_dt(const orc_params* P, int64_t n, const double* vel, double dt_rest);
+
 /* Cell index (per dim, clamped) and linear c-bin key c_x + n_x (c_y + n_y c_z). */
 void orc_cell_keys(const orc_params* P, int64_t n, const double* pos,
                    int32_t* key_out, int32_t* cidx_out /* n x 3, may be NULL */);

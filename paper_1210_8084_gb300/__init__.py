@@ -32,6 +32,7 @@ KMC_FLAG_RECORD = 1
 KMC_FLAG_NO_GRAPH = 2
 KMC_FLAG_STAGED_SEARCH = 4
 KMC_FLAG_NO_TILE_SEARCH = 8
+KMC_FLAG_ADAPTIVE_DT = 16
 KMC_MOM_RAW = 1
 KMC_MOM_DERIVED = 2
 KMC_MOM_GLOBAL = 4
@@ -95,6 +96,7 @@ class KmcInfo(ctypes.Structure):
         ("stage_tiles", ctypes.c_int64),
         ("tile_rows", ctypes.c_int),
         ("stage_cap", ctypes.c_int),
+        ("time", ctypes.c_double),
     ]
 
 

@@ -162,7 +162,7 @@ cudaError_t enqueue_step(kmc_handle* h, int want_moments, cudaEvent_t* ev = null
     }
     if ((e = mark(KMC_PHASE_FINALIZE)) != cudaSuccess) return e;
     if (want_moments) {
-        if ((e = launch_finalize(h->inst_d, h->n_inst, h->geo, h->acc, h->mom, h->glob, h->n_bins, s)) !=
+        if ((e = launch_finalize(h->inst_d, h->dyn_d, h->n_inst, h->geo, h->acc, h->mom, h->glob, h->n_bins, s)) !=
             cudaSuccess)
             return e;
     }
@@ -233,7 +233,8 @@ int check_device_error(kmc_handle* h) {
 // step searches +-1 cell) and about `target` particles per cell in the
 // densest c-bin, capped so the key count stays within a few times N.
 void choose_subdivision(const kmc_handle* h, InstDev& I, double vmax, uint32_t max_bin_occ) {
-    const double D = sqrt(I.R2) + 2.0 * vmax * I.dt;
+    const double dt0 = (I.adaptive && vmax > 0.0) ? I.dx_min / vmax : I.dt;   // timestep of step 0
+    const double D = sqrt(I.R2) + 2.0 * vmax * dt0;
     int smax[3] = {1, 1, 1};
     int nsub = 0;
     for (int d = 0; d < h->dim; ++d) {
@@ -356,7 +357,8 @@ int validate_config(const kmc_config* c, int64_t n) {
     }
     if (c->n_instances < 0) return fail(nullptr, KMC_EINVAL, "n_instances < 0");
     if (c->n_instances > 1 && !c->instances) return fail(nullptr, KMC_EINVAL, "instances is NULL");
-    if (c->flags & ~(KMC_FLAG_RECORD | KMC_FLAG_NO_GRAPH | KMC_FLAG_STAGED_SEARCH | KMC_FLAG_NO_TILE_SEARCH))
+    if (c->flags &
+        ~(KMC_FLAG_RECORD | KMC_FLAG_NO_GRAPH | KMC_FLAG_STAGED_SEARCH | KMC_FLAG_NO_TILE_SEARCH | KMC_FLAG_ADAPTIVE_DT))
         return fail(nullptr, KMC_EINVAL, "unknown flags");
     return KMC_OK;
 }
@@ -477,6 +479,9 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
         I.dt = insts[i].dt;
         I.R2f = (float)I.R2;
         I.dtf = (float)I.dt;
+        I.adaptive = (cfg->flags & KMC_FLAG_ADAPTIVE_DT) ? 1 : 0;
+        I.dx_min = INFINITY;
+        for (int d = 0; d < h->dim; ++d) I.dx_min = std::min(I.dx_min, g.L[d] / g.n[d]);
         I.seed_lo = (uint32_t)(insts[i].seed & 0xffffffffu);
         I.seed_hi = (uint32_t)(insts[i].seed >> 32);
         for (int d = 0; d < 3; ++d) {
@@ -714,7 +719,7 @@ int kmc_moments(kmc_handle* h, double* out, int where, int mask) {
         cudaError_t e = h->precision == 64 ? launch_moments<double>(make_bufs<double>(h), 0, h->stream)
                                            : launch_moments<float>(make_bufs<float>(h), 0, h->stream);
         KMC_CUDA(h, e);
-        KMC_CUDA(h, launch_finalize(h->inst_d, h->n_inst, h->geo, h->acc, h->mom, h->glob, h->n_bins, h->stream));
+        KMC_CUDA(h, launch_finalize(h->inst_d, h->dyn_d, h->n_inst, h->geo, h->acc, h->mom, h->glob, h->n_bins, h->stream));
         h->mom_state = 1;
     }
     const cudaMemcpyKind kind = where == KMC_WHERE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
@@ -825,7 +830,8 @@ int kmc_get_info(kmc_handle* h, kmc_info* info) {
     }
     info->R2 = I.R2;
     info->sigma = I.R2 * M_PI;
-    info->dt = I.dt;
+    info->dt = dy.dt;
+    info->time = dy.time;
     double v2;
     memcpy(&v2, &dy.vmax2_cur, sizeof(double));
     info->vmax = sqrt(v2);

@@ -47,6 +47,8 @@ struct InstDev {
     // shared memory before the search
     int staged;
     int tiled;           // search cells are the c-bins: one block per cell (tile_search_kernel)
+    int adaptive;        // timestep dx_min / v_max(t) per step (Sect. "Simulation setup")
+    double dx_min;       // smallest c-bin width over the position dimensions
     int tile_rows;
     int tiles_per_x;     // ceil(M[1] / tile_rows)
     uint32_t tile_base;  // first tile of the instance in the staged launch
@@ -56,6 +58,10 @@ struct InstDev {
 struct InstDyn {
     unsigned long long vmax2_cur;   // bits of the largest |v|^2 (binary64) of the current state
     unsigned long long vmax2_next;  // accumulated by the step's move kernel
+    double dt;                      // timestep of the next step (the configured one unless adaptive)
+    double dt_prev;                 // timestep of the step just taken (virial pressure)
+    double time;                    // simulated time since the state was set
+    float dtf;                      // dt rounded to binary32
     int k[3];                       // search half-window in search cells
     int pad;
 };
@@ -159,7 +165,7 @@ cudaError_t launch_cbin_hist(const Bufs<T>& b, uint32_t* hist, unsigned long lon
 cudaError_t launch_scan(uint32_t* count, uint32_t* start, uint32_t n_keys, uint32_t n_tiles,
                         unsigned long long* status, InstDyn* dyn, const InstDev* inst,
                         int n_inst, DevState* st, Geo geo, int bump_step, cudaStream_t s);
-cudaError_t launch_finalize(const InstDev* inst, int n_inst, Geo geo, const double* acc,
+cudaError_t launch_finalize(const InstDev* inst, const InstDyn* dyn, int n_inst, Geo geo, const double* acc,
                             double* mom, double* glob, int64_t n_bins, cudaStream_t s);
 
 }  // namespace kmc

@@ -61,8 +61,9 @@ struct R<double> {
 
 // Per-instance timestep and squared contact distance in the state precision
 // (binary32 copies are rounded once on the host, as the oracle rounds them).
-__device__ __forceinline__ float inst_dt(const InstDev& I, float) { return I.dtf; }
-__device__ __forceinline__ double inst_dt(const InstDev& I, double) { return I.dt; }
+// timestep of the current step (constant unless adaptive), in the state precision
+__device__ __forceinline__ float step_dt(const InstDyn& D, float) { return D.dtf; }
+__device__ __forceinline__ double step_dt(const InstDyn& D, double) { return D.dt; }
 __device__ __forceinline__ float inst_R2(const InstDev& I, float) { return I.R2f; }
 __device__ __forceinline__ double inst_R2(const InstDev& I, double) { return I.R2; }
 
@@ -228,6 +229,12 @@ __device__ __forceinline__ unsigned long long warp_max_bits(double v2, bool vali
     return m;
 }
 
+// |v|^2 in a fixed operation order (the adaptive timestep depends on its bits)
+template <typename T>
+__device__ __forceinline__ T speed2(T vx, T vy, T vz) {
+    return R<T>::fma(vz, vz, R<T>::fma(vy, vy, R<T>::mul(vx, vx)));
+}
+
 template <typename T>
 __device__ __forceinline__ void warp_vmax(InstDyn* dyn, bool valid, int inst, T v2) {
     const int inst0 = __shfl_sync(kFull, inst, 0);
@@ -377,8 +384,7 @@ __global__ void __launch_bounds__(kThreads) bin_kernel(Bufs<T> b) {
         b.key[p] = skey;
         b.slot[p] = slot;
     }
-    const T v2 = Q.x * Q.x + Q.y * Q.y + Q.z * Q.z;
-    warp_vmax<T>(b.dyn, valid, inst, v2);
+    warp_vmax<T>(b.dyn, valid, inst, speed2<T>(Q.x, Q.y, Q.z));
 }
 
 // The PoCA acceptance test of the ordered pair (i, j) and its closest-approach
@@ -765,7 +771,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) search_kerne
     const int* kk = b.dyn[inst].k;
     const T xi[3] = {P.x, P.y, P.z};
     const T vi[3] = {Q.x, Q.y, Q.z};
-    const T dt = inst_dt(I, T()), R2 = inst_R2(I, T());
+    const T dt = step_dt(b.dyn[inst], T()), R2 = inst_R2(I, T());
     int c[3] = {0, 0, 0}, g[3] = {0, 0, 0};
 #pragma unroll
     for (int d = 0; d < DIM; ++d) cell_and_search<T>(xi[d], G.lo[d], G.inv[d], G.n[d], I.s[d], c[d], g[d]);
@@ -914,7 +920,7 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
         stage(0);
         __syncthreads();
     }
-    const T dt = inst_dt(I, T()), R2 = inst_R2(I, T());
+    const T dt = step_dt(b.dyn[inst], T()), R2 = inst_R2(I, T());
     for (int32_t hc = (int32_t)h0; hc < (int32_t)h1; hc += (int32_t)blockDim.x) {
         const int32_t p = hc + tid;
         const bool home = p < (int32_t)h1;
@@ -1044,7 +1050,7 @@ __device__ __noinline__ unsigned long long search_one_direct(const Bufs<T>& b, c
     const int* kk = b.dyn[inst].k;
     const T xi[3] = {P.x, P.y, P.z};
     const T vi[3] = {Q.x, Q.y, Q.z};
-    const T dt = inst_dt(I, T()), R2 = inst_R2(I, T());
+    const T dt = step_dt(b.dyn[inst], T()), R2 = inst_R2(I, T());
     int c[3] = {0, 0, 0}, g[3] = {0, 0, 0};
 #pragma unroll
     for (int d = 0; d < DIM; ++d) cell_and_search<T>(xi[d], G.lo[d], G.inv[d], G.n[d], I.s[d], c[d], g[d]);
@@ -1331,7 +1337,7 @@ __global__ void __launch_bounds__(kStageThreads) search_staged_kernel(Bufs<T> b)
     __syncthreads();
 
     const int* kk = b.dyn[s_inst].k;
-    const T dt = inst_dt(I, T()), R2 = inst_R2(I, T());
+    const T dt = step_dt(b.dyn[s_inst], T()), R2 = inst_R2(I, T());
     if constexpr (sizeof(T) == 4) {
         staged_pairs(b, G, I, kk, sp, sv, reinterpret_cast<unsigned char*>(loc + (size_t)b.stage_rows * stride),
                      s_rowA0, s_rowL0, nr, s_xlo, s_nx, s_ylo, s_ny, s_h0, s_h1, stride, dt, R2);
@@ -1444,7 +1450,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 1) move_kernel(
     const uint32_t tag = R<T>::bits(P.w);   // ordering of tags = ordering of local ids
     const T x[3] = {P.x, P.y, P.z};
     const T v[3] = {Q.x, Q.y, Q.z};
-    const T dt = inst_dt(I, T());
+    const T dt = step_dt(b.dyn[inst], T());
     T xn[3] = {x[0], x[1], x[2]}, vn[3] = {v[0], v[1], v[2]};
     T W = (T)0;
     bool paired = false;
@@ -1543,8 +1549,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 1) move_kernel(
         }
     }
     (void)bin;
-    const T v2 = vn[0] * vn[0] + vn[1] * vn[1] + vn[2] * vn[2];
-    warp_vmax<T>(b.dyn, valid, inst, v2);
+    warp_vmax<T>(b.dyn, valid, inst, speed2<T>(vn[0], vn[1], vn[2]));
 }
 
 // Counting-sort scatter B -> A in search-key order.

@@ -35,7 +35,20 @@ __device__ void step_bookkeeping(InstDyn* dyn, const InstDev* inst, int n_inst, 
         dyn[i].vmax2_cur = nx;
         dyn[i].vmax2_next = 0ull;
         const double vmax = sqrt(__longlong_as_double((long long)nx));
-        const double D = sqrt(inst[i].R2) + 2.0 * vmax * inst[i].dt;
+        // timestep of the next step: the configured one, or dx_min / v_max(t)
+        // (adaptive; the previous one while every particle is at rest)
+        const double prev = dyn[i].dt;
+        double dt = inst[i].dt;
+        if (inst[i].adaptive) dt = vmax > 0.0 ? inst[i].dx_min / vmax : (prev > 0.0 ? prev : inst[i].dt);
+        if (bump) {
+            dyn[i].dt_prev = prev;
+            dyn[i].time += prev;
+        } else {   // state set: no step taken yet
+            dyn[i].dt_prev = dt;
+        }
+        dyn[i].dt = dt;
+        dyn[i].dtf = (float)dt;
+        const double D = sqrt(inst[i].R2) + 2.0 * vmax * dt;
         for (int d = 0; d < 3; ++d) {
             const double Dp = D * 1.001 + 1e-5 * geo.L[d];
             const double r = Dp / inst[i].w[d];
@@ -152,8 +165,9 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(uint32_t* __restrict
 
 // Derived per-c-bin moments (Eqs. vel_b, stress, 18, 19 with the readings
 // u = Sum v / N, v_rms^2 = <|v - u|^2>, T = v_rms^2 / 3, p = n T + virial).
-__global__ void finalize_bins_kernel(const InstDev* __restrict__ inst, Geo geo, const double* __restrict__ acc,
-                                     double* __restrict__ mom, int64_t n_bins, int64_t bins_per_inst) {
+__global__ void finalize_bins_kernel(const InstDev* __restrict__ inst, const InstDyn* __restrict__ dyn, Geo geo,
+                                     const double* __restrict__ acc, double* __restrict__ mom, int64_t n_bins,
+                                     int64_t bins_per_inst) {
     const int64_t bidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (bidx >= n_bins) return;
     const double* a = acc + bidx * kAccFields;
@@ -166,7 +180,7 @@ __global__ void finalize_bins_kernel(const InstDev* __restrict__ inst, Geo geo, 
         for (int k = 8; k < 16; ++k) o[k] = 0.0;
         return;
     }
-    const double dt = inst[bidx / bins_per_inst].dt;
+    const double dt = dyn[bidx / bins_per_inst].dt_prev;   // the step whose collisions W sums
     const double ux = a[1] / N, uy = a[2] / N, uz = a[3] / N;
     const double c2 = (a[4] + a[5] + a[6]) / N - (ux * ux + uy * uy + uz * uz);
     const double T = c2 / 3.0;
@@ -220,11 +234,11 @@ cudaError_t launch_scan(uint32_t* count, uint32_t* start, uint32_t n_keys, uint3
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const InstDev* inst, int n_inst, Geo geo, const double* acc, double* mom,
-                            double* glob, int64_t n_bins, cudaStream_t s) {
+cudaError_t launch_finalize(const InstDev* inst, const InstDyn* dyn, int n_inst, Geo geo, const double* acc,
+                            double* mom, double* glob, int64_t n_bins, cudaStream_t s) {
     if (n_bins == 0 || n_inst == 0) return cudaSuccess;
     const int64_t per = n_bins / n_inst;
-    finalize_bins_kernel<<<(unsigned)((n_bins + 255) / 256), 256, 0, s>>>(inst, geo, acc, mom, n_bins, per);
+    finalize_bins_kernel<<<(unsigned)((n_bins + 255) / 256), 256, 0, s>>>(inst, dyn, geo, acc, mom, n_bins, per);
     finalize_glob_kernel<<<n_inst, 256, 0, s>>>(acc, glob, per);
     return cudaGetLastError();
 }

@@ -55,8 +55,9 @@ def test_struct_layouts_match_c(built_lib):
 #include "kmc.h"
 int main(void) {
   printf("%zu %zu %zu\n", sizeof(kmc_config), sizeof(kmc_instance), sizeof(kmc_info));
-  printf("%zu %zu %zu %zu %zu\n", offsetof(kmc_config, stream), offsetof(kmc_config, flags),
-         offsetof(kmc_info, vmax), offsetof(kmc_info, bytes_device), offsetof(kmc_info, stage_cap));
+  printf("%zu %zu %zu %zu %zu %zu\n", offsetof(kmc_config, stream), offsetof(kmc_config, flags),
+         offsetof(kmc_info, vmax), offsetof(kmc_info, bytes_device), offsetof(kmc_info, stage_cap),
+         offsetof(kmc_info, time));
   return 0;
 }
 '''
@@ -70,7 +71,7 @@ int main(void) {
     offs = [int(x) for x in lines[1].split()]
     assert sizes == [ctypes.sizeof(k.KmcConfig), ctypes.sizeof(k.KmcInstance), ctypes.sizeof(k.KmcInfo)]
     assert offs == [k.KmcConfig.stream.offset, k.KmcConfig.flags.offset, k.KmcInfo.vmax.offset,
-                    k.KmcInfo.bytes_device.offset, k.KmcInfo.stage_cap.offset]
+                    k.KmcInfo.bytes_device.offset, k.KmcInfo.stage_cap.offset, k.KmcInfo.time.offset]
 
 
 def test_invalid_config_is_rejected_without_device(built_lib):

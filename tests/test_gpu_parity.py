@@ -392,3 +392,47 @@ def test_autotune_picks_a_setup_with_identical_results():
         (b1, p1), (s1, v1) = out[1]
         assert np.array_equal(b0, b1) and np.array_equal(p0, p1)
         assert np.array_equal(s0, s1) and np.array_equal(v0, v1)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_adaptive_timestep_matches_oracle(prec):
+    """KMC_FLAG_ADAPTIVE_DT (Sect. "Simulation setup": dt = dx / v_max(t)).
+    Before every step the device's timestep equals the oracle's dx / v_max of
+    the device state bit for bit (binary32 decisions use it rounded to
+    binary32 on both sides), the elapsed time is the sum of the steps, and the
+    step's closest candidates, pairs and virial pressure match the oracle."""
+    _setup()
+    import oracle
+    import paper_1210_8084_gb300 as k
+    from paper_1210_8084_gb300 import inputs
+    n, n_cells, lo, hi, bc = 100_000, (100, 1, 1), (0, 0, 0), (1, 1, 1), (WALL, PER, PER)
+    pos, vel = inputs.sod_tube(n, seed=21)
+    if prec == 32:
+        pos, vel = f32_state(pos, vel, lo, hi, bc)
+    cfg = k.make_config(dim_pos=3, n_cells=n_cells, lo=lo, hi=hi, bc=bc, lam=1e-3, dt=1.0, seed=3, precision=prec,
+                        flags=k.KMC_FLAG_RECORD | k.KMC_FLAG_ADAPTIVE_DT)
+    sim = k.Simulation(cfg, pos, vel)
+    t = 0.0
+    for s in range(4):
+        p, v = sim.state()
+        p, v = p.astype(np.float64), v.astype(np.float64)
+        info = sim.info()
+        P = oracle.make_params(3, n_cells, lo, hi, bc, R2=info.R2, dt=1.0, seed=3, step=s, decide32=prec == 32)
+        dt = oracle.adaptive_dt(P, v, 1.0)
+        assert info.dt == dt, (s, info.dt, dt)
+        assert info.time == t
+        # binary32: |v|^2 is rounded to binary32 before the binary64 root and quotient
+        assert dt == pytest.approx(0.01 / np.linalg.norm(v, axis=1).max(), rel=1e-12 if prec == 64 else 1e-6)
+        P.dt = dt
+        sim.step(1, want_moments=1)
+        best, partner = sim.partners()
+        ob = oracle.best_partners(P, p, v)
+        assert np.array_equal(best, ob), s
+        paired = oracle.collide_move(P, p, v, ob)[3]
+        assert np.array_equal(partner, paired), s
+        t += dt
+        # p_vir = Sum W / (2 d V_c dt) with the dt of the step that produced W
+        raw, der, glob = sim.moments()
+        assert np.allclose(der[:, 6], raw[:, 7] / (2 * 3 * 0.01 * dt), rtol=1e-12, atol=0)
+    assert sim.info().time == t
+    sim.close()

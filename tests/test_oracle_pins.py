@@ -491,3 +491,56 @@ def test_sod_tube_against_exact_riemann_small():
         pos, vel, best, paired, raw, der, glob, npairs = oracle.step(P, pos, vel)
     err = _sod_l1(raw, n, steps * P.dt, 25)
     assert err["n"] < 0.095 and err["p"] < 0.125 and err["T"] < 0.125, err
+
+
+# ------------------------------------------------------------ adaptive timestep
+# Sect. "Simulation setup": dt(t) = dx / v_max(t), v_max the speed of the
+# fastest particle; dx the smallest c-bin width (reading for non-square bins).
+
+def test_adaptive_dt_closed_form_345():
+    """Fastest particle (3, 4, 0): |v| = 5; c-bins 0.1 x 0.05 -> dt = 0.05 / 5."""
+    import oracle
+    P = oracle.make_params(2, (10, 20, 1), (0, 0, 0), (1, 1, 1), (0, 0, 0), R2=0.01, dt=1e-3, seed=0)
+    vel = np.array([[1.0, 0.0, 0.0], [3.0, 4.0, 0.0], [0.0, 0.0, -2.5], [-4.0, 1.0, 1.0]])
+    assert oracle.adaptive_dt(P, vel) == pytest.approx(0.01, rel=2 ** -52)
+    P32 = oracle.make_params(2, (10, 20, 1), (0, 0, 0), (1, 1, 1), (0, 0, 0), R2=0.01, dt=1e-3, seed=0, decide32=True)
+    assert oracle.adaptive_dt(P32, vel) == pytest.approx(0.01, rel=2 ** -52)
+
+
+def test_adaptive_dt_at_rest_keeps_given_step():
+    import oracle
+    P = oracle.make_params(3, (4, 4, 4), (0, 0, 0), (1, 1, 1), (0, 0, 0), R2=0.01, dt=1e-3, seed=0)
+    assert oracle.adaptive_dt(P, np.zeros((5, 3)), 0.125) == 0.125
+
+
+def test_adaptive_dt_no_particle_leaves_its_neighbourhood():
+    """Free flight over one adaptive step moves no particle by more than one
+    c-bin width in any dimension (the purpose the paper gives for the rule)."""
+    import oracle
+    from paper_1210_8084_gb300 import inputs
+    pos, vel = inputs.periodic_box(5000, seed=4, hi=(1.0, 0.5, 0.25))
+    P = oracle.make_params(3, (20, 10, 5), (0, 0, 0), (1.0, 0.5, 0.25), (0, 0, 0), R2=1e-12, dt=1.0, seed=0)
+    dt = oracle.adaptive_dt(P, vel)
+    P.dt = dt
+    p2, v2 = oracle.step(P, pos, vel)[:2]
+    assert np.array_equal(v2, vel)                      # R2 ~ 0: no collisions
+    w = np.array([0.05, 0.05, 0.05])
+    d = np.abs(p2 - pos)
+    d = np.minimum(d, np.array([1.0, 0.5, 0.25]) - d)  # periodic
+    assert (d <= w * (1 + 1e-12)).all()
+    assert np.max(np.linalg.norm(vel, axis=1)) * dt == pytest.approx(0.05, rel=1e-12)
+
+
+def test_adaptive_dt_follows_the_largest_speed_of_a_maxwellian():
+    """N Maxwell speeds (sigma = 1): dx / dt is the largest of N chi(3)
+    samples, inside the 1 % - 99 % band of that maximum's exact distribution
+    F(x)^N (a mean or rms speed would be far below it)."""
+    import oracle
+    from scipy import stats
+    n = 2_000_000
+    vel = np.random.default_rng(12).normal(0.0, 1.0, (n, 3))
+    P = oracle.make_params(3, (8, 8, 8), (0, 0, 0), (1, 1, 1), (0, 0, 0), R2=0.01, dt=1.0, seed=0)
+    vmax = (1.0 / 8) / oracle.adaptive_dt(P, vel)
+    lo = stats.chi(3).ppf(0.01 ** (1.0 / n))
+    hi = stats.chi(3).ppf(0.99 ** (1.0 / n))
+    assert lo < vmax < hi, (lo, vmax, hi)
