@@ -16,6 +16,8 @@ Recipes (units m = 1, k_B = 1, v_th = sqrt(T_left / m) = 1):
     all at rest with T = 1; 3-D velocities, z = 0.
   * Homogeneous periodic box: uniform positions, Maxwellian (T) or
     mono-energetic (|v| = v_in, isotropic directions, Sect. "Equilibration").
+  * Noh implosion (Sect. "Noh test"): uniform density, radial inflow v0 towards
+    the corner at the origin, cold (T0 << v0^2), reflective walls.
 """
 import math
 
@@ -91,6 +93,22 @@ def periodic_box(n, seed=0, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), T=1.0, v_in=
         d = gv.normal(0.0, 1.0, (n, 3))
         d /= np.linalg.norm(d, axis=1, keepdims=True)
         vel = v_in * d
+    return pos, vel
+
+
+def noh(n, seed=0, dim_pos=3, L=1.0, v0=1.0, T0=1e-6):
+    """Noh implosion (Sect. "Noh test"): uniform positions in [0, L]^dim with
+    the origin at the corner (walls at 0 are the symmetry planes), velocity
+    -v0 r_hat towards the origin in the position dimensions plus a small
+    Maxwellian spread of temperature T0 per component ("zero pressure")."""
+    g = _rng(seed, 1)
+    pos = np.zeros((n, 3))
+    pos[:, :dim_pos] = L * g.random((n, dim_pos))
+    pos = np.minimum(pos, L)
+    r = np.linalg.norm(pos[:, :dim_pos], axis=1, keepdims=True)
+    rhat = np.zeros((n, 3))
+    rhat[:, :dim_pos] = pos[:, :dim_pos] / np.maximum(r, 1e-300)
+    vel = -v0 * rhat + _rng(seed, 2).normal(0.0, math.sqrt(T0), (n, 3))
     return pos, vel
 
 

@@ -88,6 +88,7 @@ CASES = [
      0.2 / 128, 32),
     ("box3d_fp64_ragged", 12_345, 3, (5, 4, 3), (-1, 0, 2), (1, 0.5, 3), (PER, WALL, PER), 1e-2, 5e-3, 64),
     ("box2d_fp32_periodic_2cells", 3_001, 2, (2, 2, 1), (0, 0, 0), (1, 1, 1), (PER, PER, PER), 1e-2, 5e-3, 32),
+    ("noh3d_fp32_walls", 60_000, 3, (16, 16, 16), (0, 0, 0), (1, 1, 1), (WALL, WALL, WALL), 1e-3, 0.02, 32),
 ]
 
 
@@ -102,6 +103,8 @@ def make_inputs(name, n, dim, lo, hi):
     from paper_1210_8084_gb300 import inputs
     if name.startswith("quad"):
         return inputs.quadrants_2d(n, seed=3)
+    if name.startswith("noh"):
+        return inputs.noh(n, seed=3, dim_pos=dim, L=hi[0], v0=1.0, T0=0.01)
     if name.startswith("sod"):
         return inputs.sod_tube(n, seed=3, lo=lo, hi=hi)
     pos, vel = inputs.periodic_box(n, seed=3, lo=lo, hi=hi)

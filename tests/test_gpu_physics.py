@@ -181,3 +181,53 @@ def test_mono_energetic_gas_relaxes_to_maxwell_on_device():
     ks = stats.kstest(speed[::50] / math.sqrt(T), stats.chi(3).cdf)
     assert ks.pvalue > 1e-3, ks
     assert glob[0, 1] == pytest.approx(0.5 * n * v_in ** 2, rel=1e-5)
+
+
+def test_noh_spherical_implosion_against_exact_solution():
+    """3-D spherical Noh implosion (Sect. "Noh test"), gamma = 5/3: inside the
+    shock the gas is at rest with density 64 n0 and temperature v0^2 / 3; the
+    shock sits at v0 t / 3; the infall ahead of it has density n0 (1 + v0 t / r)^2."""
+    _setup()
+    import paper_1210_8084_gb300 as k
+    from paper_1210_8084_gb300 import inputs
+    from oracle import noh
+    n, nc, v0 = 4_000_000, 80, 1.0
+    dt = 0.2 / nc / v0
+    steps = 120
+    pos, vel = inputs.noh(n, seed=6, L=1.0, v0=v0, T0=1e-6)
+    wall3 = (1, 1, 1)
+    pos, vel = inputs.cast_state(pos, vel, np.float32, (0, 0, 0), (1, 1, 1), wall3)
+    sim = k.Simulation(k.make_config(dim_pos=3, n_cells=(nc, nc, nc), bc=wall3, lam=1e-3, dt=dt, seed=6,
+                                     precision=32), pos, vel)
+    e0 = sim.moments()[2][0, 1]
+    sim.step(steps, want_moments=1)
+    raw, der, glob = sim.moments()
+    sim.close()
+    t = steps * dt
+    g = 5.0 / 3.0
+    rs = noh.shock_radius(t, v0, g)
+    c = (np.arange(nc) + 0.5) / nc
+    X, Y, Z = np.meshgrid(c, c, c, indexing="ij")
+    r = np.sqrt(X ** 2 + Y ** 2 + Z ** 2).transpose(2, 1, 0).ravel()   # rows: c_x fastest
+    N = raw[:, 0]
+    n0 = n / 1.0
+    dens = N * nc ** 3
+    u = raw[:, 1:4] / np.maximum(N, 1)[:, None]
+    c2 = raw[:, 4:7].sum(1) / np.maximum(N, 1) - (u ** 2).sum(1)
+    inner = r < 0.6 * rs
+    ahead = (r > 1.6 * rs) & (r < 2.4 * rs)
+    n_in = dens[inner].sum() / inner.sum()
+    T_in = (raw[inner, 4:7].sum() - (raw[inner, 1:4].sum(0) ** 2).sum() / N[inner].sum()) / N[inner].sum() / 3
+    n_ahead = dens[ahead].sum() / noh.profile(r[ahead], t, v0, n0, g, 3)[0].sum()
+    print(f"Noh: n_in/n0 {n_in / n0:.2f} (64), T_in {T_in:.3f} ({(g - 1) * v0 ** 2 / 2:.3f}), n_ahead/exact {n_ahead:.3f}")
+    assert abs(n_in / n0 / noh.shocked_density(1.0, g, 3) - 1) < 0.15
+    assert abs(T_in / ((g - 1) * 0.5 * v0 ** 2) - 1) < 0.15
+    assert abs(n_ahead - 1) < 0.1
+    # shock position: the density falls below half of the plateau between 0.8 and 1.25 r_s
+    shells = np.linspace(0.0, 2 * rs, 41)
+    idx = np.digitize(r, shells) - 1
+    prof = np.array([dens[idx == i].mean() if np.any(idx == i) else np.nan for i in range(40)])
+    mid = 0.5 * (shells[1:] + shells[:-1])
+    half = mid[np.nanargmax(prof < 0.5 * n_in * (1 + 1e-9))] if np.any(prof < 0.5 * n_in) else np.inf
+    assert 0.8 * rs < half < 1.25 * rs, (half, rs)
+    assert abs(glob[0, 1] / e0 - 1) < 1e-5
