@@ -59,6 +59,9 @@ extern "C" {
 #define KMC_FLAG_NO_GRAPH 2 /* launch kernels directly instead of replaying a captured CUDA graph */
 #define KMC_FLAG_STAGED_SEARCH 4 /* stage tile neighbourhoods in shared memory (3-D; same results as the direct search) */
 #define KMC_FLAG_NO_TILE_SEARCH 8 /* search unsubdivided grids per particle too (default: one block per c-bin; same results) */
+#define KMC_FLAG_VELOCITY_2D 32  /* dim_pos = 2 only: velocities in the (x, y) plane (the paper's 2-D runs, f = 2,
+                                  * gamma = 2): v_z must be 0, outgoing directions isotropic in the plane
+                                  * (azimuth 2 pi u2 of the pair's draw), T = m v_rms^2 / 2 */
 #define KMC_FLAG_ADAPTIVE_DT 16  /* timestep dt(t) = dx_min / v_max(t) of each step's start state (Sect. "Simulation
                                   * setup"; dx_min the smallest c-bin width, v_max the largest speed of the instance,
                                   * |v|^2 = fma(vz, vz, fma(vy, vy, vx vx)) in the state precision, the quotient in

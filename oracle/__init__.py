@@ -28,6 +28,7 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("step", ctypes.c_uint32),
         ("decide32", ctypes.c_int),
+        ("vel_dim", ctypes.c_int),
     ]
 
 
@@ -77,7 +78,7 @@ def _i(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if a is not None else None
 
 
-def make_params(dim, n_cells, lo, hi, bc, R2, dt, seed=0, step=0, decide32=False):
+def make_params(dim, n_cells, lo, hi, bc, R2, dt, seed=0, step=0, decide32=False, vel_dim=3):
     p = Params()
     p.dim = int(dim)
     for d in range(3):
@@ -90,6 +91,7 @@ def make_params(dim, n_cells, lo, hi, bc, R2, dt, seed=0, step=0, decide32=False
     p.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
     p.step = int(step) & 0xFFFFFFFF
     p.decide32 = 1 if decide32 else 0
+    p.vel_dim = int(vel_dim)
     return p
 
 

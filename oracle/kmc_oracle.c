@@ -484,6 +484,11 @@ void orc_collide_move(const orc_params* P, int64_t n, const double* pos,
             double sth = 2.0 * sqrt(u1 * (1.0 - u1));
             double phi = 2.0 * M_PI * u2;
             double nhat[3] = {sth * cos(phi), sth * sin(phi), cth};
+            if (P->vel_dim == 2) {   /* isotropic in the plane: azimuth only */
+                nhat[0] = cos(phi);
+                nhat[1] = sin(phi);
+                nhat[2] = 0.0;
+            }
             /* CM frame: outgoing velocities opposite, |v_rel| preserved */
             for (int d = 0; d < 3; ++d) {
                 double vcm = 0.5 * (v[d] + vj[d]);
@@ -540,7 +545,7 @@ void orc_moments(const orc_params* P, int64_t n, const double* pos, const double
         /* mean square peculiar speed: <|v|^2> - |u|^2, i.e. v_rms^2 of Eq. 19
          * read as (1/N) Sum |v_i - v_b|^2 */
         double c2 = (m[4] + m[5] + m[6]) / N - (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        double T = c2 / 3.0;            /* f = 3 velocity degrees of freedom, m = 1 */
+        double T = c2 / (P->vel_dim == 2 ? 2.0 : 3.0);   /* f velocity degrees of freedom, m = 1 */
         double nd = N / Vc;
         double pkin = nd * T;           /* kinetic part of Eq. stress: -trace/3V */
         /* collisional part: (1/2)(1/dt) Sum_i Sum_j r_ij . dp_i, trace over the

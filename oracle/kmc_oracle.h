@@ -37,6 +37,7 @@ typedef struct {
     uint64_t seed;      /* Philox key: (low 32 bits, high 32 bits) */
     uint32_t step;      /* Philox counter word 1 */
     int decide32;       /* 1: decisions in binary32; 0: binary64 */
+    int vel_dim;        /* velocity components: 3, or 2 (x, y; the paper's 2-D runs, f = 2) */
 } orc_params;
 
 /* Philox4x32-10 block function (Salmon, Moraes, Dror, Shaw, SC'11). */

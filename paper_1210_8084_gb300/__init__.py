@@ -33,6 +33,7 @@ KMC_FLAG_NO_GRAPH = 2
 KMC_FLAG_STAGED_SEARCH = 4
 KMC_FLAG_NO_TILE_SEARCH = 8
 KMC_FLAG_ADAPTIVE_DT = 16
+KMC_FLAG_VELOCITY_2D = 32
 KMC_MOM_RAW = 1
 KMC_MOM_DERIVED = 2
 KMC_MOM_GLOBAL = 4

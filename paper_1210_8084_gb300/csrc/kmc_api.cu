@@ -358,8 +358,11 @@ int validate_config(const kmc_config* c, int64_t n) {
     if (c->n_instances < 0) return fail(nullptr, KMC_EINVAL, "n_instances < 0");
     if (c->n_instances > 1 && !c->instances) return fail(nullptr, KMC_EINVAL, "instances is NULL");
     if (c->flags &
-        ~(KMC_FLAG_RECORD | KMC_FLAG_NO_GRAPH | KMC_FLAG_STAGED_SEARCH | KMC_FLAG_NO_TILE_SEARCH | KMC_FLAG_ADAPTIVE_DT))
+        ~(KMC_FLAG_RECORD | KMC_FLAG_NO_GRAPH | KMC_FLAG_STAGED_SEARCH | KMC_FLAG_NO_TILE_SEARCH | KMC_FLAG_ADAPTIVE_DT |
+          KMC_FLAG_VELOCITY_2D))
         return fail(nullptr, KMC_EINVAL, "unknown flags");
+    if ((c->flags & KMC_FLAG_VELOCITY_2D) && c->dim_pos != 2)
+        return fail(nullptr, KMC_EINVAL, "2-D velocities need dim_pos = 2");
     return KMC_OK;
 }
 
@@ -435,6 +438,7 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
 
     Geo& g = h->geo;
     g.dim = h->dim;
+    g.vdim = (cfg->flags & KMC_FLAG_VELOCITY_2D) ? 2 : 3;
     for (int d = 0; d < 3; ++d) {
         const bool used = d < h->dim;
         g.n[d] = used ? cfg->n_cells[d] : 1;

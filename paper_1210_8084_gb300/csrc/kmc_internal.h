@@ -68,6 +68,7 @@ struct InstDyn {
 
 struct Geo {
     int dim;
+    int vdim;   // velocity components: 3, or 2 (x, y only: the paper's 2-D runs)
     int n[3];
     int bc[3];
     double lo[3], hi[3], L[3], inv_dx[3];

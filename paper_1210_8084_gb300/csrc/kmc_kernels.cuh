@@ -110,7 +110,9 @@ struct GeoT {
     T lo[3], hi[3], inv[3], L[3], hL[3];
     int n[3];
     bool wall[3];
+    int vdim;
     __device__ __forceinline__ void load(const Geo& g) {
+        vdim = g.vdim;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             lo[d] = (T)g.lo[d];
@@ -342,6 +344,7 @@ __global__ void __launch_bounds__(kThreads) pack_kernel(Bufs<T> b, const T* __re
     bool ok = true;
 #pragma unroll
     for (int d = 0; d < 3; ++d) ok = ok && isfinite(x[d]) && isfinite(v[d]);
+    if (b.geo.vdim == 2) ok = ok && v[2] == (T)0;   // 2-D velocities: no z component
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         const T lo = (T)b.geo.lo[d], hi = (T)b.geo.hi[d];
@@ -1491,7 +1494,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 1) move_kernel(
         const T sth = (T)2 * R<T>::sqrt_(u1 * ((T)1 - u1));
         T sphi, cphi;
         sincos_2pi(u2, &sphi, &cphi);
-        const T nh[3] = {sth * cphi, sth * sphi, cth};
+        // isotropic opposite directions: on the sphere, or in the plane for 2-D velocities
+        const T nh[3] = {G.vdim == 2 ? cphi : sth * cphi, G.vdim == 2 ? sphi : sth * sphi,
+                         G.vdim == 2 ? (T)0 : cth};
         const T h = (T)0.5 * R<T>::sqrt_(b3);
 #pragma unroll
         for (int d = 0; d < 3; ++d) {

@@ -70,6 +70,7 @@ int run(const kmc_config* cfg, int64_t n, const void* pos, const void* vel, int3
     // geometry and the single instance (Eq. 7 and Eq. reff_lambda for R^2)
     Geo g{};
     g.dim = cfg->dim_pos;
+    g.vdim = (cfg->flags & KMC_FLAG_VELOCITY_2D) ? 2 : 3;
     double V3 = 1.0;
     for (int d = 0; d < 3; ++d) {
         const bool used = d < g.dim;

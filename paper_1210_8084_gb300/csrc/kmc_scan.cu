@@ -183,7 +183,7 @@ __global__ void finalize_bins_kernel(const InstDev* __restrict__ inst, const Ins
     const double dt = dyn[bidx / bins_per_inst].dt_prev;   // the step whose collisions W sums
     const double ux = a[1] / N, uy = a[2] / N, uz = a[3] / N;
     const double c2 = (a[4] + a[5] + a[6]) / N - (ux * ux + uy * uy + uz * uz);
-    const double T = c2 / 3.0;
+    const double T = c2 / (geo.vdim == 2 ? 2.0 : 3.0);   // f velocity degrees of freedom
     const double nd = N / Vc;
     const double pkin = nd * T;
     const double pvir = a[7] / (2.0 * geo.dim * Vc * dt);

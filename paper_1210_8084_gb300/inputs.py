@@ -32,8 +32,9 @@ def _rng(seed, stream):
 
 
 def sod_tube(n, seed=0, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), split=0.5, rho=(1.0, 0.125), p=(1.0, 0.1),
-             dim_pos=3):
-    """(pos, vel) float64 arrays of shape (n, 3), left particles first."""
+             dim_pos=3, vel_dim=3):
+    """(pos, vel) float64 arrays of shape (n, 3), left particles first.
+    vel_dim = 2: velocities in the (x, y) plane (v_z = 0)."""
     lo = np.asarray(lo, dtype=np.float64)
     hi = np.asarray(hi, dtype=np.float64)
     vol_l = (split - lo[0]) / (hi[0] - lo[0])
@@ -60,6 +61,8 @@ def sod_tube(n, seed=0, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), split=0.5, rho=(
     gv = _rng(seed, 2)
     vel[:n_l] = gv.normal(0.0, math.sqrt(T[0]), (n_l, 3))
     vel[n_l:] = gv.normal(0.0, math.sqrt(T[1]), (n_r, 3))
+    if vel_dim == 2:
+        vel[:, 2] = 0.0
     return pos, vel
 
 
@@ -80,7 +83,9 @@ def quadrants_2d(n, seed=0, densities=(1.0, 0.5, 0.25, 0.125), T=1.0):
     return pos, vel
 
 
-def periodic_box(n, seed=0, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), T=1.0, v_in=None):
+def periodic_box(n, seed=0, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), T=1.0, v_in=None, vel_dim=3):
+    """Uniform positions; Maxwellian (per-component variance T) or
+    mono-energetic (|v| = v_in) velocities, isotropic in vel_dim components."""
     g = _rng(seed, 1)
     lo = np.asarray(lo, dtype=np.float64)
     hi = np.asarray(hi, dtype=np.float64)
@@ -89,8 +94,12 @@ def periodic_box(n, seed=0, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), T=1.0, v_in=
     gv = _rng(seed, 2)
     if v_in is None:
         vel = gv.normal(0.0, math.sqrt(T), (n, 3))
+        if vel_dim == 2:
+            vel[:, 2] = 0.0
     else:
         d = gv.normal(0.0, 1.0, (n, 3))
+        if vel_dim == 2:
+            d[:, 2] = 0.0
         d /= np.linalg.norm(d, axis=1, keepdims=True)
         vel = v_in * d
     return pos, vel

@@ -544,3 +544,61 @@ def test_adaptive_dt_follows_the_largest_speed_of_a_maxwellian():
     lo = stats.chi(3).ppf(0.01 ** (1.0 / n))
     hi = stats.chi(3).ppf(0.99 ** (1.0 / n))
     assert lo < vmax < hi, (lo, vmax, hi)
+
+
+# ------------------------------------------------- 2-D velocities (f = 2, gamma = 2)
+# The paper's 2-D runs (gamma = 2, Sect. "Sod test"): velocities in the plane,
+# outgoing directions isotropic in the plane.
+
+def _box2d(n, seed, **kw):
+    from paper_1210_8084_gb300 import inputs
+    pos, vel = inputs.periodic_box(n, seed=seed, vel_dim=2, **kw)
+    pos[:, 2] = 0.0
+    return pos, vel
+
+
+def test_velocity2d_collisions_conserve_and_stay_in_plane():
+    import oracle
+    pos, vel = _box2d(20_000, 31)
+    P = oracle.make_params(2, (30, 30, 1), (0, 0, 0), (1, 1, 1), (0, 0, 0), R2=2e-4, dt=0.01, seed=5,
+                           vel_dim=2)
+    p, v = pos, vel
+    npairs = 0
+    for s in range(5):
+        P.step = s
+        p, v, best, paired, raw, der, glob, k = oracle.step(P, p, v)
+        npairs += k
+    assert npairs > 1000
+    assert np.all(v[:, 2] == 0.0)
+    assert np.allclose(v.sum(0), vel.sum(0), atol=1e-9)
+    assert (v ** 2).sum() == pytest.approx((vel ** 2).sum(), rel=1e-12)
+
+
+def test_velocity2d_gas_relaxes_to_the_2d_maxwell_speed_law():
+    """Mono-energetic in the plane, |v| = v_in: the speeds relax to the
+    Rayleigh law with T = v_in^2 / 2 (two degrees of freedom); a scatter that
+    left the plane or favoured a direction would not."""
+    import oracle
+    from scipy import stats
+    v_in = 2.0
+    pos, vel = _box2d(30_000, 32, v_in=v_in)
+    P = oracle.make_params(2, (40, 40, 1), (0, 0, 0), (1, 1, 1), (0, 0, 0), R2=3e-4, dt=0.004, seed=6,
+                           vel_dim=2)
+    p, v = pos, vel
+    for s in range(60):
+        P.step = s
+        p, v = oracle.step(P, p, v)[:2]
+    T = v_in ** 2 / 2
+    speed = np.linalg.norm(v, axis=1)
+    assert stats.kstest(speed / math.sqrt(T), stats.rayleigh.cdf).pvalue > 1e-3
+    assert stats.kstest(speed / math.sqrt(T), stats.chi(3).cdf).pvalue < 1e-6
+
+
+def test_velocity2d_temperature_has_two_degrees_of_freedom():
+    import oracle
+    pos, vel = _box2d(200_000, 33, T=1.7)
+    P = oracle.make_params(2, (1, 1, 1), (0, 0, 0), (1, 1, 1), (0, 0, 0), R2=1e-6, dt=0.01, seed=0, vel_dim=2)
+    raw, der, glob = oracle.moments(P, pos, vel)
+    assert der[0, 4] == pytest.approx(1.7, rel=0.01)
+    P3 = oracle.make_params(2, (1, 1, 1), (0, 0, 0), (1, 1, 1), (0, 0, 0), R2=1e-6, dt=0.01, seed=0)
+    assert oracle.moments(P3, pos, vel)[1][0, 4] == pytest.approx(1.7 * 2 / 3, rel=0.01)
