@@ -54,6 +54,10 @@ extern "C" {
 
 #define KMC_BC_PERIODIC 0
 #define KMC_BC_WALL 1      /* specular (reflective) wall, Sect. "Sod test" */
+#define KMC_BC_ABSORB 2    /* absorbing wall, Sect. "Sedov test": a particle whose step ends outside the box
+                            * leaves the simulation (no longer searched, moved or counted in the moments;
+                            * kmc_get_state returns NaN position and velocity for it; a NaN position in the
+                            * input of kmc_init / kmc_set_state marks a particle already absorbed) */
 
 #define KMC_FLAG_RECORD 1   /* keep each particle's closest candidate and partner of the last step */
 #define KMC_FLAG_NO_GRAPH 2 /* launch kernels directly instead of replaying a captured CUDA graph */

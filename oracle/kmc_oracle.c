@@ -19,7 +19,7 @@
  *   orc_mutual_pairs    "only unambiguously determined interaction partners"
  *   orc_collide_move    CM-frame scattering with random opposite directions,
  *                       t_poca (Eq. 12) and the split position update (Eqs. 13-14),
- *                       reflective walls (Sod test set-up)
+ *                       reflective walls (Sod test set-up), absorbing walls (Sedov test)
  *   orc_moments         n = N/V, bulk velocity (Eq. vel_b), stress tensor with
  *                       kinetic and collisional parts (Eq. stress), pressure
  *                       (Eq. 18), v_rms and T = m v_rms^2 / f (Eq. 19)
@@ -67,6 +67,10 @@ static double uniform64(uint32_t hi, uint32_t lo)
     uint64_t m = ((uint64_t)hi << 20) | (uint64_t)(lo >> 12); /* 52 bits */
     return (double)(2u * m + 1u) * 0x1p-53;
 }
+
+/* Absorbing walls (Sect. "Sedov test"): a particle that left the box through
+ * one is no longer evolved; it is marked by a NaN position (and velocity). */
+static int gone(const double* r) { return isnan(r[0]); }
 
 /* ------------------------------------------------------------ parameters */
 
@@ -145,6 +149,11 @@ void orc_cell_keys(const orc_params* P, int64_t n, const double* pos,
 {
     for (int64_t i = 0; i < n; ++i) {
         int c[3] = {0, 0, 0};
+        if (gone(pos + 3 * i)) {   /* absorbed: in no c-bin */
+            if (key_out) key_out[i] = -1;
+            if (cidx_out) for (int d = 0; d < 3; ++d) cidx_out[3 * i + d] = 0;
+            continue;
+        }
         for (int d = 0; d < P->dim; ++d) c[d] = cell_1d(P, d, pos[3 * i + d]);
         if (key_out) key_out[i] = linear_key(P, c);
         if (cidx_out) for (int d = 0; d < 3; ++d) cidx_out[3 * i + d] = c[d];
@@ -305,11 +314,13 @@ static void bins_build(const orc_params* P, int64_t n, const double* pos, bins_t
     B->start = (int64_t*)calloc((size_t)C + 1, sizeof(int64_t));
     B->list = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     orc_cell_keys(P, n, pos, B->key, B->cidx);
-    for (int64_t i = 0; i < n; ++i) B->start[B->key[i] + 1]++;
+    for (int64_t i = 0; i < n; ++i)
+        if (B->key[i] >= 0) B->start[B->key[i] + 1]++;
     for (int c = 0; c < C; ++c) B->start[c + 1] += B->start[c];
     int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)C);
     for (int c = 0; c < C; ++c) fill[c] = B->start[c];
-    for (int64_t i = 0; i < n; ++i) B->list[fill[B->key[i]]++] = (int32_t)i;
+    for (int64_t i = 0; i < n; ++i)
+        if (B->key[i] >= 0) B->list[fill[B->key[i]]++] = (int32_t)i;
     free(fill);
 }
 
@@ -349,6 +360,10 @@ int64_t orc_best_partners(const orc_params* P, int64_t n, const double* pos,
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : found)
     for (int64_t i = 0; i < n; ++i) {
         int32_t bj = -1;
+        if (B.key[i] < 0) {   /* absorbed */
+            best[i] = -1;
+            continue;
+        }
         if (P->decide32) {
             float bd = INFINITY, q[5];
             FOR_NEIGHBOURHOOD(P, &B, i, j, {
@@ -375,6 +390,7 @@ int64_t orc_candidate_count(const orc_params* P, int64_t n, const double* pos)
     bins_build(P, n, pos, &B);
     int64_t total = 0;
     for (int64_t i = 0; i < n; ++i) {
+        if (B.key[i] < 0) continue;
         FOR_NEIGHBOURHOOD(P, &B, i, j, { total += 1; (void)j; });
     }
     bins_free(&B);
@@ -391,8 +407,8 @@ int64_t orc_best_partners_brute(const orc_params* P, int64_t n, const double* po
         int32_t bj = -1;
         double bd = INFINITY;
         float bdf = INFINITY;
-        for (int64_t j = 0; j < n; ++j) {
-            if (j == i || !in_neighbourhood(P, cidx + 3 * i, cidx + 3 * j)) continue;
+        for (int64_t j = 0; j < n && !gone(pos + 3 * i); ++j) {
+            if (j == i || gone(pos + 3 * j) || !in_neighbourhood(P, cidx + 3 * i, cidx + 3 * j)) continue;
             double q[5];
             if (!orc_pair_test(P, pos + 3 * i, vel + 3 * i, pos + 3 * j, vel + 3 * j, q))
                 continue;
@@ -426,10 +442,12 @@ int64_t orc_mutual_pairs(int64_t n, const int32_t* best, int32_t* pairs_out)
 
 /* Specular reflection: fold the end-of-step coordinate back into [lo, hi]
  * and flip the velocity component once per fold.  Periodic: shift into
- * [lo, hi). */
+ * [lo, hi).  Absorbing: the coordinate is left as it is (the caller removes a
+ * particle that ends outside). */
 static void boundary_1d(const orc_params* P, int d, double* x, double* v)
 {
     double lo = P->lo[d], hi = P->hi[d];
+    if (P->bc[d] == 2) return;
     if (P->bc[d] == 1) {
         for (int it = 0; it < 64 && (*x < lo || *x > hi); ++it) {
             if (*x < lo) *x = 2.0 * lo - *x;
@@ -502,7 +520,15 @@ void orc_collide_move(const orc_params* P, int64_t n, const double* pos,
         } else {
             for (int d = 0; d < P->dim; ++d) ro[d] = r[d] + v[d] * P->dt;  /* Eq. 14 */
         }
-        for (int d = 0; d < P->dim; ++d) boundary_1d(P, d, &ro[d], &vo[d]);
+        int out = gone(r);
+        for (int d = 0; d < P->dim; ++d) {
+            boundary_1d(P, d, &ro[d], &vo[d]);
+            if (P->bc[d] == 2 && (ro[d] < P->lo[d] || ro[d] > P->hi[d])) out = 1;
+        }
+        if (out) {   /* absorbed (now or earlier): NaN state */
+            for (int d = 0; d < 3; ++d) ro[d] = vo[d] = NAN;
+            W = 0.0;
+        }
         if (virial_out) virial_out[i] = W;
         if (paired_out) paired_out[i] = paired ? j : -1;
     }
@@ -519,6 +545,7 @@ void orc_moments(const orc_params* P, int64_t n, const double* pos, const double
     int32_t* key = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
     orc_cell_keys(P, n, pos, key, NULL);
     for (int64_t i = 0; i < n; ++i) {
+        if (key[i] < 0) continue;   /* absorbed */
         const double* v = vel + 3 * i;
         double W = virial ? virial[i] : 0.0;
         double* m = acc + 8 * (size_t)key[i];

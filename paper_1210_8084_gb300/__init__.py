@@ -28,6 +28,7 @@ KMC_WHERE_HOST = 0
 KMC_WHERE_DEVICE = 1
 KMC_BC_PERIODIC = 0
 KMC_BC_WALL = 1
+KMC_BC_ABSORB = 2
 KMC_FLAG_RECORD = 1
 KMC_FLAG_NO_GRAPH = 2
 KMC_FLAG_STAGED_SEARCH = 4

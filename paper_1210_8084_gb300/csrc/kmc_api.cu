@@ -351,7 +351,7 @@ int validate_config(const kmc_config* c, int64_t n) {
         if (c->n_cells[d] < 1) return fail(nullptr, KMC_EINVAL, "n_cells must be >= 1");
         if (!(c->hi[d] > c->lo[d]) || !isfinite(c->lo[d]) || !isfinite(c->hi[d]))
             return fail(nullptr, KMC_EINVAL, "box must satisfy lo < hi, finite");
-        if (c->bc[d] != KMC_BC_PERIODIC && c->bc[d] != KMC_BC_WALL)
+        if (c->bc[d] != KMC_BC_PERIODIC && c->bc[d] != KMC_BC_WALL && c->bc[d] != KMC_BC_ABSORB)
             return fail(nullptr, KMC_EINVAL, "bc must be KMC_BC_PERIODIC or KMC_BC_WALL");
         if (c->sub_cells[d] < 0) return fail(nullptr, KMC_EINVAL, "sub_cells must be >= 0");
     }
@@ -590,7 +590,8 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
                 return bail(fail(h, KMC_ERANGE, "search grid exceeds 2^32 keys; set sub_cells"));
         }
         h->n_keys = (uint32_t)keys;
-        h->n_tiles = (uint32_t)((keys + 1 + kScanTile - 1) / kScanTile);
+        // keys of the cells, one key after them for absorbed particles, and the end offset
+        h->n_tiles = (uint32_t)((keys + 2 + kScanTile - 1) / kScanTile);
         plan_staged_search(h, max_occ);
         // search cells that are the c-bins themselves: one block per cell
         h->any_tiled = 0;

@@ -41,6 +41,7 @@ struct R<float> {
     static __device__ __forceinline__ uint32_t bits(float a) { return __float_as_uint(a); }
     static __device__ __forceinline__ float from_bits(uint32_t u) { return __uint_as_float(u); }
     static __device__ __forceinline__ float inf() { return __int_as_float(0x7f800000); }
+    static __device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }
 };
 template <>
 struct R<double> {
@@ -57,6 +58,7 @@ struct R<double> {
         return __longlong_as_double((long long)(unsigned long long)u);
     }
     static __device__ __forceinline__ double inf() { return __longlong_as_double(0x7ff0000000000000LL); }
+    static __device__ __forceinline__ double qnan() { return __longlong_as_double(0x7ff8000000000000LL); }
 };
 
 // Per-instance timestep and squared contact distance in the state precision
@@ -109,7 +111,8 @@ template <typename T>
 struct GeoT {
     T lo[3], hi[3], inv[3], L[3], hL[3];
     int n[3];
-    bool wall[3];
+    bool wall[3];     // no periodic wrap: reflective or absorbing
+    bool absorb[3];   // absorbing: a particle that ends a step outside is removed
     int vdim;
     __device__ __forceinline__ void load(const Geo& g) {
         vdim = g.vdim;
@@ -120,6 +123,7 @@ struct GeoT {
             inv[d] = (T)g.inv_dx[d];
             L[d] = (T)g.L[d];
             wall[d] = g.bc[d] != 0;
+            absorb[d] = g.bc[d] == 2;
             hL[d] = wall[d] ? R<T>::inf() : (T)0.5 * L[d];
             n[d] = g.n[d];
         }
@@ -229,6 +233,12 @@ __device__ __forceinline__ unsigned long long warp_max_bits(double v2, bool vali
         m = y > m ? y : m;
     }
     return m;
+}
+
+// A particle absorbed by a wall carries vel.w = -inf (W is finite or +inf otherwise).
+template <typename T>
+__device__ __forceinline__ bool absorbed(T w) {
+    return w == -R<T>::inf();
 }
 
 // |v|^2 in a fixed operation order (the adaptive timestep depends on its bits)
@@ -341,21 +351,29 @@ __global__ void __launch_bounds__(kThreads) pack_kernel(Bufs<T> b, const T* __re
         x[d] = pos3[3 * p + d];
         v[d] = vel3[3 * p + d];
     }
+    bool any_absorb = false;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) any_absorb = any_absorb || b.geo.bc[d] == 2;
+    // a particle already absorbed (a state read back from an absorbing run) has a NaN position
+    const bool gone = any_absorb && isnan(x[0]);
     bool ok = true;
+    if (!gone) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) ok = ok && isfinite(x[d]) && isfinite(v[d]);
-    if (b.geo.vdim == 2) ok = ok && v[2] == (T)0;   // 2-D velocities: no z component
+        for (int d = 0; d < 3; ++d) ok = ok && isfinite(x[d]) && isfinite(v[d]);
+        if (b.geo.vdim == 2) ok = ok && v[2] == (T)0;   // 2-D velocities: no z component
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-        const T lo = (T)b.geo.lo[d], hi = (T)b.geo.hi[d];
-        if (b.geo.bc[d] != 0) ok = ok && x[d] >= lo && x[d] <= hi;
-        else ok = ok && x[d] >= lo && x[d] < hi;
+        for (int d = 0; d < DIM; ++d) {
+            const T lo = (T)b.geo.lo[d], hi = (T)b.geo.hi[d];
+            if (b.geo.bc[d] != 0) ok = ok && x[d] >= lo && x[d] <= hi;
+            else ok = ok && x[d] >= lo && x[d] < hi;
+        }
     }
     if (!ok) atomicAdd(bad, 1u);
     V P, Q;
     const uint32_t tag = (b.id_bits >= 32u ? 0u : ((uint32_t)inst << b.id_bits)) | id;
-    P.x = x[0]; P.y = x[1]; P.z = x[2]; P.w = R<T>::from_bits(tag);
-    Q.x = v[0]; Q.y = v[1]; Q.z = v[2]; Q.w = R<T>::inf();
+    P.x = gone ? (T)0 : x[0]; P.y = gone ? (T)0 : x[1]; P.z = gone ? (T)0 : x[2]; P.w = R<T>::from_bits(tag);
+    Q.x = gone ? (T)0 : v[0]; Q.y = gone ? (T)0 : v[1]; Q.z = gone ? (T)0 : v[2];
+    Q.w = gone ? -R<T>::inf() : R<T>::inf();
     b.posB[p] = P;
     b.velB[p] = Q;
 }
@@ -381,13 +399,15 @@ __global__ void __launch_bounds__(kThreads) bin_kernel(Bufs<T> b) {
     const T x[3] = {P.x, P.y, P.z};
     uint32_t skey = 0, bin = 0;
     keys_of<T, DIM>(G, I, x, skey, bin);
+    const bool gone = absorbed(Q.w);
+    if (gone) skey = b.n_keys;   // the key after every cell: no search window reaches it
     const unsigned active = __ballot_sync(kFull, valid);
     if (valid) {
         const uint32_t slot = aggregated_increment(b.count, skey, active);
         b.key[p] = skey;
         b.slot[p] = slot;
     }
-    warp_vmax<T>(b.dyn, valid, inst, speed2<T>(Q.x, Q.y, Q.z));
+    warp_vmax<T>(b.dyn, valid && !gone, inst, speed2<T>(Q.x, Q.y, Q.z));
 }
 
 // The PoCA acceptance test of the ordered pair (i, j) and its closest-approach
@@ -770,7 +790,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) search_kerne
     const InstDev& I = b.inst[inst];
     // sorted position by id, read by the move kernel to find a partner
     b.slot_of[I.p_off + (int64_t)tag_id(b, tag)] = (uint32_t)p;
-    if (I.staged || I.tiled) return;   // searched by the staged or the tile kernel
+    if (I.staged || I.tiled || absorbed(Q.w)) return;   // searched elsewhere, or gone
     const int* kk = b.dyn[inst].k;
     const T xi[3] = {P.x, P.y, P.z};
     const T vi[3] = {Q.x, Q.y, Q.z};
@@ -1457,6 +1477,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 1) move_kernel(
     T xn[3] = {x[0], x[1], x[2]}, vn[3] = {v[0], v[1], v[2]};
     T W = (T)0;
     bool paired = false;
+    bool gone = valid && absorbed(Q.w);   // absorbed in an earlier step: stays as it is
     uint32_t tagj = 0xffffffffu;
     int64_t j = -1;
     if (kp != kNoPartner) {
@@ -1509,15 +1530,18 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 1) move_kernel(
             xn[d] = R<T>::add(R<T>::add(x[d], R<T>::mul(v[d], tp)), R<T>::mul(vn[d], rest));  // Eq. 13
             W += (dr[d] + dv[d] * tp) * (vn[d] - v[d]);
         }
-    } else {
+    } else if (!gone) {
 #pragma unroll
         for (int d = 0; d < DIM; ++d) xn[d] = R<T>::add(x[d], R<T>::mul(v[d], dt));  // Eq. 14
     }
-    // reflective walls (fold) and periodic wrap
+    // absorbing walls (the particle leaves the simulation), reflective walls
+    // (fold) and periodic wrap
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         const T lo = G.lo[d], hi = G.hi[d];
-        if (G.wall[d]) {
+        if (G.absorb[d]) {
+            if (xn[d] < lo || xn[d] > hi) gone = true;
+        } else if (G.wall[d]) {
             for (int it = 0; it < kFoldCap && (xn[d] < lo || xn[d] > hi); ++it) {
                 xn[d] = (xn[d] < lo) ? R<T>::sub((T)2 * lo, xn[d]) : R<T>::sub((T)2 * hi, xn[d]);
                 vn[d] = -vn[d];
@@ -1537,12 +1561,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 1) move_kernel(
     }
     uint32_t skey = 0, bin = 0;
     keys_of<T, DIM>(G, I, xn, skey, bin);
+    if (gone) skey = b.n_keys;   // absorbed: the key after every cell
     const unsigned active = __ballot_sync(kFull, valid);
     if (valid) {
         const uint32_t slot = aggregated_increment(b.count, skey, active);
         V Pn, Qn;
         Pn.x = xn[0]; Pn.y = xn[1]; Pn.z = xn[2]; Pn.w = P.w;
-        Qn.x = vn[0]; Qn.y = vn[1]; Qn.z = vn[2]; Qn.w = paired ? W : R<T>::inf();
+        Qn.x = vn[0]; Qn.y = vn[1]; Qn.z = vn[2];
+        Qn.w = gone ? -R<T>::inf() : (paired ? W : R<T>::inf());
         b.posB[p] = Pn;
         b.velB[p] = Qn;
         b.key[p] = skey;
@@ -1554,7 +1580,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 1) move_kernel(
         }
     }
     (void)bin;
-    warp_vmax<T>(b.dyn, valid, inst, speed2<T>(vn[0], vn[1], vn[2]));
+    warp_vmax<T>(b.dyn, valid && !gone, inst, speed2<T>(vn[0], vn[1], vn[2]));
 }
 
 // Counting-sort scatter B -> A in search-key order.
@@ -1582,8 +1608,18 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(Bufs<T> b, T* __restri
     const V Q = b.velA[p];
     const int inst = tag_inst(b, R<T>::bits(P.w));
     const int64_t gid = b.inst[inst].p_off + (int64_t)tag_id(b, R<T>::bits(P.w));
-    if (pos3) { pos3[3 * gid] = P.x; pos3[3 * gid + 1] = P.y; pos3[3 * gid + 2] = P.z; }
-    if (vel3) { vel3[3 * gid] = Q.x; vel3[3 * gid + 1] = Q.y; vel3[3 * gid + 2] = Q.z; }
+    const bool gone = absorbed(Q.w);   // absorbed by a wall: NaN position and velocity
+    const T nan = R<T>::qnan();
+    if (pos3) {
+        pos3[3 * gid] = gone ? nan : P.x;
+        pos3[3 * gid + 1] = gone ? nan : P.y;
+        pos3[3 * gid + 2] = gone ? nan : P.z;
+    }
+    if (vel3) {
+        vel3[3 * gid] = gone ? nan : Q.x;
+        vel3[3 * gid + 1] = gone ? nan : Q.y;
+        vel3[3 * gid + 2] = gone ? nan : Q.z;
+    }
 }
 
 // c-bin key (instance-local) of every particle of A, id order.
@@ -1602,7 +1638,7 @@ __global__ void __launch_bounds__(kThreads) cellkey_kernel(Bufs<T> b, int32_t* _
     const T x[3] = {P.x, P.y, P.z};
     uint32_t skey, bin;
     keys_of<T, DIM>(G, I, x, skey, bin);
-    keys[I.p_off + (int64_t)tag_id(b, R<T>::bits(P.w))] = (int32_t)(bin - I.bin_base);
+    keys[I.p_off + (int64_t)tag_id(b, R<T>::bits(P.w))] = absorbed(Q.w) ? -1 : (int32_t)(bin - I.bin_base);
 }
 
 // Moment sums per c-bin of the sorted state A (Eqs. vel_b, stress, 18, 19):
@@ -1638,6 +1674,7 @@ __global__ void __launch_bounds__(kThreads) moments_kernel(Bufs<T> b, int use_vi
         if (p >= b.n) break;
         const V P = Ps[k];
         const V Q = Qs[k];
+        if (absorbed(Q.w)) continue;   // left through an absorbing wall
         const int inst = tag_inst(b, R<T>::bits(P.w));
         const InstDev& I = b.inst[inst];
         const T x[3] = {P.x, P.y, P.z};
@@ -1674,7 +1711,7 @@ __global__ void __launch_bounds__(kThreads) window_count_kernel(Bufs<T> b, unsig
     __syncthreads();
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long cnt = 0;
-    if (p < b.n) {
+    if (p < b.n && !absorbed(b.velA[p].w)) {
         const V P = b.posA[p];
         const int inst = tag_inst(b, R<T>::bits(P.w));
         const InstDev& I = b.inst[inst];
@@ -1730,13 +1767,14 @@ __global__ void __launch_bounds__(kThreads) cbin_hist_kernel(Bufs<T> b, uint32_t
     const T x[3] = {P.x, P.y, P.z};
     uint32_t skey = 0, bin = 0;
     keys_of<T, DIM>(G, I, x, skey, bin);
-    const unsigned active = __ballot_sync(kFull, valid);
-    if (valid) {
+    const bool live = valid && !absorbed(Q.w);
+    const unsigned active = __ballot_sync(kFull, live);
+    if (live) {
         const unsigned peers = __match_any_sync(active, bin);
         if ((int)lane_id() == __ffs(peers) - 1) atomicAdd(hist + bin, (uint32_t)__popc(peers));
     }
     const double v2 = (double)Q.x * Q.x + (double)Q.y * Q.y + (double)Q.z * Q.z;
-    double m = valid ? v2 : 0.0;
+    double m = live ? v2 : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
     const int inst0 = __shfl_sync(kFull, inst, 0);

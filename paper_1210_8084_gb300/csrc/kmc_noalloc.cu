@@ -102,7 +102,7 @@ int run(const kmc_config* cfg, int64_t n, const void* pos, const void* vel, int3
     }
     if (keys > (uint64_t)KMC_STATIC_MAX_CELLS) return KMC_ERANGE;
     const uint32_t n_keys = (uint32_t)keys;
-    const uint32_t n_tiles = (uint32_t)((keys + 1 + kScanTile - 1) / kScanTile);
+    const uint32_t n_tiles = (uint32_t)((keys + 2 + kScanTile - 1) / kScanTile);   // + absorbed key, end
     // carve the scratch array
     unsigned char* p = (unsigned char*)base;
     size_t off = 0;

@@ -18,6 +18,8 @@ Recipes (units m = 1, k_B = 1, v_th = sqrt(T_left / m) = 1):
     mono-energetic (|v| = v_in, isotropic directions, Sect. "Equilibration").
   * Noh implosion (Sect. "Noh test"): uniform density, radial inflow v0 towards
     the corner at the origin, cold (T0 << v0^2), reflective walls.
+  * Sedov-Taylor blast (Sect. "Sedov test"): uniform density, speed v0 in
+    random directions, v_blast inside r_blast of the centre, absorbing walls.
 """
 import math
 
@@ -119,6 +121,21 @@ def noh(n, seed=0, dim_pos=3, L=1.0, v0=1.0, T0=1e-6):
     rhat[:, :dim_pos] = pos[:, :dim_pos] / np.maximum(r, 1e-300)
     vel = -v0 * rhat + _rng(seed, 2).normal(0.0, math.sqrt(T0), (n, 3))
     return pos, vel
+
+
+def sedov(n, seed=0, dim_pos=3, L=1.0, v0=1e-3, r_blast=0.02, v_blast=85.0):
+    """Sedov-Taylor blast (Sect. "Sedov test"): uniform positions in [0, L]^dim,
+    velocities of magnitude v0 in random directions, except |v| = v_blast
+    inside r_blast of the centre (the energy deposition)."""
+    g = _rng(seed, 1)
+    pos = np.zeros((n, 3))
+    pos[:, :dim_pos] = L * g.random((n, dim_pos))
+    pos = np.minimum(pos, L)
+    d = _rng(seed, 2).normal(0.0, 1.0, (n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    r = np.linalg.norm(pos[:, :dim_pos] - 0.5 * L, axis=1)
+    speed = np.where(r <= r_blast, v_blast, v0)
+    return pos, speed[:, None] * d
 
 
 def cast_state(pos, vel, dtype, lo, hi, bc):

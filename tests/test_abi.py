@@ -85,7 +85,8 @@ def test_invalid_config_is_rejected_without_device(built_lib):
         k.make_config(precision=16),
         k.make_config(n_cells=(0, 1, 1)),
         k.make_config(lo=(1, 0, 0), hi=(0, 1, 1)),
-        k.make_config(bc=(2, 0, 0)),
+        k.make_config(bc=(3, 0, 0)),
+        k.make_config(dim_pos=3, flags=k.KMC_FLAG_VELOCITY_2D),
         k.make_config(dt=0.0),
         k.make_config(lam=0.0, sigma=0.0),
         k.make_config(flags=1 << 8),

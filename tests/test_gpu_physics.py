@@ -276,3 +276,49 @@ def test_sod_2d_with_2d_velocities_matches_gamma_2():
     print("Sod 2-D velocities L1:", l1, "star:", stat)
     assert l1["n"] <= 0.025 and l1["p"] <= 0.025 and l1["T"] <= 0.025, l1
     assert all(abs(v) < 0.02 for v in stat.values()), stat
+
+
+def test_sedov_blast_radius_grows_as_t_to_two_fifths():
+    """3-D Sedov-Taylor blast (Sect. "Sedov test"): absorbing walls, adaptive
+    timestep, energy deposited as speed v_blast inside 2 c-bins of the centre.
+    The shock (the radius of the density peak) grows as (E t^2 / n0)^(1/5):
+    between two times its radius scales as (t2 / t1)^(2/5), whatever the
+    constant alpha; the peak is compressed above 1.8 n0 (4 n0 for an
+    infinitely thin shock)."""
+    _setup()
+    import paper_1210_8084_gb300 as k
+    from paper_1210_8084_gb300 import inputs
+    n, nc = 8_000_000, 100
+    A = k.KMC_BC_ABSORB
+    pos, vel = inputs.sedov(n, seed=7, r_blast=2.0 / nc, v_blast=85.0)
+    pos, vel = inputs.cast_state(pos, vel, np.float32, (0, 0, 0), (1, 1, 1), (1, 1, 1))
+    sim = k.Simulation(k.make_config(dim_pos=3, n_cells=(nc, nc, nc), bc=(A, A, A), lam=1e-3, dt=1.0, seed=7,
+                                     precision=32, flags=k.KMC_FLAG_ADAPTIVE_DT), pos, vel)
+    c = (np.arange(nc) + 0.5) / nc - 0.5
+    X, Y, Z = np.meshgrid(c, c, c, indexing="ij")
+    r = np.sqrt(X ** 2 + Y ** 2 + Z ** 2).ravel()
+    shells = np.arange(0.0, 0.5, 1.0 / nc)
+    idx = np.digitize(r, shells) - 1
+    n0 = float(n)
+
+    def peak():
+        raw = sim.moments()[0]
+        dens = raw[:, 0] * nc ** 3 / n0
+        prof = np.array([dens[idx == i].mean() for i in range(len(shells) - 1)])
+        i = int(np.argmax(prof[3:])) + 3
+        return 0.5 * (shells[i] + shells[i + 1]), prof[i]
+
+    out = []
+    for t_goal in (0.05, 0.1):
+        while sim.info().time < t_goal:
+            sim.step(25, want_moments=1)
+        t = sim.info().time
+        rp, npk = peak()
+        out.append((t, rp, npk))
+    glob = sim.moments()[2]
+    sim.close()
+    (t1, r1, n1), (t2, r2, n2) = out
+    print(f"Sedov: t {t1:.4f} r {r1:.3f} peak {n1:.2f}; t {t2:.4f} r {r2:.3f} peak {n2:.2f}; live {glob[0, 0]:.0f}")
+    assert abs((r2 / r1) / (t2 / t1) ** 0.4 - 1) < 0.08
+    assert n1 > 1.8 and n2 > 1.8
+    assert 0.1 < r1 < r2 < 0.45

@@ -602,3 +602,33 @@ def test_velocity2d_temperature_has_two_degrees_of_freedom():
     assert der[0, 4] == pytest.approx(1.7, rel=0.01)
     P3 = oracle.make_params(2, (1, 1, 1), (0, 0, 0), (1, 1, 1), (0, 0, 0), R2=1e-6, dt=0.01, seed=0)
     assert oracle.moments(P3, pos, vel)[1][0, 4] == pytest.approx(1.7 * 2 / 3, rel=0.01)
+
+
+# ------------------------------------------------------- absorbing walls (Sedov)
+# Sect. "Sedov test": particles that leave the box through an absorbing wall
+# are no longer evolved.
+
+def test_absorbing_walls_remove_exactly_the_particles_that_leave():
+    """Free flight (no collisions): a particle is removed iff r + v dt lies
+    outside the box in an absorbing dimension; removed particles stay removed,
+    are nobody's candidate, and leave the moments."""
+    import oracle
+    from paper_1210_8084_gb300 import inputs
+    pos, vel = inputs.periodic_box(4000, seed=51, T=4.0)
+    ABS, PER = 2, 0
+    P = oracle.make_params(3, (6, 6, 6), (0, 0, 0), (1, 1, 1), (ABS, PER, ABS), R2=1e-14, dt=0.05, seed=1)
+    p1, v1, best, paired, raw, der, glob, k = oracle.step(P, pos, vel)
+    end = pos + vel * 0.05
+    out = (end[:, 0] < 0) | (end[:, 0] > 1) | (end[:, 2] < 0) | (end[:, 2] > 1)
+    assert 50 < out.sum() < 3000
+    assert np.array_equal(np.isnan(p1[:, 0]), out)
+    assert np.all(np.isnan(v1[out])) and np.all(np.isfinite(v1[~out]))
+    assert glob[0] == (~out).sum()
+    assert glob[1] == pytest.approx(0.5 * (vel[~out] ** 2).sum(), rel=1e-12)
+    # a second step: removed particles stay removed and are never candidates
+    P.R2 = 1e-3
+    P.step = 1
+    p2, v2, best2 = oracle.step(P, p1, v1)[:3]
+    assert np.all(np.isnan(p2[out, 0]))
+    assert np.all(best2[out] == -1)
+    assert not np.isin(best2[best2 >= 0], np.nonzero(out)[0]).any()
