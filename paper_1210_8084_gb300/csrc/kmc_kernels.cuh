@@ -598,7 +598,7 @@ __device__ __forceinline__ T image_of(uint32_t c, T L) {
     return c == 1u ? L : (c == 2u ? -L : (T)0);
 }
 
-template <typename T, int DIM, bool MINIMG, bool SYM>
+template <typename T, int DIM, bool MINIMG, bool SYM, bool SHIFT = true>
 __device__ __forceinline__ void walk_rows(const Bufs<T>& b, const GeoT<T>& G, const int2* rng, uint32_t mask,
                                           uint32_t code, T sf, const T xi[3], const T vi[3], T dt, T R2, T& bd,
                                           uint32_t& bid, int32_t& bq, uint32_t tag) {
@@ -646,7 +646,7 @@ __device__ __forceinline__ void walk_rows(const Bufs<T>& b, const GeoT<T>& G, co
         const T vj[3] = {Qj.x, Qj.y, Qj.z};
         T d2;
         // the particle itself has v_rel = 0 and fails b > 0
-        if (poca_test_sh<T, DIM, MINIMG>(G, xi, vi, xj, vj, sh, dt, R2, d2)) {
+        if (poca_test_sh<T, DIM, MINIMG, SHIFT>(G, xi, vi, xj, vj, sh, dt, R2, d2)) {
             const uint32_t idj = R<T>::bits(Pj.w);
             if (d2 < bd || (d2 == bd && idj < bid)) {
                 bd = d2;
@@ -728,7 +728,11 @@ __device__ __forceinline__ void scan_window(const Bufs<T>& b, const GeoT<T>& G, 
                 code |= (sx[i] > (T)0 ? 1u : (sx[i] < (T)0 ? 2u : 0u)) << (2 * i);
                 if (DIM == 3) code |= (sy[i] > (T)0 ? 1u : (sy[i] < (T)0 ? 2u : 0u)) << (6 + 2 * i);
             }
-            walk_rows<T, DIM, MINIMG, SYM>(b, G, rng, mask, code, fs[0], xi, vi, dt, R2, bd, bid, bq, tag);
+            // no row of the window has a periodic image (the common case): skip the image additions
+            if (code == 0u && fs[0] == (T)0)
+                walk_rows<T, DIM, MINIMG, SYM, false>(b, G, rng, mask, code, fs[0], xi, vi, dt, R2, bd, bid, bq, tag);
+            else
+                walk_rows<T, DIM, MINIMG, SYM, true>(b, G, rng, mask, code, fs[0], xi, vi, dt, R2, bd, bid, bq, tag);
         } else {
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
@@ -1453,7 +1457,7 @@ __global__ void __launch_bounds__(kStageThreads) search_staged_kernel(Bufs<T> b)
 // next step's search key / slot / histogram.  The particle's collisional
 // virial goes to vel.w for the moment pass.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 1) move_kernel(Bufs<T> b) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 1) move_kernel(Bufs<T> b) {
     using V = typename Vec4<T>::type;
     __shared__ GeoT<T> G;
     if (threadIdx.x == 0) G.load(b.geo);
