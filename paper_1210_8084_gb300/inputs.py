@@ -107,11 +107,12 @@ def periodic_box(n, seed=0, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), T=1.0, v_in=
     return pos, vel
 
 
-def noh(n, seed=0, dim_pos=3, L=1.0, v0=1.0, T0=1e-6):
+def noh(n, seed=0, dim_pos=3, L=1.0, v0=1.0, T0=1e-6, vel_dim=3):
     """Noh implosion (Sect. "Noh test"): uniform positions in [0, L]^dim with
     the origin at the corner (walls at 0 are the symmetry planes), velocity
     -v0 r_hat towards the origin in the position dimensions plus a small
-    Maxwellian spread of temperature T0 per component ("zero pressure")."""
+    Maxwellian spread of temperature T0 per component ("zero pressure");
+    vel_dim = 2: velocities in the (x, y) plane."""
     g = _rng(seed, 1)
     pos = np.zeros((n, 3))
     pos[:, :dim_pos] = L * g.random((n, dim_pos))
@@ -120,6 +121,8 @@ def noh(n, seed=0, dim_pos=3, L=1.0, v0=1.0, T0=1e-6):
     rhat = np.zeros((n, 3))
     rhat[:, :dim_pos] = pos[:, :dim_pos] / np.maximum(r, 1e-300)
     vel = -v0 * rhat + _rng(seed, 2).normal(0.0, math.sqrt(T0), (n, 3))
+    if vel_dim == 2:
+        vel[:, 2] = 0.0
     return pos, vel
 
 

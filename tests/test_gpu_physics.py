@@ -322,3 +322,44 @@ def test_sedov_blast_radius_grows_as_t_to_two_fifths():
     assert abs((r2 / r1) / (t2 / t1) ** 0.4 - 1) < 0.08
     assert n1 > 1.8 and n2 > 1.8
     assert 0.1 < r1 < r2 < 0.45
+
+
+def test_noh_cylindrical_2d_reaches_nine_times_n0():
+    """The paper's 2-D cylindrical Noh test with 2-D velocities (gamma = 2):
+    the gas inside the shock at rest with density 9 n0 (the value the paper
+    reports its runs approach) and temperature v0^2 / 2, the shock at v0 t / 2,
+    the infall ahead of it at n0 (1 + v0 t / r)."""
+    _setup()
+    import paper_1210_8084_gb300 as k
+    from paper_1210_8084_gb300 import inputs
+    from oracle import noh
+    n, nc, v0 = 5_000_000, 500, 1.0
+    dt = 0.2 / nc / v0
+    steps = 750
+    pos, vel = inputs.noh(n, seed=9, dim_pos=2, L=1.0, v0=v0, T0=1e-6, vel_dim=2)
+    bc = (1, 1, 0)
+    pos, vel = inputs.cast_state(pos, vel, np.float32, (0, 0, 0), (1, 1, 1), bc)
+    sim = k.Simulation(k.make_config(dim_pos=2, n_cells=(nc, nc, 1), bc=bc, lam=1e-3, dt=dt, seed=9, precision=32,
+                                     flags=k.KMC_FLAG_VELOCITY_2D), pos, vel)
+    sim.step(steps, want_moments=1)
+    raw = sim.moments()[0]
+    sim.close()
+    t = steps * dt
+    g = 2.0
+    rs = noh.shock_radius(t, v0, g)
+    c = (np.arange(nc) + 0.5) / nc
+    X, Y = np.meshgrid(c, c, indexing="xy")      # rows: c_x fastest
+    r = np.sqrt(X ** 2 + Y ** 2).ravel()
+    N = raw[:, 0]
+    dens = N * nc ** 2 / float(n)
+    inner = r < 0.6 * rs
+    ahead = (r > 1.6 * rs) & (r < 2.4 * rs)
+    Nin = N[inner].sum()
+    c2 = (raw[inner, 4:6].sum() - (raw[inner, 1:3].sum(0) ** 2).sum() / Nin) / Nin
+    T_in = c2 / 2.0
+    n_in = dens[inner].mean()
+    n_ahead = dens[ahead].sum() / noh.profile(r[ahead], t, v0, 1.0, g, 2)[0].sum()
+    print(f"Noh 2-D: n_in/n0 {n_in:.2f} (9), T_in {T_in:.3f} (0.5), n_ahead/exact {n_ahead:.3f}")
+    assert abs(n_in / noh.shocked_density(1.0, g, 2) - 1) < 0.1
+    assert abs(T_in / ((g - 1) * 0.5 * v0 ** 2) - 1) < 0.1
+    assert abs(n_ahead - 1) < 0.05
