@@ -802,6 +802,45 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) search_kerne
     int c[3] = {0, 0, 0}, g[3] = {0, 0, 0};
 #pragma unroll
     for (int d = 0; d < DIM; ++d) cell_and_search<T>(xi[d], G.lo[d], G.inv[d], G.n[d], I.s[d], c[d], g[d]);
+    T bd = R<T>::inf();
+    uint32_t bid = 0xffffffffu;
+    int32_t bq = -1;
+    if (kSym && DIM == 3) {
+        // Common case: c-bins not split in x, half-window 1 in y and z, and a
+        // search cell at least one cell from the y and z faces.  The window is
+        // then the z-ranges [g_z - 1, g_z + 1] of the rows (c_x + {-1, 0, 1},
+        // g_y + {-1, 0, 1}), none with a periodic image; the symmetric search
+        // keeps the own row from p + 1 on and the four rows after it.
+        const int My = I.M[1], Mz = I.M[2];
+        const bool x_ok = G.wall[0] || (G.n[0] >= 5 && c[0] >= 1 && c[0] <= G.n[0] - 2);
+        if (I.s[0] == 1 && kk[1] == 1 && kk[2] == 1 && My >= 5 && Mz >= 5 && g[1] >= 1 && g[1] <= My - 2 &&
+            g[2] >= 1 && g[2] <= Mz - 2 && x_ok) {
+            const uint32_t own = I.key_base + ((uint32_t)g[0] * (uint32_t)My + (uint32_t)g[1]) * (uint32_t)Mz +
+                                 (uint32_t)g[2];
+            const uint32_t dy = (uint32_t)Mz, dx = (uint32_t)My * (uint32_t)Mz;
+            // the next x row: cut at a wall, wrapped when periodic (c_x <= n_x - 2 there)
+            const bool has_x = c[0] + 1 < G.n[0];
+            const uint32_t nxt = own + dx;
+            const uint32_t rows[5] = {own - 1u, own + dy - 1u, nxt - dy - 1u, nxt - 1u, nxt + dy - 1u};
+            const uint32_t nmax = (uint32_t)b.n;
+            int2* rng_t = rng + threadIdx.x;
+            uint32_t mask = 0u;
+#pragma unroll
+            for (int r = 0; r < 5; ++r) {
+                if (r >= 2 && !has_x) break;
+                int32_t q0 = (int32_t)min(b.start[rows[r]], nmax);
+                const int32_t q1 = (int32_t)min(b.start[rows[r] + 3u], nmax);
+                if (r == 0) q0 = max(q0, (int32_t)p + 1);
+                if (q1 > q0) {
+                    rng_t[r * kThreads] = make_int2(q0, q1);
+                    mask |= 1u << r;
+                }
+            }
+            walk_rows<T, DIM, false, true, false>(b, G, rng_t, mask, 0u, (T)0, xi, vi, dt, R2, bd, bid, bq, tag);
+            if (bq >= 0) atomicMin(&b.bkey[p], partner_key<T>(bd, bid));
+            return;
+        }
+    }
     Win w[3];
     bool amb = false;
 #pragma unroll
@@ -809,9 +848,6 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) search_kerne
         w[d] = window_1d(g[d], c[d], I.s[d], I.M[d], kk[d], G.wall[d]);
         amb = amb || w[d].amb;
     }
-    T bd = R<T>::inf();
-    uint32_t bid = 0xffffffffu;
-    int32_t bq = -1;
     uint32_t self_key = 0;
     if (kSym) {
         self_key = (DIM == 3) ? I.key_base + ((uint32_t)g[0] * (uint32_t)I.M[1] + (uint32_t)g[1]) * (uint32_t)I.M[2] +
