@@ -1520,15 +1520,17 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 1) move_kernel(
     bool gone = valid && absorbed(Q.w);   // absorbed in an earlier step: stays as it is
     uint32_t tagj = 0xffffffffu;
     int64_t j = -1;
+    V Pj = {}, Qj = {};
     if (kp != kNoPartner) {
         tagj = (uint32_t)kp;
         j = b.slot_of[I.p_off + (int64_t)tag_id(b, tagj)];
+        // the candidate's key and state in one round trip; the state is used if the pair is mutual
         const unsigned long long kj = b.bkey[j];
+        Pj = b.posA[j];
+        Qj = b.velA[j];
         paired = kj != kNoPartner && (uint32_t)kj == tag;
     }
     if (paired) {
-        const V Pj = b.posA[j];
-        const V Qj = b.velA[j];
         const T xj[3] = {Pj.x, Pj.y, Pj.z};
         const T vj[3] = {Qj.x, Qj.y, Qj.z};
         T dr[3] = {0, 0, 0}, dv[3];

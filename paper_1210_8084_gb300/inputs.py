@@ -178,6 +178,9 @@ WORKLOADS = {
         kind="batched_sod", n_instances=256, n_range=(50_000, 2_000_000), lam_range=(1e-4, 1.0),
         dim_pos=3, n_cells=(200, 1, 1), lo=(0, 0, 0), hi=(1, 1, 1), bc=(WALL, PERIODIC, PERIODIC),
         dt=0.2 / 200, steps=400, precision=32, seed=0),
+    "sod3d_fp32_16M": dict(     # the 512M case's cubic c-bins and occupancy (~122 per c-bin) on 16M particles
+        kind="sod", n=16_000_000, dim_pos=3, n_cells=(512, 16, 16), lo=(0, 0, 0), hi=(1, 1 / 32, 1 / 32),
+        bc=(WALL, PERIODIC, PERIODIC), lam=2e-4, dt=0.2 / 512, steps=300, precision=32, seed=0),
     "sod3d_fp32_512M": dict(
         kind="sod", n=512_000_000, dim_pos=3, n_cells=(1024, 64, 64), lo=(0, 0, 0), hi=(1, 1 / 16, 1 / 16),
         bc=(WALL, PERIODIC, PERIODIC), lam=2e-4, dt=0.2 / 1024, steps=300, precision=32, seed=0),
