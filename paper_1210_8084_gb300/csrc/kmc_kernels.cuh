@@ -1000,12 +1000,15 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
         // binary32: a home tests only higher positions; binary64: the whole
         // window (the particle itself fails b > 0)
         const int32_t lim = kSym ? p : -1;
-        // the candidates [e0, e1) of one range; SH: the range has a periodic image
-        auto scan = [&](auto has_shift, int e0, int e1, int c0, int32_t qoff, const T sh[3]) {
+        // the candidates [e0, e1) of one range; SH: the range has a periodic image;
+        // CHK: the range may hold positions at or below the home's (own c-bin)
+        auto scan = [&](auto has_shift, auto check, int e0, int e1, int c0, int32_t qoff, const T sh[3]) {
             constexpr bool SH = decltype(has_shift)::value;
+            constexpr bool CHK = decltype(check)::value;
+#pragma unroll 2
             for (int e = e0; e < e1; ++e) {
                 const int32_t q = qoff + e;
-                if (q <= lim) continue;
+                if (CHK && q <= lim) continue;
                 const V Pj = sp[e - c0];
                 const V Qj = sv[e - c0];
                 const T xj[3] = {Pj.x, Pj.y, Pj.z};
@@ -1036,10 +1039,17 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
                 if (e0 >= e1) continue;
                 const T sh[3] = {rsh[r][0], rsh[r][1], rsh[r][2]};
                 const int32_t qoff = rq0[r] - rpre[r];
-                if (sh[0] != (T)0 || sh[1] != (T)0 || sh[2] != (T)0)
-                    scan(std::true_type{}, e0, e1, c0, qoff, sh);
-                else
-                    scan(std::false_type{}, e0, e1, c0, qoff, sh);
+                // binary32: a range that starts after the cell's last particle needs no position check
+                // (binary64 tests the whole window: the particle itself fails b > 0)
+                const bool chk = kSym && qoff + e0 <= (int32_t)h1 - 1;
+                const bool shifted = sh[0] != (T)0 || sh[1] != (T)0 || sh[2] != (T)0;
+                if (shifted) {
+                    if (chk) scan(std::true_type{}, std::true_type{}, e0, e1, c0, qoff, sh);
+                    else scan(std::true_type{}, std::false_type{}, e0, e1, c0, qoff, sh);
+                } else {
+                    if (chk) scan(std::false_type{}, std::true_type{}, e0, e1, c0, qoff, sh);
+                    else scan(std::false_type{}, std::false_type{}, e0, e1, c0, qoff, sh);
+                }
             }
         }
         if (home) {
