@@ -3,15 +3,17 @@
 //
 // Step structure (Sagert et al., Sect. "Simulation setup" and Fig. 2):
 //   search  : closest PoCA candidate per particle over its c-bin neighbourhood
+//             (per particle, or per c-bin block on unsubdivided grids)
 //   move    : unambiguous pairs, CM scattering, split free flight, walls,
-//             next search key + histogram, moment sums (fused)
+//             next search key + histogram
 //   scan    : exclusive scan of the key histogram (kmc_scan.cu)
 //   scatter : counting-sort scatter into search-key order
+//   moments : per-c-bin sums of the new state (finalised in kmc_scan.cu)
 //
 // Layout: SoA of 16-byte (binary32) or 32-byte (binary64) vectors,
 //   pos = (x, y, z, tag bits), vel = (vx, vy, vz, W),
 // tag = (instance << id_bits) | instance-local id, W = collisional virial of the
-// particle's last step (+inf when it did not collide),
+// particle's last step (+inf when it did not collide, -inf once absorbed),
 // sorted by search key = key_base + (gx * My + gy) * Mz + gz where g is the
 // search cell (a c-bin subdivided s_d times per dimension, x slowest).
 #pragma once
@@ -61,9 +63,9 @@ struct R<double> {
     static __device__ __forceinline__ double qnan() { return __longlong_as_double(0x7ff8000000000000LL); }
 };
 
-// Per-instance timestep and squared contact distance in the state precision
-// (binary32 copies are rounded once on the host, as the oracle rounds them).
-// timestep of the current step (constant unless adaptive), in the state precision
+// Timestep of the current step (constant unless adaptive; set on the device by
+// the step bookkeeping) and squared contact distance, in the state precision
+// (binary32 copies are rounded once from binary64, as the oracle rounds them).
 __device__ __forceinline__ float step_dt(const InstDyn& D, float) { return D.dtf; }
 __device__ __forceinline__ double step_dt(const InstDyn& D, double) { return D.dt; }
 __device__ __forceinline__ float inst_R2(const InstDev& I, float) { return I.R2f; }
