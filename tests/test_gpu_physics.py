@@ -284,7 +284,8 @@ def test_sedov_blast_radius_grows_as_t_to_two_fifths():
     The shock (the radius of the density peak) grows as (E t^2 / n0)^(1/5):
     between two times its radius scales as (t2 / t1)^(2/5), whatever the
     constant alpha; the peak is compressed above 1.8 n0 (4 n0 for an
-    infinitely thin shock)."""
+    infinitely thin shock); the peak sits at the similarity solution's radius
+    (E t^2 / (alpha n0))^(1/5), alpha from oracle/sedov.py."""
     _setup()
     import paper_1210_8084_gb300 as k
     from paper_1210_8084_gb300 import inputs
@@ -318,8 +319,15 @@ def test_sedov_blast_radius_grows_as_t_to_two_fifths():
     glob = sim.moments()[2]
     sim.close()
     (t1, r1, n1), (t2, r2, n2) = out
-    print(f"Sedov: t {t1:.4f} r {r1:.3f} peak {n1:.2f}; t {t2:.4f} r {r2:.3f} peak {n2:.2f}; live {glob[0, 0]:.0f}")
+    from oracle import sedov
+    E = 0.5 * float((vel.astype(np.float64) ** 2).sum())
+    al = sedov.alpha(3, 5.0 / 3.0)
+    rs1, rs2 = (sedov.shock_radius(E, n0, t, alpha_value=al) for t in (t1, t2))
+    print(f"Sedov: t {t1:.4f} r {r1:.3f} (exact {rs1:.3f}) peak {n1:.2f}; t {t2:.4f} r {r2:.3f} "
+          f"(exact {rs2:.3f}) peak {n2:.2f}; live {glob[0, 0]:.0f}")
     assert abs((r2 / r1) / (t2 / t1) ** 0.4 - 1) < 0.08
+    # the density peak sits at the similarity solution's shock radius (within a few c-bins)
+    assert abs(r1 / rs1 - 1) < 0.08 and abs(r2 / rs2 - 1) < 0.08
     assert n1 > 1.8 and n2 > 1.8
     assert 0.1 < r1 < r2 < 0.45
 
