@@ -310,7 +310,7 @@ def ours(args):
         "clocks": clk,
     }
     if not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(w, args.cpu_slice_bins)
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_slice_bins, single_thread_bins=2)
     return out
 
 
@@ -421,23 +421,38 @@ def oracle_slice(w, n_bins_slice, seed=0):
     return pos, vel, lo, hi
 
 
-def cpu_baseline(w, n_bins_slice=8, steps=1):
+def cpu_baseline(w, n_bins_slice=8, steps=1, single_thread_bins=0):
+    """The CPU oracle on the host cores (all OpenMP threads) on a slice of
+    central c-bins at full density; optionally also on one thread."""
     import oracle
-    pos, vel, lo, hi = oracle_slice(w, n_bins_slice)
-    m = pos.shape[0]
-    nbar = w["n"] / 1.0
-    P = oracle.make_params(w["dim_pos"], (n_bins_slice, 1, 1), lo, hi, w["bc"],
-                           R2=oracle.contact_R2(w["lam"], 0.0, nbar), dt=w["dt"], seed=0,
-                           decide32=w["precision"] == 32)
-    t0 = time.perf_counter()
-    for s in range(steps):
-        P.step = s
-        pos, vel = oracle.step(P, pos, vel)[:2]
-    el = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": m * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle", "particles": m,
-            "sample": f"{steps} oracle step(s) of the {n_bins_slice} central c-bins at full density: "
-                      f"{m} particles with the full run's neighbourhood occupancy, {el:.2f} s"}
+
+    def run(nb):
+        pos, vel, lo, hi = oracle_slice(w, nb)
+        nbar = w["n"] / 1.0
+        P = oracle.make_params(w["dim_pos"], (nb, 1, 1), lo, hi, w["bc"],
+                               R2=oracle.contact_R2(w["lam"], 0.0, nbar), dt=w["dt"], seed=0,
+                               decide32=w["precision"] == 32)
+        t0 = time.perf_counter()
+        for s in range(steps):
+            P.step = s
+            pos, vel = oracle.step(P, pos, vel)[:2]
+        return pos.shape[0], time.perf_counter() - t0
+
+    cores = oracle.set_threads(0)
+    m, el = run(n_bins_slice)
+    out = {"value": m * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle", "particles": m,
+           "sample": f"{steps} oracle step(s) of the {n_bins_slice} central c-bins at full density: "
+                     f"{m} particles with the full run's neighbourhood occupancy, {el:.2f} s"}
+    if single_thread_bins > 0:
+        oracle.set_threads(1)
+        try:
+            m1, el1 = run(single_thread_bins)
+        finally:
+            oracle.set_threads(cores)
+        out["single_thread"] = {"value": m1 * steps / el1, "unit": UNIT, "cores": 1, "particles": m1,
+                                "sample": f"{steps} oracle step(s) of the {single_thread_bins} central c-bins, "
+                                          f"{el1:.2f} s"}
+    return out
 
 
 def reference(args):

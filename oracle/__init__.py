@@ -46,6 +46,8 @@ def lib():
         L.orc_philox4x32_10.restype = None
         L.orc_contact_R2.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.orc_contact_R2.restype = ctypes.c_double
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_set_threads.restype = ctypes.c_int
         L.orc_adaptive_dt.argtypes = [P, i64, dp, ctypes.c_double]
         L.orc_adaptive_dt.restype = ctypes.c_double
         L.orc_cell_keys.argtypes = [P, i64, dp, ip, ip]
@@ -106,6 +108,11 @@ def philox4x32_10(ctr, key):
 
 def contact_R2(lam, sigma, nbar):
     return lib().orc_contact_R2(float(lam), float(sigma), float(nbar))
+
+
+def set_threads(n):
+    """OpenMP threads of the oracle's loops (n <= 0: unchanged); returns the number in use."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def adaptive_dt(P, vel, dt_rest=0.0):

@@ -29,6 +29,9 @@
 #include "kmc_oracle.h"
 
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -66,6 +69,17 @@ static double uniform64(uint32_t hi, uint32_t lo)
 {
     uint64_t m = ((uint64_t)hi << 20) | (uint64_t)(lo >> 12); /* 52 bits */
     return (double)(2u * m + 1u) * 0x1p-53;
+}
+
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* Absorbing walls (Sect. "Sedov test"): a particle that left the box through

@@ -40,6 +40,10 @@ typedef struct {
     int vel_dim;        /* velocity components: 3, or 2 (x, y; the paper's 2-D runs, f = 2) */
 } orc_params;
 
+/* Threads of the OpenMP loops (closest-candidate search); <= 0 keeps the default.
+ * Returns the number in use. */
+int orc_set_threads(int n);
+
 /* Philox4x32-10 block function (Salmon, Moraes, Dror, Shaw, SC'11). */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
