@@ -217,8 +217,10 @@ KMC_API int kmc_get_partners(kmc_handle* h, int32_t* best, int32_t* partner, int
  * *best receives a copy of *cfg with occupancy_target and flags (the
  * KMC_FLAG_NO_TILE_SEARCH / KMC_FLAG_STAGED_SEARCH bits) of the fastest
  * setting and sub_cells = 0 (automatic); *ms_per_step (may be NULL) its time.
- * Device memory: one handle at a time.  Synchronises cfg->stream.  Returns the
- * first error of kmc_init for an invalid configuration. */
+ * Device memory: one handle at a time.  Synchronises cfg->stream.  Returns
+ * KMC_EINVAL for an invalid configuration or state; a setting whose handle
+ * cannot be created (e.g. KMC_ENOMEM) is skipped, and its error is returned
+ * only when no setting could be timed. */
 KMC_API int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, const void* vel, int where,
                          int trial_steps, kmc_config* best, double* ms_per_step);
 

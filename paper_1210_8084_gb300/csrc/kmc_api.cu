@@ -761,6 +761,7 @@ int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, const void* 
     if (cfg->dim_pos == 3) trials.push_back({0.0, keep | KMC_FLAG_STAGED_SEARCH});
     double best_ms = -1.0;
     kmc_config pick = *cfg;
+    int first_rc = KMC_OK;
     std::vector<std::vector<int>> tried;   // search set-up of every timed trial
     for (const Trial& t : trials) {
         kmc_config c = *cfg;
@@ -768,10 +769,11 @@ int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, const void* 
         c.occupancy_target = t.occ;
         c.flags = t.flags;
         kmc_handle* h = nullptr;
-        int rc = kmc_init(&c, n, pos, vel, where, &h);
+        const int rc = kmc_init(&c, n, pos, vel, where, &h);
         if (rc != KMC_OK) {
-            if (best_ms < 0.0) return rc;   // the configuration itself is invalid
-            continue;                       // e.g. out of memory for this subdivision
+            if (rc == KMC_EINVAL) return rc;   // the configuration or the data are invalid
+            if (first_rc == KMC_OK) first_rc = rc;
+            continue;                          // e.g. out of memory for this subdivision
         }
         // settings that end in an already timed set-up (same subdivision and
         // search kernel for every instance) are not timed again
@@ -798,6 +800,7 @@ int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, const void* 
             pick = c;
         }
     }
+    if (best_ms < 0.0) return first_rc != KMC_OK ? first_rc : fail(nullptr, KMC_ECUDA, "no autotune trial ran");
     *best = pick;
     if (ms_per_step) *ms_per_step = best_ms;
     return KMC_OK;
