@@ -64,6 +64,8 @@ def lib():
         L.orc_mutual_pairs.restype = i64
         L.orc_collide_move.argtypes = [P, i64, dp, dp, ip, dp, dp, dp, ip]
         L.orc_collide_move.restype = None
+        L.orc_collide_move_ids.argtypes = [P, i64, dp, dp, ip, ctypes.c_void_p, dp, dp, dp, ip]
+        L.orc_collide_move_ids.restype = None
         L.orc_moments.argtypes = [P, i64, dp, dp, dp, dp, dp, dp]
         L.orc_moments.restype = None
         L.orc_step.argtypes = [P, i64, dp, dp, ip, ip, dp, dp, dp]
@@ -167,7 +169,10 @@ def mutual_pairs(best):
     return out[: 2 * m].reshape(m, 2)
 
 
-def collide_move(P, pos, vel, best):
+def collide_move(P, pos, vel, best, ids=None):
+    """Scatter, move and walls.  ids (increasing int64 global identities of the
+    entries) key the pairs' random directions when the state is a subset of a
+    larger system; None means ids = arange(n)."""
     pos, vel = _state(pos, vel)
     n = pos.shape[0]
     best = np.ascontiguousarray(best, dtype=np.int32)
@@ -175,7 +180,14 @@ def collide_move(P, pos, vel, best):
     vo = np.zeros_like(vel)
     W = np.zeros(n)
     paired = np.zeros(n, dtype=np.int32)
-    lib().orc_collide_move(ctypes.byref(P), n, _d(pos), _d(vel), _i(best), _d(po), _d(vo), _d(W), _i(paired))
+    if ids is None:
+        lib().orc_collide_move(ctypes.byref(P), n, _d(pos), _d(vel), _i(best), _d(po), _d(vo), _d(W), _i(paired))
+    else:
+        ids = np.ascontiguousarray(ids, dtype=np.int64)
+        if ids.shape != (n,) or (n > 1 and not np.all(np.diff(ids) > 0)):
+            raise ValueError("ids must be n strictly increasing identities")
+        lib().orc_collide_move_ids(ctypes.byref(P), n, _d(pos), _d(vel), _i(best),
+                                   ids.ctypes.data_as(ctypes.c_void_p), _d(po), _d(vo), _d(W), _i(paired))
     return po, vo, W, paired
 
 

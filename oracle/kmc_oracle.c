@@ -483,6 +483,14 @@ void orc_collide_move(const orc_params* P, int64_t n, const double* pos,
                       const double* vel, const int32_t* best, double* pos_out,
                       double* vel_out, double* virial_out, int32_t* paired_out)
 {
+    orc_collide_move_ids(P, n, pos, vel, best, NULL, pos_out, vel_out, virial_out, paired_out);
+}
+
+void orc_collide_move_ids(const orc_params* P, int64_t n, const double* pos,
+                          const double* vel, const int32_t* best, const int64_t* ids,
+                          double* pos_out, double* vel_out, double* virial_out,
+                          int32_t* paired_out)
+{
     const uint32_t key[2] = {(uint32_t)(P->seed & 0xffffffffu), (uint32_t)(P->seed >> 32)};
     for (int64_t i = 0; i < n; ++i) {
         const double* r = pos + 3 * i;
@@ -508,7 +516,8 @@ void orc_collide_move(const orc_params* P, int64_t n, const double* pos,
             double g = sqrt(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
             /* random isotropic direction for the pair, drawn once per pair from
              * Philox keyed by (lower id, step) */
-            uint32_t ctr[4] = {(uint32_t)lo, P->step, 0u, 0u}, x[4];
+            uint32_t id_lo = ids ? (uint32_t)ids[lo] : (uint32_t)lo;
+            uint32_t ctr[4] = {id_lo, P->step, 0u, 0u}, x[4];
             orc_philox4x32_10(ctr, key, x);
             double u1 = P->decide32 ? uniform32(x[0]) : uniform64(x[0], x[1]);
             double u2 = P->decide32 ? uniform32(x[2]) : uniform64(x[2], x[3]);

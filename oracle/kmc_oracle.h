@@ -94,6 +94,15 @@ void orc_collide_move(const orc_params* P, int64_t n, const double* pos,
                       const double* vel, const int32_t* best, double* pos_out,
                       double* vel_out, double* virial_out, int32_t* paired_out);
 
+/* The same for a subset of a larger system (one domain plus its halo): ids[i]
+ * is the global identity of entry i, which keys the pair's random direction.
+ * The entries must be in increasing id order, so that "lower index" and "lower
+ * id" agree.  ids == NULL means ids[i] = i. */
+void orc_collide_move_ids(const orc_params* P, int64_t n, const double* pos,
+                          const double* vel, const int32_t* best, const int64_t* ids,
+                          double* pos_out, double* vel_out, double* virial_out,
+                          int32_t* paired_out);
+
 /* Per-c-bin moments of the given state.  raw: C x 8 =
  * [N, Sum vx, Sum vy, Sum vz, Sum vx^2, Sum vy^2, Sum vz^2, Sum W];
  * derived: C x 8 = [n, ux, uy, uz, T, p_kin, p_vir, p];
