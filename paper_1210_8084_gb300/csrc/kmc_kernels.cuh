@@ -970,6 +970,18 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
     __syncthreads();
     const int nr = nr_s, total = tot_s;
     const bool once = total <= CAP;   // the whole window fits: stage it once for all home chunks
+    // Binary32 without per-candidate minimum image: candidates are staged in
+    // pairs (staged entries 2k and 2k + 1 side by side, negated so that
+    // x_i - x_j is one paired addition) and every home tests two candidates at
+    // once with the paired binary32 instructions of sm_100+.  Each component of
+    // __fadd2_rn / __fmul2_rn / __ffma2_rn rounds exactly as the scalar
+    // operation, and x - y is x + (-y) in IEEE arithmetic, so the decisions and
+    // d^2 are bit for bit those of poca_test_sh.
+    constexpr bool kPair = std::is_same<T, float>::value && !MINIMG;
+    float4* pA = reinterpret_cast<float4*>(sp);          // (-x, -x', -y, -y')
+    float4* pB = pA + CAP / 2;                            // (-z, -z', -vx, -vx')
+    float4* pC = reinterpret_cast<float4*>(sv);          // (-vy, -vy', -vz, -vz')
+    uint2* pT = reinterpret_cast<uint2*>(pC + CAP / 2);  // (tag, tag')
     auto stage = [&](int c0) {
         const int cn = min(CAP, total - c0);
         for (int e = tid; e < cn; e += blockDim.x) {
@@ -977,8 +989,23 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
             int r = 0;
             while (r + 1 < nr && rpre[r + 1] <= ge) ++r;
             const int64_t q = (int64_t)rq0[r] + (ge - rpre[r]);
-            sp[e] = ldg_vec(b.posA + q);
-            sv[e] = ldg_vec(b.velA + q);
+            if constexpr (kPair) {
+                const float4 P = ldg_vec(b.posA + q), Q = ldg_vec(b.velA + q);
+                const int k = e >> 1, s = e & 1;
+                float* a = reinterpret_cast<float*>(pA + k);
+                float* bz = reinterpret_cast<float*>(pB + k);
+                float* c = reinterpret_cast<float*>(pC + k);
+                a[s] = -P.x;
+                a[2 + s] = -P.y;
+                bz[s] = -P.z;
+                bz[2 + s] = -Q.x;
+                c[s] = -Q.y;
+                c[2 + s] = -Q.z;
+                reinterpret_cast<uint32_t*>(pT + k)[s] = __float_as_uint(P.w);
+            } else {
+                sp[e] = ldg_vec(b.posA + q);
+                sv[e] = ldg_vec(b.velA + q);
+            }
         }
     };
     if (once) {
@@ -1028,6 +1055,89 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
                 }
             }
         };
+        // paired layout: candidates [e0, e1) of one range, two per step; an
+        // entry without its pair (odd start or end of the range) alone
+        auto scan2 = [&](auto has_shift, auto check, int e0, int e1, int c0, int32_t qoff, const T sh[3]) {
+            if constexpr (kPair) {
+                constexpr bool SH = decltype(has_shift)::value;
+                constexpr bool CHK = decltype(check)::value;
+                // the closest-candidate bookkeeping of one passing candidate
+                auto take = [&](float d2, uint32_t idj, int32_t q) {
+                    if (d2 < bd || (d2 == bd && idj < bid)) {
+                        bd = d2;
+                        bid = idj;
+                    }
+                    atomicMin(&b.bkey[q], partner_key<float>(d2, tag));
+                };
+                auto one = [&](int e) {
+                    const int32_t q = qoff + e;
+                    if (CHK && q <= lim) return;
+                    const int l = e - c0, k = l >> 1, s = l & 1;
+                    const float* a = reinterpret_cast<const float*>(pA + k);
+                    const float* bz = reinterpret_cast<const float*>(pB + k);
+                    const float* c = reinterpret_cast<const float*>(pC + k);
+                    const float xj[3] = {-a[s], -a[2 + s], -bz[s]};
+                    const float vj[3] = {-bz[2 + s], -c[s], -c[2 + s]};
+                    float d2;
+                    if (poca_test_sh<float, DIM, false, SH>(G, xi, vi, xj, vj, sh, dt, R2, d2))
+                        take(d2, reinterpret_cast<const uint32_t*>(pT + k)[s], q);
+                };
+                // criteria 1-2 of one component after the paired part; then the
+                // real-root test and d^2 in scalar form, in poca_test_sh's order
+                auto rest = [&](float r0, float r1, float r2c, float a, float bb, uint32_t idj, int32_t q) {
+                    float rr = R<float>::mul(r0, r0);
+                    rr = R<float>::fma(r1, r1, rr);
+                    if (DIM == 3) rr = R<float>::fma(r2c, r2c, rr);
+                    const float disc = R<float>::fma(a, a, -R<float>::mul(bb, R<float>::sub(rr, R2)));
+                    if (!(disc >= 0.f)) return;
+                    take(R<float>::sub(rr, R<float>::div(R<float>::mul(a, a), bb)), idj, q);
+                };
+                const float2 xi0 = make_float2(xi[0], xi[0]), xi1 = make_float2(xi[1], xi[1]);
+                const float2 xi2 = make_float2(xi[2], xi[2]);
+                const float2 vi0 = make_float2(vi[0], vi[0]), vi1 = make_float2(vi[1], vi[1]);
+                const float2 vi2 = make_float2(vi[2], vi[2]);
+                const float2 sh0 = make_float2(sh[0], sh[0]), sh1 = make_float2(sh[1], sh[1]);
+                const float2 sh2 = make_float2(sh[2], sh[2]);
+                const float2 dt2 = make_float2(dt, dt);
+                int e = e0;
+                if ((e - c0) & 1) one(e++);
+#pragma unroll 2
+                for (; e + 1 < e1; e += 2) {
+                    const int k = (e - c0) >> 1;
+                    const float4 A = pA[k], B = pB[k], C = pC[k];
+                    float2 d0 = __fadd2_rn(xi0, make_float2(A.x, A.y));
+                    float2 d1 = __fadd2_rn(xi1, make_float2(A.z, A.w));
+                    float2 d2v = make_float2(0.f, 0.f);
+                    if (DIM == 3) d2v = __fadd2_rn(xi2, make_float2(B.x, B.y));
+                    if (SH) {
+                        d0 = __fadd2_rn(d0, sh0);
+                        d1 = __fadd2_rn(d1, sh1);
+                        if (DIM == 3) d2v = __fadd2_rn(d2v, sh2);
+                    }
+                    const float2 u0 = __fadd2_rn(vi0, make_float2(B.z, B.w));
+                    const float2 u1 = __fadd2_rn(vi1, make_float2(C.x, C.y));
+                    float2 a = __fmul2_rn(d0, u0);
+                    a = __ffma2_rn(d1, u1, a);
+                    float2 bb = __fmul2_rn(u0, u0);
+                    bb = __ffma2_rn(u1, u1, bb);
+                    if (DIM == 3) {
+                        const float2 u2 = __fadd2_rn(vi2, make_float2(C.z, C.w));
+                        a = __ffma2_rn(d2v, u2, a);
+                        bb = __ffma2_rn(u2, u2, bb);
+                    }
+                    const float2 f = __ffma2_rn(bb, dt2, a);
+                    const int32_t q = qoff + e;
+                    const bool ok0 = (!CHK || q > lim) && bb.x > 0.f && a.x < 0.f && f.x > 0.f;
+                    const bool ok1 = (!CHK || q + 1 > lim) && bb.y > 0.f && a.y < 0.f && f.y > 0.f;
+                    if (ok0 || ok1) {
+                        const uint2 tg = pT[k];
+                        if (ok0) rest(d0.x, d1.x, d2v.x, a.x, bb.x, tg.x, q);
+                        if (ok1) rest(d0.y, d1.y, d2v.y, a.y, bb.y, tg.y, q + 1);
+                    }
+                }
+                if (e < e1) one(e);
+            }
+        };
         for (int c0 = 0; c0 < total; c0 += CAP) {
             if (!once) {
                 __syncthreads();
@@ -1045,7 +1155,15 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
                 // (binary64 tests the whole window: the particle itself fails b > 0)
                 const bool chk = kSym && qoff + e0 <= (int32_t)h1 - 1;
                 const bool shifted = sh[0] != (T)0 || sh[1] != (T)0 || sh[2] != (T)0;
-                if (shifted) {
+                if constexpr (kPair) {
+                    if (shifted) {
+                        if (chk) scan2(std::true_type{}, std::true_type{}, e0, e1, c0, qoff, sh);
+                        else scan2(std::true_type{}, std::false_type{}, e0, e1, c0, qoff, sh);
+                    } else {
+                        if (chk) scan2(std::false_type{}, std::true_type{}, e0, e1, c0, qoff, sh);
+                        else scan2(std::false_type{}, std::false_type{}, e0, e1, c0, qoff, sh);
+                    }
+                } else if (shifted) {
                     if (chk) scan(std::true_type{}, std::true_type{}, e0, e1, c0, qoff, sh);
                     else scan(std::true_type{}, std::false_type{}, e0, e1, c0, qoff, sh);
                 } else {
