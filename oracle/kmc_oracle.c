@@ -20,6 +20,8 @@
  *   orc_collide_move    CM-frame scattering with random opposite directions,
  *                       t_poca (Eq. 12) and the split position update (Eqs. 13-14),
  *                       reflective walls (Sod test set-up), absorbing walls (Sedov test)
+ *   orc_collide_move_ids  the same on a subset of a larger system (one domain and
+ *                       its halo), the pair's random direction keyed by global ids
  *   orc_moments         n = N/V, bulk velocity (Eq. vel_b), stress tensor with
  *                       kinetic and collisional parts (Eq. stress), pressure
  *                       (Eq. 18), v_rms and T = m v_rms^2 / f (Eq. 19)
