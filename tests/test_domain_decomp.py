@@ -299,3 +299,43 @@ def test_two_gloo_ranks_equal_undivided():
     for k in range(steps):
         got = np.array([res[0]["partners"].get(f"{k}:{i}", res[1]["partners"].get(f"{k}:{i}")) for i in ids])
         assert np.array_equal(got, ref[k]["paired"])
+
+
+def _exchange_rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        g = np.random.default_rng(rank)
+        # block q of rank r has (r + 2 q) % 4 rows (some empty), tagged (r, q, row)
+        blocks = []
+        for q in range(world):
+            m = (rank + 2 * q) % 4
+            blocks.append(np.column_stack([np.full(m, rank), np.full(m, q), np.arange(m), g.random(m)]))
+        got = decomp.exchange(blocks)
+        out[rank] = dict(sent=[b.tolist() for b in blocks], got=[b.tolist() for b in got],
+                         dtmin=decomp.allreduce_min(1.0 + rank))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_exchange_three_gloo_ranks_with_empty_blocks():
+    """Every block arrives at its rank intact, empty blocks included, and the
+    minimum reduces over all ranks."""
+    mp = pytest.importorskip("torch.multiprocessing")
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    world = 3
+    with ctx.Manager() as m:
+        out = m.dict()
+        procs = [ctx.Process(target=_exchange_rank, args=(r, world, port, out)) for r in range(world)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(120)
+        assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
+        res = [dict(out[r]) for r in range(world)]
+    for r in range(world):
+        assert res[r]["dtmin"] == 1.0
+        for q in range(world):
+            assert res[r]["got"][q] == res[q]["sent"][r]
