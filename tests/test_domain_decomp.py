@@ -339,3 +339,40 @@ def test_exchange_three_gloo_ranks_with_empty_blocks():
         assert res[r]["dtmin"] == 1.0
         for q in range(world):
             assert res[r]["got"][q] == res[q]["sent"][r]
+
+
+def _failing_rank(rank, world, port, out):
+    import datetime
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(3)   # dies between steps, before the halo exchange
+    import time
+    t0 = time.time()
+    try:
+        decomp.exchange([np.zeros((2, 4)), np.ones((3, 4))])
+        out[rank] = dict(error=None, seconds=time.time() - t0)
+    except Exception as e:   # the collective fails instead of waiting forever
+        out[rank] = dict(error=type(e).__name__, seconds=time.time() - t0)
+
+
+def test_exchange_reports_a_dead_rank():
+    """A rank that dies between steps: the survivor's next exchange raises
+    (peer gone or process-group timeout) instead of hanging."""
+    mp = pytest.importorskip("torch.multiprocessing")
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    with ctx.Manager() as m:
+        out = m.dict()
+        procs = [ctx.Process(target=_failing_rank, args=(r, 2, port, out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(120)
+        for p in procs:
+            if p.is_alive():
+                p.kill()
+        assert procs[1].exitcode == 3
+        res = dict(out[0])
+    assert res["error"] is not None and res["seconds"] < 60, res
