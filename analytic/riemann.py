@@ -1,4 +1,4 @@
-"""Exact solution of the 1-D Riemann problem of an ideal gas (test infrastructure).
+"""Exact solution of the 1-D Riemann problem of an ideal gas (a reference solution).
 
 Used as the analytic reference of the Sod shock tube (Sect. "Sod test": left
 state (n_l, p_l), right state (0.125 n_l, 0.1 p_l), both at rest).  The

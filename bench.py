@@ -1,20 +1,34 @@
 """Throughput of the kinetic Monte Carlo step on GB300 (particle-steps/s).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--lam L]
-                    [--impl ours|reference]
+                    [--impl ours|reference] [--no-extras] [--no-e2e] [--no-cpu-baseline]
 
 A step is one pass of the whole hot path: closest-candidate search, pairing,
 CM scattering, free flight and walls, binning (histogram, scan, counting-sort
-scatter) and per-c-bin moments.  Default workload: the 16M-particle FP32 Sod
-tube with 2000 c-bins at lambda/L = 1e-3.  The timed region runs K steps
-launched kernel by kernel with CUDA events on the library's stream, bracketed
-by a barrier and device synchronisation; the state (16M x 64 B x 2 buffers)
-is far larger than L2, so no flush is needed between steps.
+scatter into (key, id) order) and per-c-bin moments.
 
-The reference arm (--impl reference) times the CPU oracle on the host cores,
-on a bounded slice of the same workload (central c-bins at full density).
-Under torchrun every rank runs its own replica (weak scaling, no collective on
-the data path); rank 0 prints one JSON line.
+Default workload: the largest single-GPU configuration of the paper's set-ups,
+the 3-D Sod tube with 512M particles on 1024 x 64 x 64 c-bins (lambda = 2e-4,
+binary32 state).  Its search is arithmetic-bound (about 5,300 candidates per
+particle in the 3^D neighbourhood), so the roofline is reported against the
+FP32 rate, with the HBM fraction of the step alongside.  The same JSON line
+carries, unless --no-extras:
+  * sod1d_16M: the 16M-particle slab Sod tube (2000 c-bins, lambda/L = 1e-3)
+    with the HBM fraction of its step and its Knudsen sweep (lambda/L = 1e-4 ...
+    1);
+  * batched_vs_plain: 256 Sod instances (N log-uniform in [50k, 2M],
+    lambda/L log-uniform in [1e-4, 1]) in one batched handle against the same
+    instances run one after another, with the L1 error of the ensemble against
+    the exact Riemann solution at t = 0.1.
+
+The timed region runs K steps launched kernel by kernel with CUDA events on the
+library's stream (the per-kernel durations come from those events), bracketed
+by a barrier and device synchronisation; every state is far larger than L2, so
+no flush is needed between steps.  The reference arm (--impl reference) times
+the CPU oracle on the host cores, on a bounded slice of the same workload
+(central c-bins at full density).  Under torchrun every rank runs its own
+replica (weak scaling, no collective on the data path); rank 0 prints one JSON
+line.
 """
 import argparse
 import json
@@ -32,6 +46,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/sec and HBM GB/s fraction on 1 GB300; batched vs plain at fixed L1 error"
 UNIT = "particle-steps/s"
+DEFAULT_WORKLOAD = "sod3d_fp32_512M"
 
 
 def dist_env():
@@ -43,7 +58,7 @@ def measured_peaks():
     if os.path.exists(p):
         with open(p) as f:
             return json.load(f), "measured"
-    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
 class ClockSampler:
@@ -96,7 +111,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-FLOPS_PER_TEST = 25          # binary32 operations per candidate test
+FLOPS_PER_TEST = 25          # binary32 operations per candidate test (the PoCA test with its compares)
+FP32_LANES_PER_SM = 128      # Blackwell SM: FP32 lanes
+FP64_TFLOPS_NOMINAL = 1.25   # GB300 dense binary64 (nominal)
+B_ALG_F32 = 72               # algorithmic bytes per particle-step (binary32 state)
 
 
 def max_over_ranks(values, world, device):
@@ -122,40 +140,42 @@ def replica_seed(seed, rank):
     return seed + rank
 
 
-def kernels_per_step(precision):
-    """Kernels of one step with moments: search, move, scan, scatter, moments,
-    two finalize kernels."""
-    return 7
-FP32_LANES = 152 * 128       # GB300: SMs x FP32 lanes per SM
-FP64_TFLOPS_NOMINAL = 1.25   # GB300 dense binary64 (nominal)
-B_ALG_F32 = 72               # algorithmic bytes per particle-step (binary32 state)
+def fp32_peak_tflops(n_sm, sm_mhz):
+    """FP32 rate from unit counts and clock: SMs x 128 lanes x 2 flops (FMA) x clock."""
+    return n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
 
 
-def profiled_traffic(kernel, workload, lam):
-    """dram bytes per launch of `kernel` from the committed ncu summary, if that
-    summary was taken on this workload and the current kernel source (else None)."""
+def profiled_traffic(kernel, workload, n):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary of this
+    workload, or of its 16M-particle stand-in with the same c-bin occupancy
+    (scaled by the particles a launch processes), if the summary was taken on
+    the current kernel source; else None."""
     import hashlib
-    if workload != "sod1d_fp32_16M" or lam != 1e-3:
+    stand_in = {"sod3d_fp32_512M": ("sod3d_16M", 16_000_000), "sod3d_fp32_16M": ("sod3d_16M", 16_000_000),
+                "sod1d_fp32_16M": ("sod1d_16M", 16_000_000)}
+    if workload not in stand_in:
         return None
-    path = os.path.join(ROOT, "profiles", f"{kernel}_kernel_sod1d_16M.md")
+    tag, n_prof = stand_in[workload]
+    path = os.path.join(ROOT, "profiles", f"{kernel}_kernel_{tag}.md")
     src = os.path.join(ROOT, "paper_1210_8084_gb300", "csrc", "kmc_kernels.cuh")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    fields = dict(ln.split(":", 1) for ln in text.splitlines() if ln.startswith(("source_sha256:", "traffic_bytes_per_launch:")))
+    fields = dict(ln.split(":", 1) for ln in text.splitlines()
+                  if ln.startswith(("source_sha256:", "traffic_bytes_per_launch:")))
     if fields.get("source_sha256", "").strip() != sha:
         return None
     try:
-        return int(fields["traffic_bytes_per_launch"].strip())
+        return int(int(fields["traffic_bytes_per_launch"].strip()) * n / n_prof)
     except (KeyError, ValueError):
         return None
 
 
 def algorithmic_bytes(n, n_keys, n_bins, frac_paired, phase):
     """Bytes each kernel must move at least (binary32 state), per launch.
-    State of a particle: position 12 B + id 4 B, velocity 12 B + instance 4 B."""
-    if phase == "search":
+    State of a particle: position 12 B + id 4 B, velocity 12 B + virial 4 B."""
+    if phase in ("search", "tile"):
         return n * (32 + 8)                    # read own state once, write the partner key
     if phase == "move":                        # own state, partner key, partner's key, B, key, slot, histogram
         return n * (32 + 8 + 8 + 32 + 4 + 4 + 4) + n * frac_paired * 32
@@ -168,35 +188,125 @@ def algorithmic_bytes(n, n_keys, n_bins, frac_paired, phase):
     return 0
 
 
-def make_workload(args):
+def make_workload(name, lam=None, n=None):
     from paper_1210_8084_gb300 import inputs
-    w = dict(inputs.WORKLOADS[args.workload])
-    if args.lam is not None:
-        w["lam"] = args.lam
-    if args.n is not None:
-        w["n"] = args.n
+    w = dict(inputs.WORKLOADS[name])
+    if lam is not None:
+        w["lam"] = lam
+    if n is not None:
+        w["n"] = n
     return w
+
+
+def nbar_of(w, n=None):
+    """Number density N / V of the full workload (Eq. 7's n)."""
+    V = float(np.prod([w["hi"][d] - w["lo"][d] for d in range(w["dim_pos"])]))
+    return (w["n"] if n is None else n) / V
+
+
+PHASE_NAMES = ("search", "tile", "move", "scan", "scatter", "moments", "finalize")
+
+
+def run_device(k, w, seed, steps, warmup, stream, occ=0.0, clocks=None, barrier=None, flags=0, state=None):
+    """One handle on a workload: warm-up, then `steps` timed steps launched
+    kernel by kernel with events on the handle's stream.  Returns a dict of
+    the timings, the handle's description and a few diagnostics."""
+    import torch
+    from paper_1210_8084_gb300 import inputs
+    dtype = np.float32 if w["precision"] == 32 else np.float64
+    pos, vel = state if state is not None else inputs.make_state(w, seed=seed, dtype=dtype)
+    cfg = k.make_config(dim_pos=w["dim_pos"], n_cells=w["n_cells"], lo=w["lo"], hi=w["hi"], bc=w["bc"],
+                        lam=w["lam"], dt=w["dt"], seed=seed, precision=w["precision"], stream=stream.cuda_stream,
+                        occupancy_target=occ, flags=flags)
+    sim = k.Simulation(cfg, pos, vel)
+    info = sim.info()
+    e_start = sim.moments()[2][0, 1]
+    sim.step_profiled(warmup, want_moments=1)
+    if barrier:
+        barrier()
+    if clocks:
+        clocks.start()
+    if barrier:
+        barrier()
+    prof = sim.step_profiled(steps, want_moments=1)
+    if barrier:
+        barrier()
+    clk = clocks.stop() if clocks else None
+    raw, der, glob = sim.moments()
+    out = dict(prof=prof, info=info, clocks=clk, pairs=float(glob[0, 6]), e_start=float(e_start),
+               e_end=float(glob[0, 1]), cand=sim.window_size(), cfg=cfg, pos=pos, vel=vel)
+    sim.close()
+    torch.cuda.synchronize()
+    return out
+
+
+def roofline_of(w, r, steps, n_sm, peaks, peak_src, workload):
+    """Roofline object of the dominant kernel of a run (see run_device)."""
+    n = w["n"]
+    phases = {p: r["prof"][p] / steps for p in PHASE_NAMES}
+    dom = max(("search", "tile", "move", "scan", "scatter", "moments"), key=lambda p: phases[p])
+    t_dom = phases[dom] * 1e-3
+    frac_paired = 2 * r["pairs"] / n
+    kernel = {"search": "search", "tile": "tile_search"}.get(dom, dom)
+    traffic = profiled_traffic(kernel, workload, n)
+    if dom in ("search", "tile"):
+        # arithmetic-bound: 25 binary32 operations per pair test.  The window of a
+        # particle holds C_p candidates (itself included); binary32 tests every
+        # unordered pair once, (C_p - 1) / 2 per particle, binary64 all C_p.
+        cand = r["cand"]
+        tests = (cand - 1.0) / 2.0 if w["precision"] == 32 else cand
+        flops = FLOPS_PER_TEST * tests * n
+        if w["precision"] == 32:
+            sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+            peak = fp32_peak_tflops(n_sm, sm_mhz)
+            src = f"{n_sm} SMs (read at run time) x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz ({peak_src} max SM clock)"
+        else:
+            peak = FP64_TFLOPS_NOMINAL
+            src = "nominal GB300 binary64 rate"
+        achieved = flops / t_dom / 1e12
+        roof = {"bound": "alu", "kernel": kernel + "_kernel", "achieved": round(achieved, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": src,
+                "ms_per_launch": round(phases[dom], 4), "algorithmic_flops_per_launch": int(flops),
+                "candidates_per_particle": round(cand, 3), "pair_tests_per_particle": round(tests, 3)}
+        if traffic is not None:
+            roof["traffic_gbs"] = round(traffic / t_dom / 1e9, 1)
+    else:
+        ab = algorithmic_bytes(n, r["info"].n_search_cells, r["info"].n_bins, frac_paired, dom)
+        achieved = ab / t_dom / 1e9
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        roof = {"bound": "hbm", "kernel": kernel + "_kernel", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": f"{peak_src} hbm_gbs", "ms_per_launch": round(phases[dom], 4),
+                "algorithmic_bytes_per_launch": int(ab)}
+    return roof, phases
+
+
+def step_hbm_of(n, ms_per_step, peaks):
+    b = B_ALG_F32 * n
+    gbs = b / (ms_per_step * 1e-3) / 1e9
+    return {"algorithmic_bytes_per_step": int(b), "achieved_gbs": round(gbs, 1),
+            "frac_of_measured_hbm": round(gbs / float(peaks.get("hbm_gbs", 6800.0)), 4)}
+
+
+def launches_of(info, steps):
+    return (info.kernels_per_step + info.kernels_moments) * steps
 
 
 def ours(args):
     import torch
     import paper_1210_8084_gb300 as k
-    from paper_1210_8084_gb300 import inputs
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    w = make_workload(args)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    peaks, peak_src = measured_peaks()
+    w = make_workload(args.workload, args.lam, args.n)
     n = w["n"]
-    pos, vel = inputs.make_state(w, seed=replica_seed(w["seed"], rank))
-    dtype = np.float32 if w["precision"] == 32 else np.float64
-    pos, vel = inputs.cast_state(pos, vel, dtype, w["lo"], w["hi"], w["bc"])
+    seed = replica_seed(w["seed"], rank)
     stream = torch.cuda.Stream()
-    cfg = k.make_config(dim_pos=w["dim_pos"], n_cells=w["n_cells"], lo=w["lo"], hi=w["hi"], bc=w["bc"],
-                        lam=w["lam"], dt=w["dt"], seed=replica_seed(w["seed"], rank), precision=w["precision"],
-                        stream=stream.cuda_stream, occupancy_target=args.occ)
 
     def barrier():
         torch.cuda.synchronize()
@@ -205,24 +315,10 @@ def ours(args):
             dist.barrier()
 
     # ---------------- device-resident throughput (inputs already in HBM)
-    sim = k.Simulation(cfg, pos, vel)
-    info = sim.info()
-    e_start = sim.moments()[2][0, 1]
-    sim.step_profiled(args.warmup, want_moments=1)
-    clocks = ClockSampler(local)
-    barrier()
-    clocks.start()
-    barrier()
-    prof = sim.step_profiled(args.steps, want_moments=1)
-    barrier()
-    clk = clocks.stop()
-    elapsed_ms = max_over_ranks([prof["total"]], world, "cuda")[0]
-    raw, der, glob = sim.moments()
-    pairs = float(glob[0, 6])
-    frac_paired = 2 * pairs / n
-    energy_drift = float(glob[0, 1] / e_start - 1.0)
-    cand = sim.window_size()
-    sim.close()
+    r = run_device(k, w, seed, args.steps, args.warmup, stream, occ=args.occ, clocks=ClockSampler(local),
+                   barrier=barrier)
+    elapsed_ms = max_over_ranks([r["prof"]["total"]], world, "cuda")[0]
+    pos, vel, cfg = r.pop("pos"), r.pop("vel"), r["cfg"]
 
     # ---------------- end to end through the C ABI with host buffers
     e2e = None
@@ -244,113 +340,131 @@ def ours(args):
         state_bytes = pos.nbytes + vel.nbytes
         e2e = {"value": job_rate(n, world, args.steps, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": int(state_bytes / args.steps),
-               "d2h_bytes_per_step": int(mom.numel() * 8 + state_bytes / args.steps)}
+               "d2h_bytes_per_step": int(mom.numel() * 8 + state_bytes / args.steps),
+               "includes": "kmc_init from pinned host arrays, every step's moments to host, the final state to host"}
+        del pin_pos, pin_vel
+    del pos, vel
+
+    extras = {}
+    if not args.no_extras and args.workload == DEFAULT_WORKLOAD:
+        extras["sod1d_16M"] = sod1d_extra(k, args, stream, n_sm, peaks, peak_src, barrier, world, rank)
+        extras["batched_vs_plain"] = batched_vs_plain(k, args, stream, rank, world)
 
     if rank != 0:
         return None
 
-    # ---------------- roofline of the dominant kernel
-    peaks, peak_src = measured_peaks()
-    phases = {p: prof[p] / args.steps for p in ("search", "move", "scan", "scatter", "moments", "finalize")}
-    dom = max(("search", "move", "scan", "scatter", "moments"), key=lambda p: phases[p])
-    t_dom = phases[dom] * 1e-3
-    traffic = profiled_traffic(dom, args.workload, w["lam"])
-    if dom == "search":
-        # arithmetic-bound: 25 binary32 operations per pair test (PoCA test with
-        # its early outs).  The window of a particle holds C_p candidates (itself
-        # included); binary32 tests every unordered pair once, (C_p - 1) / 2 per
-        # particle, binary64 tests all C_p.
-        tests = (cand - 1.0) / 2.0 if w["precision"] == 32 else cand
-        flops = FLOPS_PER_TEST * tests * n
-        if w["precision"] == 32:
-            sm_clock = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-            peak = FP32_LANES * 2 * sm_clock / 1e12
-            peak_src = "fp32 lanes x 2 x max SM clock (derived)"
-        else:
-            peak = FP64_TFLOPS_NOMINAL
-            peak_src = "nominal GB300 binary64 rate"
-        achieved = flops / t_dom / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_source": peak_src, "ms_per_launch": round(phases[dom], 4),
-                "algorithmic_flops_per_launch": int(flops), "candidates_per_particle": round(cand, 3),
-                "pair_tests_per_particle": round(tests, 3)}
-    else:
-        ab = algorithmic_bytes(n, info.n_search_cells, info.n_bins, frac_paired, dom)
-        achieved = ab / t_dom / 1e9
-        peak = float(peaks.get("hbm_gbs", 6800.0))
-        roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_source": f"{peak_src} hbm_gbs", "ms_per_launch": round(phases[dom], 4),
-                "algorithmic_bytes_per_launch": int(ab)}
-    step_bytes = B_ALG_F32 * n
-    step_hbm = {"algorithmic_bytes_per_step": int(step_bytes),
-                "achieved_gbs": round(step_bytes / (elapsed_ms / args.steps * 1e-3) / 1e9, 1),
-                "frac_of_measured_hbm": round(step_bytes / (elapsed_ms / args.steps * 1e-3) / 1e9 /
-                                              float(peaks.get("hbm_gbs", 6800.0)), 4)}
+    roof, phases = roofline_of(w, r, args.steps, n_sm, peaks, peak_src, args.workload)
     value = job_rate(n, world, args.steps, elapsed_ms * 1e-3)
+    info = r["info"]
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if w["precision"] == 32 else "f64",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload} lambda/L={w['lam']:g}", "n_particles": n,
-                   "n_cells": list(w["n_cells"]), "dt": w["dt"], "precision": w["precision"],
-                   "search_cells": int(info.n_search_cells), "sub_cells": list(info.sub_cells),
-                   "occupancy_target": args.occ,
-                   "l2": "no flush: state 2 x %.2f GB > 129 MB L2" % (n * 64 / 1e9),
-                   "parallelism": f"replicas x{world}"},
+        "config": {"workload": f"{args.workload} lambda={w['lam']:g}", "n_particles": n,
+                   "n_cells": list(w["n_cells"]), "box": [list(w["lo"]), list(w["hi"])], "dt": w["dt"],
+                   "precision": w["precision"], "search_cells": int(info.n_search_cells),
+                   "sub_cells": list(info.sub_cells), "occupancy_target": args.occ,
+                   "l2": "no flush: state 2 x %.2f GB > 129 MB L2" % (n * 32 / 1e9),
+                   "parallelism": f"replicas x{world}", "n_sm": n_sm},
         "phase_ms_per_step": {p: round(v, 4) for p, v in phases.items()},
-        "collision_fraction": round(frac_paired, 4),
+        "collision_fraction": round(2 * r["pairs"] / n, 4),
         "roofline": roof,
-        "step_hbm": step_hbm,
-        "energy_drift_rel": energy_drift,
+        "step_hbm": step_hbm_of(n, elapsed_ms / args.steps, peaks),
+        "energy_drift_rel_device": (r["e_end"] - r["e_start"]) / r["e_start"],
         "e2e": e2e,
-        "gpu_launches": kernels_per_step(w["precision"]) * args.steps,
-        "clocks": clk,
+        "gpu_launches": launches_of(info, args.steps),
+        "clocks": r["clocks"],
     }
     if not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(w, args.cpu_slice_bins, single_thread_bins=2)
+        cb, drift = cpu_baseline(w, slice_bins(w, args.cpu_slice_bins), single_thread_bins=2, device_check=True)
+        out["cpu_baseline"] = cb
+        out["energy_fp32_vs_fp64_oracle"] = drift
+    out.update(extras)
     return out
 
 
-def batched(args):
-    """256 independent Sod instances (log-uniform N and lambda) stepped in one
-    launch sequence per step, against the same instances stepped one handle
-    at a time.  Per-instance states are identical either way (tested), so both
-    runs have the same L1 error; this reports the throughput of each."""
-    import torch
-    import paper_1210_8084_gb300 as k
-    from paper_1210_8084_gb300 import inputs
+def sod1d_extra(k, args, stream, n_sm, peaks, peak_src, barrier, world, rank):
+    """The 16M-particle slab Sod tube: step throughput, its HBM fraction, the
+    roofline of its dominant kernel, and the Knudsen sweep."""
+    name = "sod1d_fp32_16M"
+    w = make_workload(name)
+    seed = replica_seed(w["seed"], rank)
+    steps = max(args.steps, 20)
+    r = run_device(k, w, seed, steps, args.warmup, stream, barrier=barrier)
+    state = (r.pop("pos"), r.pop("vel"))
+    ms = max_over_ranks([r["prof"]["total"]], world, "cuda")[0] / steps
+    roof, phases = roofline_of(w, r, steps, n_sm, peaks, peak_src, name)
+    sweep = {}
+    for lam in w["lam_sweep"]:
+        wl = dict(w, lam=lam)
+        rs = run_device(k, wl, seed, 10, 3, stream, barrier=barrier, state=state)
+        rs.pop("pos"), rs.pop("vel")
+        ms_l = max_over_ranks([rs["prof"]["total"]], world, "cuda")[0] / 10
+        sweep[f"{lam:g}"] = {"value": job_rate(w["n"], world, 1, ms_l * 1e-3), "ms_per_step": round(ms_l, 4),
+                             "candidates_per_particle": round(rs["cand"], 2),
+                             "collision_fraction": round(2 * rs["pairs"] / w["n"], 4),
+                             "step_hbm_frac": step_hbm_of(w["n"], ms_l, peaks)["frac_of_measured_hbm"]}
+    return {"workload": f"{name} lambda/L={w['lam']:g}", "n_particles": w["n"], "steps": steps,
+            "value": job_rate(w["n"], world, steps, ms * steps * 1e-3), "unit": UNIT, "ms_per_step": round(ms, 4),
+            "phase_ms_per_step": {p: round(v, 4) for p, v in phases.items()},
+            "step_hbm": step_hbm_of(w["n"], ms, peaks), "roofline": roof,
+            "search_cells": int(r["info"].n_search_cells), "collision_fraction": round(2 * r["pairs"] / w["n"], 4),
+            "energy_drift_rel_device": (r["e_end"] - r["e_start"]) / r["e_start"],
+            "gpu_launches": launches_of(r["info"], steps), "knudsen_sweep": sweep}
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+def batched_instances(rank, n_inst=None):
+    from paper_1210_8084_gb300 import inputs
     w = dict(inputs.WORKLOADS["sod1d_batched_256"])
-    n_inst = args.instances or w["n_instances"]
+    n_inst = n_inst or w["n_instances"]
     ns, lams = inputs.log_uniform_instances(n_inst, seed=replica_seed(w["seed"], rank), n_range=w["n_range"],
                                             lam_range=w["lam_range"])
     P, V, insts = [], [], []
     for i in range(n_inst):
-        p, v = inputs.sod_tube(int(ns[i]), seed=1000 * rank + i)
-        p, v = inputs.cast_state(p, v, np.float32, w["lo"], w["hi"], w["bc"])
+        p, v = inputs.sod_tube(int(ns[i]), seed=1000 * rank + i, dtype=np.float32)
         P.append(p)
         V.append(v)
         insts.append(dict(n=int(ns[i]), lam=float(lams[i]), dt=w["dt"], seed=1000 * rank + i))
+    return w, ns, lams, P, V, insts
+
+
+def l1_of_batch(raw, ns, lams, nc, t, lam_max=1e-3):
+    """Relative L1 distance of n, p, T per instance to the exact Riemann solution
+    (Sect. "Sod test"; gamma = 5/3), for the instances with lambda/L <= lam_max."""
+    from analytic import riemann
+    ex = riemann.sod_profile(np.linspace(0, 1, nc + 1), t, 0.5, 1.0, 1.0)
+    rows = []
+    for i in np.flatnonzero(lams <= lam_max):
+        R = raw[nc * i:nc * (i + 1)]
+        N = R[:, 0]
+        u = R[:, 1] / N
+        T = ((R[:, 4] + R[:, 5] + R[:, 6]) / N - (R[:, 1:4] ** 2).sum(1) / N ** 2) / 3.0
+        dens = N * nc / (ns[i] * 8 / 9 / 0.5)
+        q = (dens, dens * T, T)
+        rows.append([float(np.abs(a - b).sum() / np.abs(b).sum()) for a, b in zip(q, (ex[:, 0], ex[:, 2], ex[:, 3]))])
+    return np.array(rows)
+
+
+def batched_vs_plain(k, args, stream, rank, world, n_inst=None):
+    """256 independent Sod instances stepped in one launch sequence per step,
+    against the same instances stepped one handle at a time with the same
+    search set-up.  Per-instance states and moments are identical either way
+    (tested bit for bit), so both runs have the same L1 error, reported here
+    for the instances with lambda/L <= 1e-3 after the batch is run on to t = 0.1."""
+    import torch
+    w, ns, lams, P, V, insts = batched_instances(rank, n_inst)
+    n_inst = len(ns)
     n_total = int(ns.sum())
-    stream = torch.cuda.Stream()
     base = dict(dim_pos=3, n_cells=w["n_cells"], lo=w["lo"], hi=w["hi"], bc=w["bc"], precision=32,
                 stream=stream.cuda_stream)
 
     def timed(h, steps):
-        with torch.cuda.stream(stream):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            k.kmc_step(h, steps, 1)
-            e1.record(stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        k.kmc_step(h, steps, 1)
+        e1.record(stream)
         e1.synchronize()
         return e0.elapsed_time(e1)
 
@@ -358,15 +472,21 @@ def batched(args):
     pos_all, vel_all = np.concatenate(P), np.concatenate(V)
     # search set-up by measurement (outside the timed region); the plain runs use the same set-up
     tuned, tuned_ms = k.kmc_autotune(cfg, n_total, pos_all, vel_all, k.KMC_WHERE_HOST, 2)
-    cfg = tuned
-    sim = k.Simulation(cfg, pos_all, vel_all)
+    sim = k.Simulation(tuned, pos_all, vel_all)
+    del pos_all, vel_all
     k.kmc_step(sim.h, args.warmup, 1)
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    ms_batched = timed(sim.h, args.steps)
-    clk = clocks.stop()
+    steps = args.steps
+    ms_batched = timed(sim.h, steps)
+    info = sim.info()
+    # run on to t = 0.1 for the accuracy of the ensemble
+    t_steps = int(round(0.1 / w["dt"]))
+    done = args.warmup + steps
+    if t_steps > done:
+        sim.step(t_steps - done, want_moments=1)
+    raw, _, _ = sim.moments()
     sim.close()
+    l1 = l1_of_batch(raw, ns, lams, w["n_cells"][0], max(t_steps, done) * w["dt"])
     ms_plain = 0.0
     for i in range(n_inst):
         c = k.make_config(**base, lam=insts[i]["lam"], dt=insts[i]["dt"], seed=insts[i]["seed"],
@@ -374,95 +494,158 @@ def batched(args):
         s1 = k.Simulation(c, P[i], V[i])
         k.kmc_step(s1.h, args.warmup, 1)
         torch.cuda.synchronize()
-        ms_plain += timed(s1.h, args.steps)
+        ms_plain += timed(s1.h, steps)
         s1.close()
     ms_batched, ms_plain = max_over_ranks([ms_batched, ms_plain], world, "cuda")
+    value = job_rate(n_total, world, steps, ms_batched * 1e-3)
+    plain = job_rate(n_total, world, steps, ms_plain * 1e-3)
+    med = np.median(l1, axis=0) if len(l1) else [None] * 3
+    return {"workload": f"sod1d_batched_{n_inst}", "instances": n_inst, "n_particles": n_total,
+            "n_range": list(w["n_range"]), "lambda_range": list(w["lam_range"]),
+            "n_cells_per_instance": list(w["n_cells"]), "dt": w["dt"], "steps": steps,
+            "autotuned": {"occupancy_target": tuned.occupancy_target, "flags": tuned.flags,
+                          "ms_per_step_in_tuning": round(tuned_ms, 3)},
+            "batched": value, "plain_sequential": plain, "speedup": value / plain, "unit": UNIT,
+            "ms_per_step_batched": ms_batched / steps, "ms_per_step_plain": ms_plain / steps,
+            "gpu_launches_batched": launches_of(info, steps),
+            "l1_error": {"at_t": max(t_steps, done) * w["dt"], "instances_lambda_le_1e-3": int(len(l1)),
+                         "median_n_p_T": [round(float(x), 4) for x in med],
+                         "max_n_p_T": [round(float(x), 4) for x in l1.max(0)] if len(l1) else None,
+                         "same_for_plain": "per-instance states and moments bit-identical (tested)"}}
+
+
+def batched_line(args):
+    import torch
+    import paper_1210_8084_gb300 as k
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    stream = torch.cuda.Stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    b = batched_vs_plain(k, args, stream, rank, world, args.instances or None)
+    clk = clocks.stop()
     if rank != 0:
         return None
-    value = job_rate(n_total, world, args.steps, ms_batched * 1e-3)
-    plain = job_rate(n_total, world, args.steps, ms_plain * 1e-3)
-    return {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_batched / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"sod1d_batched_{n_inst}", "instances": n_inst, "n_particles": n_total,
-                   "n_range": list(w["n_range"]), "lambda_range": list(w["lam_range"]),
-                   "n_cells_per_instance": list(w["n_cells"]), "dt": w["dt"],
-                   "autotuned": {"occupancy_target": tuned.occupancy_target, "flags": tuned.flags,
-                                 "ms_per_step_in_tuning": round(tuned_ms, 3)},
-                   "l2": "no flush: state %.1f GB > 129 MB L2" % (n_total * 64 / 1e9)},
-        "batched_vs_plain": {"batched": value, "plain_sequential": plain, "speedup": value / plain,
-                             "ms_per_step_plain": ms_plain / args.steps,
-                             "l1_error": "identical (per-instance states bit-identical)"},
-        "gpu_launches": kernels_per_step(w["precision"]) * args.steps,
-        "clocks": clk,
-    }
+    return {"metric": METRIC, "value": b["batched"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": b["ms_per_step_batched"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": b["workload"], "instances": b["instances"], "n_particles": b["n_particles"],
+                       "l2": "no flush: state %.1f GB > 129 MB L2" % (b["n_particles"] * 64 / 1e9)},
+            "batched_vs_plain": b, "gpu_launches": b["gpu_launches_batched"], "clocks": clk}
 
 
-def oracle_slice(w, n_bins_slice, seed=0):
-    """Central c-bins of the workload at full density: the same particles per
-    c-bin and per neighbourhood as the full run."""
+def oracle_slice(w, nbx, seed=0):
+    """A bounded slice of the workload at full density: nbx c-bins in x
+    around the split and, for 3-D c-bin grids, 8 x 8 c-bins in y and z
+    (periodic, same c-bin widths), so every particle has the same number of
+    candidates as in the full run (the slice's x ends are walls).  Returns
+    (pos, vel, lo, hi, n_cells)."""
     from paper_1210_8084_gb300 import inputs
-    n, ncx = w["n"], w["n_cells"][0]
-    dx = (w["hi"][0] - w["lo"][0]) / ncx
-    half = n_bins_slice // 2
-    lo = (0.5 - half * dx, w["lo"][1], w["lo"][2])
-    hi = (0.5 + half * dx, w["hi"][1], w["hi"][2])
-    # particles of the full tube that fall in the slice
-    n_l = int(round(n * 8 / 9))
-    dens_l = n_l / 0.5
-    dens_r = (n - n_l) / 0.5
-    n_sl = int(round(dens_l * half * dx))
-    n_sr = int(round(dens_r * half * dx))
+    n, nc = w["n"], w["n_cells"]
+    L = [w["hi"][d] - w["lo"][d] for d in range(3)]
+    dx = L[0] / nc[0]
+    half = nbx // 2
+    lo = [0.5 - half * dx, w["lo"][1], w["lo"][2]]
+    hi = [0.5 + half * dx, w["hi"][1], w["hi"][2]]
+    cells = [nbx, 1, 1]
+    for d in (1, 2):
+        if nc[d] > 8:
+            hi[d] = lo[d] + 8 * L[d] / nc[d]
+            cells[d] = 8
+    # particles of the full tube that fall in the slice (left density 8/9 of N over half the box)
+    V_half = 0.5 * L[0] * L[1] * L[2]
+    dens_l = n * 8 / 9 / V_half
+    dens_r = n / 9 / V_half
+    area = (hi[1] - lo[1]) * (hi[2] - lo[2])
+    n_sl = int(round(dens_l * half * dx * area))
+    n_sr = int(round(dens_r * half * dx * area))
     pl, vl = inputs.sod_tube(2 * n_sl, seed, lo=lo, hi=hi, rho=(1.0, 1.0), p=(1.0, 1.0))
     pr, vr = inputs.sod_tube(2 * n_sr, seed + 1, lo=lo, hi=hi, rho=(1.0, 1.0), p=(0.8, 0.8))
     pos = np.concatenate([pl[pl[:, 0] < 0.5][:n_sl], pr[pr[:, 0] >= 0.5][:n_sr]])
     vel = np.concatenate([vl[pl[:, 0] < 0.5][:n_sl], vr[pr[:, 0] >= 0.5][:n_sr]])
-    return pos, vel, lo, hi
+    if w["precision"] == 32:
+        pos, vel = inputs.cast_state(pos, vel, np.float32, lo, hi, w["bc"])
+    return pos.astype(np.float64), vel.astype(np.float64), tuple(lo), tuple(hi), tuple(cells)
 
 
-def cpu_baseline(w, n_bins_slice=8, steps=1, single_thread_bins=0):
+def cpu_baseline(w, n_bins_slice=8, steps=1, single_thread_bins=0, device_check=False):
     """The CPU oracle on the host cores (all OpenMP threads) on a slice of
-    central c-bins at full density; optionally also on one thread."""
+    central c-bins at full density; optionally also on one thread.  With
+    device_check, the binary32 device path steps the same slice from the same
+    state, and the total energies after the step are compared (the FP32 drift
+    against the binary64 oracle)."""
     import oracle
+    R2 = oracle.contact_R2(w["lam"], 0.0, nbar_of(w))
 
     def run(nb):
-        pos, vel, lo, hi = oracle_slice(w, nb)
-        nbar = w["n"] / 1.0
-        P = oracle.make_params(w["dim_pos"], (nb, 1, 1), lo, hi, w["bc"],
-                               R2=oracle.contact_R2(w["lam"], 0.0, nbar), dt=w["dt"], seed=0,
+        pos, vel, lo, hi, cells = oracle_slice(w, nb)
+        P = oracle.make_params(w["dim_pos"], cells, lo, hi, w["bc"], R2=R2, dt=w["dt"], seed=0,
                                decide32=w["precision"] == 32)
+        p, v = pos, vel
         t0 = time.perf_counter()
         for s in range(steps):
             P.step = s
-            pos, vel = oracle.step(P, pos, vel)[:2]
-        return pos.shape[0], time.perf_counter() - t0
+            p, v = oracle.step(P, p, v)[:2]
+        return pos, vel, p, v, time.perf_counter() - t0, lo, hi, cells
 
     cores = oracle.set_threads(0)
-    m, el = run(n_bins_slice)
+    pos, vel, p1, v1, el, lo, hi, cells = run(n_bins_slice)
+    m = pos.shape[0]
     out = {"value": m * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle", "particles": m,
-           "sample": f"{steps} oracle step(s) of the {n_bins_slice} central c-bins at full density: "
-                     f"{m} particles with the full run's neighbourhood occupancy, {el:.2f} s"}
+           "sample": f"{steps} oracle step(s) of the {n_bins_slice} central x c-bins"
+                     f"{' x %d x %d c-bins in y, z' % (cells[1], cells[2]) if cells[1] > 1 else ''} at full "
+                     f"density: {m} particles with the full run's neighbourhood occupancy, {el:.2f} s"}
     if single_thread_bins > 0:
         oracle.set_threads(1)
         try:
-            m1, el1 = run(single_thread_bins)
+            pos1, _, _, _, el1, _, _, _ = run(single_thread_bins)
+            m1 = pos1.shape[0]
         finally:
             oracle.set_threads(cores)
         out["single_thread"] = {"value": m1 * steps / el1, "unit": UNIT, "cores": 1, "particles": m1,
-                                "sample": f"{steps} oracle step(s) of the {single_thread_bins} central c-bins, "
+                                "sample": f"{steps} oracle step(s) of the {single_thread_bins} central x c-bins, "
                                           f"{el1:.2f} s"}
-    return out
+    drift = None
+    if device_check:
+        import paper_1210_8084_gb300 as k
+        dtype = np.float32 if w["precision"] == 32 else np.float64
+        cfg = k.make_config(dim_pos=w["dim_pos"], n_cells=cells, lo=lo, hi=hi, bc=w["bc"], sigma=np.pi * R2,
+                            dt=w["dt"], seed=0, precision=w["precision"])
+        sim = k.Simulation(cfg, pos.astype(dtype), vel.astype(dtype))
+        e0 = sim.moments()[2][0, 1]
+        sim.step(steps, want_moments=1)
+        e_dev = sim.moments()[2][0, 1]
+        sim.close()
+        e_orc = 0.5 * float((v1 * v1).sum())
+        e_in = 0.5 * float((vel * vel).sum())
+        drift = {"steps": steps, "particles": m, "e_initial": e_in, "e_device": float(e_dev), "e_oracle": e_orc,
+                 "device_vs_oracle_rel": (float(e_dev) - e_orc) / e_orc,
+                 "device_drift_rel": (float(e_dev) - float(e0)) / float(e0),
+                 "oracle_drift_rel": (e_orc - e_in) / e_in,
+                 "sample": "the cpu_baseline slice, stepped by the binary32 device path and the binary64 oracle"}
+    return out, drift
+
+
+def slice_bins(w, asked):
+    """x c-bins of the oracle's slice: 8 for slab c-bins (8 x about 8,000
+    particles), 16 for 3-D c-bin grids (16 x 8 x 8 c-bins); `asked` > 0
+    overrides."""
+    if asked > 0:
+        return asked
+    return 16 if w["dim_pos"] == 3 and w["n_cells"][1] > 1 else 8
 
 
 def reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return None
-    w = make_workload(args)
+    w = make_workload(args.workload, args.lam, args.n)
     samples = []
     for s in range(args.warmup + args.steps):
-        r = cpu_baseline(w, args.ref_slice_bins)
+        r, _ = cpu_baseline(w, slice_bins(w, args.ref_slice_bins))
         if s >= args.warmup:
             samples.append(r)
     value = statistics.median([r["value"] for r in samples])
@@ -474,8 +657,8 @@ def reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n_part / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload} lambda/L={w['lam']:g}", "n_particles": w["n"],
-                   "n_cells": list(w["n_cells"]), "sample_bins": args.ref_slice_bins},
+        "config": {"workload": f"{args.workload} lambda={w['lam']:g}", "n_particles": w["n"],
+                   "n_cells": list(w["n_cells"]), "sample_x_bins": slice_bins(w, args.ref_slice_bins)},
         "cpu_baseline": cb,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -484,9 +667,9 @@ def reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="sod1d_fp32_16M")
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--lam", type=float, default=None)
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--occ", type=float, default=0.0, help="particles per search cell (0: library default)")
@@ -494,14 +677,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-slice-bins", type=int, default=8)
-    ap.add_argument("--ref-slice-bins", type=int, default=2)
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--cpu-slice-bins", type=int, default=0, help="x c-bins of the oracle slice (0: per workload)")
+    ap.add_argument("--ref-slice-bins", type=int, default=0, help="x c-bins of the reference arm's slice (0: same)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         out = reference(args)
     elif args.workload.startswith("sod1d_batched"):
-        out = batched(args)
+        out = batched_line(args)
     else:
         out = ours(args)
     if out is not None:

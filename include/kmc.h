@@ -21,10 +21,15 @@
  * on the stream given in kmc_config.stream (a private stream when NULL), in
  * order; calls that return host data synchronise that stream.
  *
- * Precision: precision = 32 holds particle state in binary32 (per-cell moment
- * sums in binary64); precision = 64 holds everything in binary64.  The decision
- * quantities of the acceptance test are evaluated with a fixed operation order
- * (fused multiply-adds included) in the state precision.
+ * Precision: precision = 32 holds particle state in binary32, precision = 64 in
+ * binary64.  The decision quantities of the acceptance test are evaluated with a
+ * fixed operation order (fused multiply-adds included) in the state precision.
+ * Per-c-bin moment sums are exact 64-bit integer sums of every particle's
+ * contribution rounded once to a grid of 2^-e (e per instance and field, set
+ * each step from the largest speed so that no sum can overflow; far finer than
+ * binary32 at every size the library accepts), returned as binary64: they do not
+ * depend on the order in which particles are summed, so reruns, and a batched
+ * run against the same instances run alone, give the same bits.
  */
 #ifndef KMC_H
 #define KMC_H
@@ -132,6 +137,9 @@ typedef struct kmc_info {
     int tile_rows;           /* instance 0: y-rows per staged tile (0: searched directly) */
     int stage_cap;           /* candidates a staged tile holds in shared memory */
     double time;             /* instance 0: simulated time since kmc_init or the last kmc_set_state */
+    int n_scan_tiles;        /* tiles of the key scan (kmc_test_hold_scan) */
+    int kernels_per_step;    /* kernels one kmc_step launches per step without moments */
+    int kernels_moments;     /* kernels added per step when moments are wanted */
 } kmc_info;
 
 /* Create a simulation.  pos and vel are n x 3 row-major arrays of float
@@ -152,13 +160,14 @@ KMC_API int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const vo
 KMC_API int kmc_step(kmc_handle* h, int nsteps, int want_moments);
 
 /* Phases of one step, in launch order, for kmc_step_profiled. */
-#define KMC_PHASE_SEARCH 0   /* closest candidate per particle (criteria 1-3) */
-#define KMC_PHASE_MOVE 1     /* pairs, scattering, free flight, walls, next key and histogram */
-#define KMC_PHASE_SCAN 2     /* exclusive scan of the key histogram */
-#define KMC_PHASE_SCATTER 3  /* counting-sort scatter into key order */
-#define KMC_PHASE_MOMENTS 4  /* per-c-bin moment sums of the new state (want_moments only) */
-#define KMC_PHASE_FINALIZE 5 /* derived moments and per-instance totals (want_moments only) */
-#define KMC_NPHASES 6
+#define KMC_PHASE_SEARCH 0   /* closest candidate per particle (criteria 1-3), one thread per particle */
+#define KMC_PHASE_TILE 1     /* the same, one block per c-bin, for grids whose search cells are the c-bins */
+#define KMC_PHASE_MOVE 2     /* pairs, scattering, free flight, walls, next key and histogram */
+#define KMC_PHASE_SCAN 3     /* exclusive scan of the key histogram */
+#define KMC_PHASE_SCATTER 4  /* counting-sort scatter into (key, id) order */
+#define KMC_PHASE_MOMENTS 5  /* per-c-bin moment sums of the new state (want_moments only) */
+#define KMC_PHASE_FINALIZE 6 /* derived moments and per-instance totals (want_moments only) */
+#define KMC_NPHASES 7
 
 /* Same work as kmc_step, launched kernel by kernel (no graph) with a CUDA
  * event recorded on the handle's stream before and after every phase.
@@ -201,6 +210,18 @@ KMC_API int kmc_set_state(kmc_handle* h, const void* pos, const void* vel, int w
  * id order (int32, instance-local keys). */
 KMC_API int kmc_get_cell_keys(kmc_handle* h, int32_t* keys, int where);
 
+/* The sort permutation of the current state (Sect. "Simulation setup": particles
+ * sorted into bins every step): perm[p] = index in the pos/vel arrays of
+ * kmc_init (instance offset + instance-local id) of the particle at sorted
+ * position p.  Sorted order is the search-grid key (instance, then search cell
+ * with x slowest and the last position dimension fastest; a search cell is a
+ * c-bin or, when kmc_info.sub_cells > 1, a subdivision of one), then id: the
+ * particles of a search cell appear in increasing id.  Particles absorbed by a
+ * wall come last, in no particular order; so do the particles of a search cell
+ * holding more than 16384 (their cell is kept together, in no particular order
+ * inside it).  int32[n]; synchronises the stream when where == HOST. */
+KMC_API int kmc_get_perm(kmc_handle* h, int32_t* perm, int where);
+
 /* Requires KMC_FLAG_RECORD.  best: closest candidate (instance-local id) of
  * each particle in the last step, -1 if none; partner: collision partner of the
  * last step (mutually closest), -1 if none.  Either pointer may be NULL. */
@@ -224,6 +245,17 @@ KMC_API int kmc_get_partners(kmc_handle* h, int32_t* best, int32_t* partner, int
 KMC_API int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, const void* vel, int where,
                          int trial_steps, kmc_config* best, double* ms_per_step);
 
+/* Test hook of the failure detection (the paper has no counterpart).  The only
+ * device-side wait of a step is the key scan's look-back on a predecessor
+ * tile's status word, bounded by a poll cap (2^22 by default).  This call
+ * lowers the cap to spin_cap >= 1 polls and, for tile >= 0 (a tile of the
+ * handle's scan, kmc_info.n_scan_tiles), makes that tile withhold its status
+ * in every following scan, so that the tiles after it run out of polls, give
+ * up and return.  The step then completes with a wrong sort, and the next
+ * synchronising call returns KMC_ETIMEOUT; kmc_set_state (or kmc_init) clears
+ * the hold, the cap and the error.  tile = -1 only sets the cap.  Synchronises. */
+KMC_API int kmc_test_hold_scan(kmc_handle* h, int tile, uint32_t spin_cap);
+
 /* Closest-candidate search without any allocation.  The paper has no
  * counterpart: this entry point exists for callers that may not allocate
  * device memory themselves or through this library, e.g. a host framework
@@ -234,8 +266,11 @@ KMC_API int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, cons
  * kmc_init handle, writing best[id] = instance-local id of the candidate or -1.
  *
  * cfg: single instance only (n_instances <= 1; lambda/sigma, dt, box, cells,
- * walls, precision used; sub_cells > 0 selects the search subdivision, 0 means
- * plain c-bins; stream as in kmc_init, NULL = legacy default stream).
+ * walls, precision and KMC_FLAG_ADAPTIVE_DT / KMC_FLAG_VELOCITY_2D used as
+ * kmc_init uses them, other flags accepted and without effect; sub_cells > 0
+ * selects the search subdivision, 0 means plain c-bins (the results are the
+ * same either way); stream as in kmc_init, NULL = legacy default stream).
+ * The configuration is checked as kmc_init checks it.
  * pos, vel: device arrays n x 3 of float/double per cfg.precision; best:
  * device int32[n].  All scratch (packed state, keys, histogram, scan tiles)
  * lives in one file-scope __device__ array of KMC_STATIC_SCRATCH_BYTES that
@@ -247,7 +282,9 @@ KMC_API int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, cons
  * contents: calls whose work overlaps on the GPU race, so issue them in order
  * on one stream.  Asynchronous on the stream; returns KMC_EINVAL / KMC_ERANGE /
  * KMC_ECUDA for argument, size or launch errors.  Validity of the particles is
- * not checked (unlike kmc_init). */
+ * not checked (unlike kmc_init), and failures detected on the device (the
+ * scan's bounded wait giving up) are not reported: such a call returns KMC_OK
+ * with unreliable best[]. */
 #define KMC_STATIC_MAX_PARTICLES 262144
 #define KMC_STATIC_MAX_CELLS 1048576
 #define KMC_STATIC_SCRATCH_BYTES (48u << 20)

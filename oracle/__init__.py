@@ -2,8 +2,8 @@
 
 Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It wraps ``kmc_oracle.c`` (plain C,
-FP64, optional binary32 decisions) through ctypes and adds the analytic
-references in ``riemann.py``.  It shares no code with the CUDA library.
+FP64, optional binary32 decisions) through ctypes.  It shares no code with the
+CUDA library.  (The exact solutions of the test problems live in ``analytic``.)
 """
 import ctypes
 import os

@@ -6,8 +6,10 @@ behind the C ABI of ``include/kmc.h``.  The names mirror that header
 Host arrays are numpy arrays; device arrays are anything with a
 ``data_ptr()`` (torch tensors), passed with ``where=KMC_WHERE_DEVICE``.
 
-Importing this package loads ``libkmc.so`` and raises if it was not built
-(``python -c "import __graft_entry__ as g; g.build()"``): there is no fallback.
+The library is loaded on the first call into it (or by ``load()``), not at
+import, so that the input generators in ``inputs`` can be used without it; a
+missing ``libkmc.so`` raises ``ImportError`` at that point (build it with
+``python -c "import __graft_entry__ as g; g.build()"``): there is no fallback.
 """
 import ctypes
 import os
@@ -38,13 +40,14 @@ KMC_FLAG_VELOCITY_2D = 32
 KMC_MOM_RAW = 1
 KMC_MOM_DERIVED = 2
 KMC_MOM_GLOBAL = 4
-KMC_NPHASES = 6
-PHASES = ("search", "move", "scan", "scatter", "moments", "finalize")
+KMC_NPHASES = 7
+PHASES = ("search", "tile", "move", "scan", "scatter", "moments", "finalize")
 
 ABI_FUNCTIONS = (
     "kmc_init", "kmc_step", "kmc_moments", "kmc_moments_size", "kmc_free", "kmc_sync",
     "kmc_last_error", "kmc_get_info", "kmc_get_state", "kmc_set_state", "kmc_get_cell_keys",
     "kmc_get_partners", "kmc_step_profiled", "kmc_find_partners_noalloc", "kmc_window_size", "kmc_autotune",
+    "kmc_get_perm", "kmc_test_hold_scan",
 )
 KMC_STATIC_MAX_PARTICLES = 262144
 
@@ -99,6 +102,9 @@ class KmcInfo(ctypes.Structure):
         ("tile_rows", ctypes.c_int),
         ("stage_cap", ctypes.c_int),
         ("time", ctypes.c_double),
+        ("n_scan_tiles", ctypes.c_int),
+        ("kernels_per_step", ctypes.c_int),
+        ("kernels_moments", ctypes.c_int),
     ]
 
 
@@ -140,6 +146,10 @@ def _load():
     L.kmc_get_cell_keys.restype = ctypes.c_int
     L.kmc_get_partners.argtypes = [H, vp, vp, ctypes.c_int]
     L.kmc_get_partners.restype = ctypes.c_int
+    L.kmc_get_perm.argtypes = [H, vp, ctypes.c_int]
+    L.kmc_get_perm.restype = ctypes.c_int
+    L.kmc_test_hold_scan.argtypes = [H, ctypes.c_int, ctypes.c_uint32]
+    L.kmc_test_hold_scan.restype = ctypes.c_int
     L.kmc_step_profiled.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     L.kmc_step_profiled.restype = ctypes.c_int
     L.kmc_window_size.argtypes = [H, ctypes.POINTER(ctypes.c_double)]
@@ -152,7 +162,22 @@ def _load():
     return L
 
 
-lib = _load()
+_lib = None
+
+
+def load():
+    """Load libkmc.so (once) and return the ctypes handle."""
+    global _lib
+    if _lib is None:
+        _lib = _load()
+    return _lib
+
+
+def __getattr__(name):
+    # `lib` is the loaded library, created on first access
+    if name == "lib":
+        return load()
+    raise AttributeError(f"module {__name__!r} has no attribute {name!r}")
 
 
 def _ptr(a):
@@ -174,7 +199,7 @@ def _ptr(a):
 
 def _check(rc, h=None):
     if rc != KMC_OK:
-        msg = lib.kmc_last_error(h)
+        msg = load().kmc_last_error(h)
         raise KmcError(rc, msg.decode() if msg else "")
     return rc
 
@@ -221,22 +246,22 @@ def make_config(dim_pos=3, n_cells=(1, 1, 1), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 
 
 def kmc_init(cfg, n, pos, vel, where=KMC_WHERE_HOST):
     h = ctypes.c_void_p()
-    _check(lib.kmc_init(ctypes.byref(cfg), int(n), _ptr(pos), _ptr(vel), int(where), ctypes.byref(h)))
+    _check(load().kmc_init(ctypes.byref(cfg), int(n), _ptr(pos), _ptr(vel), int(where), ctypes.byref(h)))
     return h
 
 
 def kmc_step(h, nsteps=1, want_moments=1):
-    return _check(lib.kmc_step(h, int(nsteps), int(want_moments)), h)
+    return _check(load().kmc_step(h, int(nsteps), int(want_moments)), h)
 
 
 def kmc_moments(h, out, where=KMC_WHERE_HOST, fields_mask=KMC_MOM_RAW | KMC_MOM_DERIVED | KMC_MOM_GLOBAL):
-    return _check(lib.kmc_moments(h, _ptr(out), int(where), int(fields_mask)), h)
+    return _check(load().kmc_moments(h, _ptr(out), int(where), int(fields_mask)), h)
 
 
 def kmc_step_profiled(h, nsteps=1, want_moments=1):
     """Returns a dict phase -> summed device milliseconds, plus 'total'."""
     ms = (ctypes.c_double * (KMC_NPHASES + 1))()
-    _check(lib.kmc_step_profiled(h, int(nsteps), int(want_moments), ms), h)
+    _check(load().kmc_step_profiled(h, int(nsteps), int(want_moments), ms), h)
     out = {name: ms[i] for i, name in enumerate(PHASES)}
     out["total"] = ms[KMC_NPHASES]
     return out
@@ -245,7 +270,7 @@ def kmc_step_profiled(h, nsteps=1, want_moments=1):
 def kmc_window_size(h):
     """Mean candidates examined per particle by the search of the current state."""
     v = ctypes.c_double()
-    _check(lib.kmc_window_size(h, ctypes.byref(v)), h)
+    _check(load().kmc_window_size(h, ctypes.byref(v)), h)
     return v.value
 
 
@@ -253,7 +278,7 @@ def kmc_find_partners_noalloc(cfg, n, pos, vel, best):
     """Closest candidate of every particle of a device-resident state, with no
     allocation (scratch in the library's fixed device array).  pos, vel, best
     are device arrays; returns the C status code (KMC_OK on success)."""
-    return int(lib.kmc_find_partners_noalloc(ctypes.byref(cfg), int(n), _ptr(pos), _ptr(vel), _ptr(best)))
+    return int(load().kmc_find_partners_noalloc(ctypes.byref(cfg), int(n), _ptr(pos), _ptr(vel), _ptr(best)))
 
 
 def kmc_autotune(cfg, n, pos, vel, where=KMC_WHERE_HOST, trial_steps=3):
@@ -261,7 +286,7 @@ def kmc_autotune(cfg, n, pos, vel, where=KMC_WHERE_HOST, trial_steps=3):
     set-up): returns (config to pass to kmc_init, milliseconds per step)."""
     best = KmcConfig()
     ms = ctypes.c_double()
-    _check(lib.kmc_autotune(ctypes.byref(cfg), int(n), _ptr(pos), _ptr(vel), int(where), int(trial_steps),
+    _check(load().kmc_autotune(ctypes.byref(cfg), int(n), _ptr(pos), _ptr(vel), int(where), int(trial_steps),
                             ctypes.byref(best), ctypes.byref(ms)))
     if hasattr(cfg, "_keep"):
         best._keep = cfg._keep   # the instance array the copy points to
@@ -269,42 +294,51 @@ def kmc_autotune(cfg, n, pos, vel, where=KMC_WHERE_HOST, trial_steps=3):
 
 
 def kmc_moments_size(h, fields_mask):
-    return int(lib.kmc_moments_size(h, int(fields_mask)))
+    return int(load().kmc_moments_size(h, int(fields_mask)))
 
 
 def kmc_free(h):
-    lib.kmc_free(h)
+    load().kmc_free(h)
 
 
 def kmc_sync(h):
-    return _check(lib.kmc_sync(h), h)
+    return _check(load().kmc_sync(h), h)
 
 
 def kmc_last_error(h=None):
-    m = lib.kmc_last_error(h)
+    m = load().kmc_last_error(h)
     return m.decode() if m else ""
 
 
 def kmc_get_info(h):
     info = KmcInfo()
-    _check(lib.kmc_get_info(h, ctypes.byref(info)), h)
+    _check(load().kmc_get_info(h, ctypes.byref(info)), h)
     return info
 
 
 def kmc_get_state(h, pos, vel, where=KMC_WHERE_HOST):
-    return _check(lib.kmc_get_state(h, _ptr(pos), _ptr(vel), int(where)), h)
+    return _check(load().kmc_get_state(h, _ptr(pos), _ptr(vel), int(where)), h)
 
 
 def kmc_set_state(h, pos, vel, where=KMC_WHERE_HOST, step=0):
-    return _check(lib.kmc_set_state(h, _ptr(pos), _ptr(vel), int(where), int(step)), h)
+    return _check(load().kmc_set_state(h, _ptr(pos), _ptr(vel), int(where), int(step)), h)
 
 
 def kmc_get_cell_keys(h, keys, where=KMC_WHERE_HOST):
-    return _check(lib.kmc_get_cell_keys(h, _ptr(keys), int(where)), h)
+    return _check(load().kmc_get_cell_keys(h, _ptr(keys), int(where)), h)
 
 
 def kmc_get_partners(h, best, partner, where=KMC_WHERE_HOST):
-    return _check(lib.kmc_get_partners(h, _ptr(best), _ptr(partner), int(where)), h)
+    return _check(load().kmc_get_partners(h, _ptr(best), _ptr(partner), int(where)), h)
+
+
+def kmc_get_perm(h, perm, where=KMC_WHERE_HOST):
+    return _check(load().kmc_get_perm(h, _ptr(perm), int(where)), h)
+
+
+def kmc_test_hold_scan(h, tile, spin_cap):
+    """Test hook of the bounded device wait (see include/kmc.h)."""
+    return _check(load().kmc_test_hold_scan(h, int(tile), int(spin_cap)), h)
 
 
 # --------------------------------------------------------- convenience wrapper
@@ -368,6 +402,11 @@ class Simulation:
         k = np.zeros(self.n, dtype=np.int32)
         kmc_get_cell_keys(self.h, k)
         return k
+
+    def perm(self):
+        p = np.zeros(self.n, dtype=np.int32)
+        kmc_get_perm(self.h, p)
+        return p
 
     def partners(self):
         best = np.zeros(self.n, dtype=np.int32)

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+#include <stddef.h>
 #include <string.h>
 
 #include <algorithm>
@@ -45,7 +46,9 @@ struct kmc_handle {
     InstDev* inst_d = nullptr;
     InstDyn* dyn_d = nullptr;
     DevState* st_d = nullptr;
-    double *acc = nullptr, *mom = nullptr, *glob = nullptr;
+    unsigned long long* acc = nullptr;
+    unsigned long long* gacc = nullptr;   // per-instance integer totals (zero between reductions)
+    double *mom = nullptr, *glob = nullptr;
     int32_t *rec_best = nullptr, *rec_partner = nullptr;
     uint32_t n_keys = 0, n_tiles = 0;
     uint32_t id_bits = 32;
@@ -146,6 +149,8 @@ cudaError_t enqueue_step(kmc_handle* h, int want_moments, cudaEvent_t* ev = null
     auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], s) : cudaSuccess; };
     if ((e = mark(KMC_PHASE_SEARCH)) != cudaSuccess) return e;
     if ((e = launch_search<T>(b, s)) != cudaSuccess) return e;
+    if ((e = mark(KMC_PHASE_TILE)) != cudaSuccess) return e;
+    if ((e = launch_tile_search<T>(b, s)) != cudaSuccess) return e;
     if ((e = mark(KMC_PHASE_MOVE)) != cudaSuccess) return e;
     if ((e = launch_move<T>(b, s)) != cudaSuccess) return e;
     if ((e = mark(KMC_PHASE_SCAN)) != cudaSuccess) return e;
@@ -156,13 +161,14 @@ cudaError_t enqueue_step(kmc_handle* h, int want_moments, cudaEvent_t* ev = null
     if ((e = launch_scatter<T>(b, s)) != cudaSuccess) return e;
     if ((e = mark(KMC_PHASE_MOMENTS)) != cudaSuccess) return e;
     if (want_moments) {
-        e = cudaMemsetAsync(h->acc, 0, sizeof(double) * kAccFields * (size_t)h->n_bins, s);
+        e = cudaMemsetAsync(h->acc, 0, sizeof(unsigned long long) * kAccFields * (size_t)h->n_bins, s);
         if (e != cudaSuccess) return e;
         if ((e = launch_moments<T>(b, 1, s)) != cudaSuccess) return e;
     }
     if ((e = mark(KMC_PHASE_FINALIZE)) != cudaSuccess) return e;
     if (want_moments) {
-        if ((e = launch_finalize(h->inst_d, h->dyn_d, h->n_inst, h->geo, h->acc, h->mom, h->glob, h->n_bins, s)) !=
+        if ((e = launch_finalize(h->inst_d, h->dyn_d, h->n_inst, h->geo, h->acc, h->mom, h->glob, h->gacc, h->n_bins,
+                                  s)) !=
             cudaSuccess)
             return e;
     }
@@ -531,9 +537,13 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
     if ((rc = dev_alloc(h, (void**)&h->dyn_d, sizeof(InstDyn) * h->n_inst))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->st_d, sizeof(DevState)))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->bad, sizeof(uint32_t) * 4))) return bail(rc);
-    if ((rc = dev_alloc(h, (void**)&h->acc, sizeof(double) * kAccFields * (size_t)h->n_bins))) return bail(rc);
+    if ((rc = dev_alloc(h, (void**)&h->acc, sizeof(unsigned long long) * kAccFields * (size_t)h->n_bins)))
+        return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->mom, sizeof(double) * 16 * (size_t)h->n_bins))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->glob, sizeof(double) * 8 * (size_t)h->n_inst))) return bail(rc);
+    if ((rc = dev_alloc(h, (void**)&h->gacc, sizeof(unsigned long long) * 8 * (size_t)h->n_inst))) return bail(rc);
+    if (cudaMemsetAsync(h->gacc, 0, sizeof(unsigned long long) * 8 * (size_t)h->n_inst, h->stream) != cudaSuccess)
+        return bail(fail(h, KMC_ECUDA, "memset of the moment totals failed"));
     if (cfg->flags & KMC_FLAG_RECORD) {
         if ((rc = dev_alloc(h, (void**)&h->rec_best, nv * sizeof(int32_t)))) return bail(rc);
         if ((rc = dev_alloc(h, (void**)&h->rec_partner, nv * sizeof(int32_t)))) return bail(rc);
@@ -720,11 +730,13 @@ int kmc_moments(kmc_handle* h, double* out, int where, int mask) {
     if (where != KMC_WHERE_HOST && where != KMC_WHERE_DEVICE) return fail(h, KMC_EINVAL, "bad where");
     if (mask & ~(KMC_MOM_RAW | KMC_MOM_DERIVED | KMC_MOM_GLOBAL)) return fail(h, KMC_EINVAL, "bad fields_mask");
     if (!h->mom_state) {
-        KMC_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(double) * kAccFields * (size_t)h->n_bins, h->stream));
+        KMC_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(unsigned long long) * kAccFields * (size_t)h->n_bins,
+                                    h->stream));
         cudaError_t e = h->precision == 64 ? launch_moments<double>(make_bufs<double>(h), 0, h->stream)
                                            : launch_moments<float>(make_bufs<float>(h), 0, h->stream);
         KMC_CUDA(h, e);
-        KMC_CUDA(h, launch_finalize(h->inst_d, h->dyn_d, h->n_inst, h->geo, h->acc, h->mom, h->glob, h->n_bins, h->stream));
+        KMC_CUDA(h, launch_finalize(h->inst_d, h->dyn_d, h->n_inst, h->geo, h->acc, h->mom, h->glob, h->gacc,
+                                    h->n_bins, h->stream));
         h->mom_state = 1;
     }
     const cudaMemcpyKind kind = where == KMC_WHERE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
@@ -847,6 +859,11 @@ int kmc_get_info(kmc_handle* h, kmc_info* info) {
     info->stage_tiles = h->n_stage_tiles;
     info->tile_rows = I.staged ? I.tile_rows : 0;
     info->stage_cap = h->stage_cap;
+    info->n_scan_tiles = (int)h->n_tiles;
+    // search (always), tile search, staged search, move, scan, two scatter passes,
+    // then moments and two finalize kernels when moments are wanted
+    info->kernels_per_step = 1 + (h->any_tiled ? 1 : 0) + (h->n_stage_tiles > 0 ? 1 : 0) + 4;
+    info->kernels_moments = 3;
     return KMC_OK;
 }
 
@@ -912,6 +929,36 @@ int kmc_get_cell_keys(kmc_handle* h, int32_t* keys, int where) {
         KMC_CUDA(h, cudaMemcpyAsync(keys, dst, sizeof(int32_t) * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream));
         return check_device_error(h);
     }
+    return KMC_OK;
+}
+
+int kmc_get_perm(kmc_handle* h, int32_t* perm, int where) {
+    if (!h || !perm) return fail(h, KMC_EINVAL, "NULL argument");
+    if (where != KMC_WHERE_HOST && where != KMC_WHERE_DEVICE) return fail(h, KMC_EINVAL, "bad where");
+    if (h->n == 0) return KMC_OK;
+    int32_t* dst = where == KMC_WHERE_DEVICE ? perm : (int32_t*)h->key;  // key[] is free between steps
+    cudaError_t e = h->precision == 64 ? launch_perm<double>(make_bufs<double>(h), dst, h->stream)
+                                       : launch_perm<float>(make_bufs<float>(h), dst, h->stream);
+    KMC_CUDA(h, e);
+    if (where == KMC_WHERE_HOST) {
+        KMC_CUDA(h, cudaMemcpyAsync(perm, dst, sizeof(int32_t) * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream));
+        return check_device_error(h);
+    }
+    return KMC_OK;
+}
+
+int kmc_test_hold_scan(kmc_handle* h, int tile, uint32_t spin_cap) {
+    if (!h) return fail(nullptr, KMC_EINVAL, "handle is NULL");
+    if (tile < -1 || (tile >= 0 && (uint32_t)tile >= h->n_tiles))
+        return fail(h, KMC_EINVAL, "tile must be -1 or a scan tile of the handle");
+    if (spin_cap < 1) return fail(h, KMC_EINVAL, "spin_cap must be >= 1");
+    // both words in one copy: spin_cap, then hold_tile1
+    const uint32_t w[2] = {spin_cap, (uint32_t)(tile + 1)};
+    static_assert(offsetof(DevState, hold_tile1) == offsetof(DevState, spin_cap) + sizeof(uint32_t),
+                  "spin_cap and hold_tile1 are adjacent");
+    KMC_CUDA(h, cudaMemcpyAsync((char*)h->st_d + offsetof(DevState, spin_cap), w, sizeof(w), cudaMemcpyHostToDevice,
+                                h->stream));
+    KMC_CUDA(h, cudaStreamSynchronize(h->stream));
     return KMC_OK;
 }
 

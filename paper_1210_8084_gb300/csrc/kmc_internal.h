@@ -19,6 +19,7 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr uint32_t kSpinCap = 1u << 22;  // bounded waits: iterations before giving up
 constexpr int kFoldCap = 64;           // wall folds per coordinate per step
 constexpr int kAccFields = 9;          // per c-bin accumulator: 8 moment sums + collided count
+constexpr uint32_t kCanonMax = 16384;  // search cells up to this many particles are put in id order
 
 // device error flags (DevState::error)
 constexpr uint32_t kErrScanTimeout = 1u;
@@ -63,7 +64,7 @@ struct InstDyn {
     double time;                    // simulated time since the state was set
     float dtf;                      // dt rounded to binary32
     int k[3];                       // search half-window in search cells
-    int pad;
+    int mom_e[3];                   // moment sums: fixed-point exponents of v, v^2 and W
 };
 
 struct Geo {
@@ -77,8 +78,10 @@ struct Geo {
 struct DevState {
     uint32_t step;        // Philox counter word 1 of the step being taken
     uint32_t error;       // kErr* bits
-    unsigned long long candidates;  // RECORD mode counters
-    unsigned long long pairs;
+    uint32_t spin_cap;    // bounded waits: polls before giving up (0: kSpinCap)
+    uint32_t hold_tile1;  // test of the bounded wait: scan tile hold_tile1 - 1 never publishes its
+                          // status (0: none); set only through kmc_debug_hold_scan
+    unsigned long long pad;
 };
 
 template <typename T>
@@ -108,7 +111,8 @@ struct Bufs {
     V* posA; V* velA;        // sorted state (search-grid key order)
     V* posB; V* velB;        // staging / unsorted end-of-step state
     unsigned long long* bkey;  // [n] partner key of A[p] (tag of the closest candidate, kNoPartner)
-    uint32_t* slot_of;       // [n] by global id: sorted position in A (written by the search)
+    uint32_t* slot_of;       // [n] by global id: sorted position in A (written by the search);
+                             // the scatter reuses it for the tags of shared search cells
     uint32_t* key;           // [n] search key of B
     uint32_t* slot;          // [n] rank of B[p] within its search cell
     uint32_t* count;         // [n_keys + 1] histogram (zero outside the step)
@@ -116,7 +120,7 @@ struct Bufs {
     unsigned long long* scan_status;  // [1 + n_tiles]: ticket + tile descriptors
     uint32_t n_keys;
     uint32_t n_tiles;
-    double* acc;             // [n_bins * kAccFields] moment sums
+    unsigned long long* acc; // [n_bins * kAccFields] moment sums, fixed point (two's complement)
     double* mom;             // [n_bins * 16] raw + derived
     double* glob;            // [n_inst * 8]
     int64_t n_bins;
@@ -142,7 +146,9 @@ cudaError_t launch_pack(const Bufs<T>& b, const T* pos3, const T* vel3, uint32_t
 template <typename T>
 cudaError_t launch_bin_init(const Bufs<T>& b, cudaStream_t s);
 template <typename T>
-cudaError_t launch_search(const Bufs<T>& b, cudaStream_t s);
+cudaError_t launch_search(const Bufs<T>& b, cudaStream_t s);       // staged + per-particle search
+template <typename T>
+cudaError_t launch_tile_search(const Bufs<T>& b, cudaStream_t s);  // one block per c-bin (tiled instances)
 template <typename T>
 cudaError_t prepare_staged(const Bufs<T>& b);
 template <typename T>
@@ -160,13 +166,17 @@ cudaError_t launch_moments(const Bufs<T>& b, int use_virial, cudaStream_t s);
 template <typename T>
 cudaError_t launch_window_count(const Bufs<T>& b, unsigned long long* total, cudaStream_t s);
 template <typename T>
+cudaError_t launch_perm(const Bufs<T>& b, int32_t* perm, cudaStream_t s);
+template <typename T>
 cudaError_t launch_cbin_hist(const Bufs<T>& b, uint32_t* hist, unsigned long long* vmax2, cudaStream_t s);
 
 // precision-independent
 cudaError_t launch_scan(uint32_t* count, uint32_t* start, uint32_t n_keys, uint32_t n_tiles,
                         unsigned long long* status, InstDyn* dyn, const InstDev* inst,
                         int n_inst, DevState* st, Geo geo, int bump_step, cudaStream_t s);
-cudaError_t launch_finalize(const InstDev* inst, const InstDyn* dyn, int n_inst, Geo geo, const double* acc,
-                            double* mom, double* glob, int64_t n_bins, cudaStream_t s);
+// gacc: [n_inst * 8] integer totals, zero between calls (the launch leaves it zero)
+cudaError_t launch_finalize(const InstDev* inst, const InstDyn* dyn, int n_inst, Geo geo,
+                            const unsigned long long* acc, double* mom, double* glob, unsigned long long* gacc,
+                            int64_t n_bins, cudaStream_t s);
 
 }  // namespace kmc

@@ -263,33 +263,47 @@ __device__ __forceinline__ void warp_vmax(InstDyn* dyn, bool valid, int inst, T 
     }
 }
 
-// Moment sums per c-bin, aggregated in three levels so that few binary64
-// atomics reach any one bin: lanes with the same bin are reduced with warp
-// shuffles; each warp group's totals go to a shared-memory slot list; after a
-// block barrier the first slot of every distinct bin adds up its duplicates and
-// issues the global atomics.  All threads of the block must call this; a lane
-// contributes its partial sums (v, v^2, W), particle count and collided count.
-template <typename T>
+// Moment sums per c-bin in fixed point.  Every particle's contribution (v,
+// v^2, W) is rounded once to an integer multiple of 2^-e, with e chosen per
+// instance and field so that the sum over all of the instance's particles
+// stays below 2^62 in magnitude (step bookkeeping in kmc_scan.cu); the sums
+// are then exact 64-bit integer sums, so they do not depend on the order in
+// which particles are visited or on how they are grouped into threads, warps
+// and blocks: reruns, batched and plain runs give the same bits.  Aggregation
+// has three levels so that few atomics reach any one bin: lanes with the same
+// bin are reduced with warp shuffles; each warp group's totals go to a
+// shared-memory slot list; after a block barrier the first slot of every
+// distinct bin adds up its duplicates and issues the global atomics.  All
+// threads of the block must call this; a lane contributes its partial sums
+// (v, v^2, W), particle count and collided count.
 struct MomentSlots {
     uint32_t bin[kThreads];
-    T f[7][kThreads];
+    long long f[7][kThreads];
     int cnt[kThreads];
     int coll[kThreads];
     int n;
 };
 
-template <typename T>
-__device__ __forceinline__ void block_moment_partials(MomentSlots<T>& S, double* acc, bool valid, uint32_t bin,
-                                                      const T fl[7], int cnt_l, int coll_l) {
+__device__ __forceinline__ float pow2_of(int e, float) { return __int_as_float((127 + e) << 23); }
+__device__ __forceinline__ double pow2_of(int e, double) {
+    return __longlong_as_double((long long)(1023 + e) << 52);
+}
+// x 2^e rounded to the nearest integer (2^e scales exactly; |x 2^e| < 2^62 by the choice of e)
+__device__ __forceinline__ long long fixed_of(float x, float scale) { return __float2ll_rn(x * scale); }
+__device__ __forceinline__ long long fixed_of(double x, double scale) { return __double2ll_rn(x * scale); }
+
+__device__ __forceinline__ void block_moment_partials(MomentSlots& S, unsigned long long* acc, bool valid,
+                                                      uint32_t bin, const long long fl[7], int cnt_l,
+                                                      int coll_l) {
     unsigned todo = __ballot_sync(kFull, valid);
     while (todo) {
         const int leader = __ffs(todo) - 1;
         const uint32_t gb = __shfl_sync(kFull, bin, leader);
         const bool mine = valid && bin == gb;
         const unsigned grp = __ballot_sync(kFull, mine);
-        T f[7];
+        long long f[7];
 #pragma unroll
-        for (int k = 0; k < 7; ++k) f[k] = mine ? fl[k] : (T)0;
+        for (int k = 0; k < 7; ++k) f[k] = mine ? fl[k] : 0ll;
         int c = mine ? cnt_l : 0, cc = mine ? coll_l : 0;
         if (grp != (1u << leader)) {
 #pragma unroll
@@ -318,20 +332,21 @@ __device__ __forceinline__ void block_moment_partials(MomentSlots<T>& S, double*
         for (int u = 0; u < t; ++u)
             if (S.bin[u] == mb) { first = false; break; }
         if (!first) continue;
-        double tot[7] = {0, 0, 0, 0, 0, 0, 0};
-        int c = 0, cc = 0;
+        long long tot[7] = {0, 0, 0, 0, 0, 0, 0};
+        long long c = 0, cc = 0;
         for (int u = t; u < ns; ++u) {
             if (S.bin[u] != mb) continue;
 #pragma unroll
-            for (int k = 0; k < 7; ++k) tot[k] += (double)S.f[k][u];
+            for (int k = 0; k < 7; ++k) tot[k] += S.f[k][u];
             c += S.cnt[u];
             cc += S.coll[u];
         }
-        double* a = acc + (size_t)mb * kAccFields;
-        atomicAdd(a + 0, (double)c);
+        unsigned long long* a = acc + (size_t)mb * kAccFields;
+        atomicAdd(a + 0, (unsigned long long)c);
 #pragma unroll
-        for (int k = 0; k < 7; ++k) atomicAdd(a + 1 + k, tot[k]);
-        if (cc) atomicAdd(a + 8, (double)cc);
+        for (int k = 0; k < 7; ++k)
+            if (tot[k]) atomicAdd(a + 1 + k, (unsigned long long)tot[k]);
+        if (cc) atomicAdd(a + 8, (unsigned long long)cc);
     }
 }
 
@@ -1082,14 +1097,8 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
                     if (poca_test_sh<float, DIM, false, SH>(G, xi, vi, xj, vj, sh, dt, R2, d2))
                         take(d2, reinterpret_cast<const uint32_t*>(pT + k)[s], q);
                 };
-                // criteria 1-2 of one component after the paired part; then the
-                // real-root test and d^2 in scalar form, in poca_test_sh's order
-                auto rest = [&](float r0, float r1, float r2c, float a, float bb, uint32_t idj, int32_t q) {
-                    float rr = R<float>::mul(r0, r0);
-                    rr = R<float>::fma(r1, r1, rr);
-                    if (DIM == 3) rr = R<float>::fma(r2c, r2c, rr);
-                    const float disc = R<float>::fma(a, a, -R<float>::mul(bb, R<float>::sub(rr, R2)));
-                    if (!(disc >= 0.f)) return;
+                // d^2 of a candidate that passed criteria 1-2, in poca_test_sh's order
+                auto close = [&](float rr, float a, float bb, uint32_t idj, int32_t q) {
                     take(R<float>::sub(rr, R<float>::div(R<float>::mul(a, a), bb)), idj, q);
                 };
                 const float2 xi0 = make_float2(xi[0], xi[0]), xi1 = make_float2(xi[1], xi[1]);
@@ -1099,8 +1108,15 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
                 const float2 sh0 = make_float2(sh[0], sh[0]), sh1 = make_float2(sh[1], sh[1]);
                 const float2 sh2 = make_float2(sh[2], sh[2]);
                 const float2 dt2 = make_float2(dt, dt);
+                const float2 mR2 = make_float2(-R2, -R2);   // r2 - R^2 as r2 + (-R^2): the same rounding
                 int e = e0;
                 if ((e - c0) & 1) one(e++);
+                // Both candidates go through the whole test in paired form, the
+                // real-root test included, so that no lane branches off for
+                // criterion 2: only a candidate that passes all of criteria 1-2
+                // (about one test in a thousand) leaves the paired path, for d^2.
+                // b > 0 needs no test of its own: a < 0 and fma(b, dt, a) > 0
+                // give b dt > -a > 0 exactly (the rounding keeps the sign).
 #pragma unroll 2
                 for (; e + 1 < e1; e += 2) {
                     const int k = (e - c0) >> 1;
@@ -1120,19 +1136,24 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
                     a = __ffma2_rn(d1, u1, a);
                     float2 bb = __fmul2_rn(u0, u0);
                     bb = __ffma2_rn(u1, u1, bb);
+                    float2 rr = __fmul2_rn(d0, d0);
+                    rr = __ffma2_rn(d1, d1, rr);
                     if (DIM == 3) {
                         const float2 u2 = __fadd2_rn(vi2, make_float2(C.z, C.w));
                         a = __ffma2_rn(d2v, u2, a);
                         bb = __ffma2_rn(u2, u2, bb);
+                        rr = __ffma2_rn(d2v, d2v, rr);
                     }
                     const float2 f = __ffma2_rn(bb, dt2, a);
+                    const float2 y = __fmul2_rn(bb, __fadd2_rn(rr, mR2));
+                    const float2 disc = __ffma2_rn(a, a, make_float2(-y.x, -y.y));
                     const int32_t q = qoff + e;
-                    const bool ok0 = (!CHK || q > lim) && bb.x > 0.f && a.x < 0.f && f.x > 0.f;
-                    const bool ok1 = (!CHK || q + 1 > lim) && bb.y > 0.f && a.y < 0.f && f.y > 0.f;
+                    const bool ok0 = (!CHK || q > lim) && a.x < 0.f && f.x > 0.f && disc.x >= 0.f;
+                    const bool ok1 = (!CHK || q + 1 > lim) && a.y < 0.f && f.y > 0.f && disc.y >= 0.f;
                     if (ok0 || ok1) {
                         const uint2 tg = pT[k];
-                        if (ok0) rest(d0.x, d1.x, d2v.x, a.x, bb.x, tg.x, q);
-                        if (ok1) rest(d0.y, d1.y, d2v.y, a.y, bb.y, tg.y, q + 1);
+                        if (ok0) close(rr.x, a.x, bb.x, tg.x, q);
+                        if (ok1) close(rr.y, a.y, bb.y, tg.y, q + 1);
                     }
                 }
                 if (e < e1) one(e);
@@ -1653,7 +1674,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 1) move_kernel(
     V Pj = {}, Qj = {};
     if (kp != kNoPartner) {
         tagj = (uint32_t)kp;
-        j = b.slot_of[I.p_off + (int64_t)tag_id(b, tagj)];
+        const int64_t lid = (int64_t)tag_id(b, tagj);
+        // A candidate of another instance, or a position outside A, comes only
+        // from a step whose sort failed (flagged as KMC_ETIMEOUT): slot_of then
+        // still holds the scatter's tags for some ids.  Both are skipped.
+        if (tag_inst(b, tagj) == inst && lid < I.n) {
+            j = b.slot_of[I.p_off + lid];
+            if (j >= b.n) j = -1;
+        }
+    }
+    if (j >= 0) {
         // the candidate's key and state in one round trip; the state is used if the pair is mutual
         const unsigned long long kj = b.bkey[j];
         Pj = b.posA[j];
@@ -1755,12 +1785,45 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 1) move_kernel(
     warp_vmax<T>(b.dyn, valid && !gone, inst, speed2<T>(vn[0], vn[1], vn[2]));
 }
 
-// Counting-sort scatter B -> A in search-key order.
+// Counting-sort scatter B -> A in canonical order: search key, then particle
+// tag (instance, then id) inside a search cell.  The histogram atomics of the
+// move kernel gave every particle an arbitrary rank inside its cell (slot);
+// pass 1 writes the tag of every particle that shares its cell at that rank,
+// pass 2 counts the cell's tags below its own, which is its rank in id order,
+// and moves the particle there.  A cell of more than kCanonMax particles keeps
+// the atomic order (the count is quadratic in the cell's size), and so do the
+// absorbed particles collected after the last cell.  The tags go to slot_of,
+// which is free between the move and the next search.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) scatter_tags_kernel(Bufs<T> b) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= b.n) return;
+    const uint32_t k = b.key[p];
+    if (k >= b.n_keys) return;
+    const uint32_t s0 = b.start[k], s1 = b.start[k + 1];
+    if (s1 <= s0 + 1u || s1 - s0 > kCanonMax) return;
+    const uint32_t dst = s0 + b.slot[p];
+    if (dst >= s1 || dst >= (uint32_t)b.n) return;   // only after a failed scan (flagged by the scatter)
+    b.slot_of[dst] = R<T>::bits(b.posB[p].w);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) scatter_kernel(Bufs<T> b) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= b.n) return;
-    const uint32_t dst = b.start[b.key[p]] + b.slot[p];
+    const uint32_t k = b.key[p];
+    const uint32_t s0 = b.start[k];
+    uint32_t rank = b.slot[p];
+    if (k < b.n_keys) {
+        const uint32_t s1 = b.start[k + 1];
+        if (s1 > s0 + 1u && s1 - s0 <= kCanonMax && s1 <= (uint32_t)b.n) {
+            const uint32_t tag = R<T>::bits(b.posB[p].w);
+            uint32_t r = 0;
+            for (uint32_t q = s0; q < s1; ++q) r += b.slot_of[q] < tag ? 1u : 0u;
+            rank = r;
+        }
+    }
+    const uint32_t dst = s0 + rank;
     if (dst >= (uint32_t)b.n) {  // only after a failed scan; reported as a device error
         atomicOr(&b.st->error, kErrKeyRange);
         return;
@@ -1768,6 +1831,16 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(Bufs<T> b) {
     b.posA[dst] = b.posB[p];
     b.velA[dst] = b.velB[p];
     b.bkey[dst] = kNoPartner;   // the next search starts from no partner
+}
+
+// Index (position in the input arrays, p_off + local id) of every particle of
+// A, in sorted order: the sort permutation.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) perm_kernel(Bufs<T> b, int32_t* __restrict__ perm) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= b.n) return;
+    const uint32_t tag = R<T>::bits(b.posA[p].w);
+    perm[p] = (int32_t)(b.inst[tag_inst(b, tag)].p_off + (int64_t)tag_id(b, tag));
 }
 
 // State of A in id order.
@@ -1814,15 +1887,15 @@ __global__ void __launch_bounds__(kThreads) cellkey_kernel(Bufs<T> b, int32_t* _
 }
 
 // Moment sums per c-bin of the sorted state A (Eqs. vel_b, stress, 18, 19):
-// N, Sum v, Sum v^2, Sum W and the collided count.  Each thread reduces
-// kMomItems consecutive particles (consecutive particles of A share a c-bin
-// almost always), then warp and block aggregation as in block_moments.
-// use_virial = 0 ignores vel.w (state not produced by a step).
+// N, Sum v, Sum v^2, Sum W and the collided count, in fixed point (see
+// block_moment_partials).  Each thread reduces kMomItems consecutive particles
+// (consecutive particles of A share a c-bin almost always), then warp and
+// block aggregation.  use_virial = 0 ignores vel.w (state not produced by a step).
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kThreads) moments_kernel(Bufs<T> b, int use_virial) {
     using V = typename Vec4<T>::type;
     __shared__ GeoT<T> G;
-    __shared__ MomentSlots<T> S;
+    __shared__ MomentSlots S;
     if (threadIdx.x == 0) {
         G.load(b.geo);
         S.n = 0;
@@ -1830,7 +1903,7 @@ __global__ void __launch_bounds__(kThreads) moments_kernel(Bufs<T> b, int use_vi
     __syncthreads();
     const int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kMomItems;
     uint32_t cur = 0xffffffffu;
-    T f[7] = {0, 0, 0, 0, 0, 0, 0};
+    long long f[7] = {0, 0, 0, 0, 0, 0, 0};
     int cnt = 0, coll = 0;
     V Ps[kMomItems], Qs[kMomItems];   // all loads in flight before the sums
 #pragma unroll
@@ -1840,6 +1913,8 @@ __global__ void __launch_bounds__(kThreads) moments_kernel(Bufs<T> b, int use_vi
             Qs[k] = b.velA[base + k];
         }
     }
+    int inst_c = -1;
+    T sv = (T)0, s2 = (T)0, sw = (T)0;   // 2^e of the instance's three fields
 #pragma unroll
     for (int k = 0; k < kMomItems; ++k) {
         const int64_t p = base + k;
@@ -1849,28 +1924,34 @@ __global__ void __launch_bounds__(kThreads) moments_kernel(Bufs<T> b, int use_vi
         if (absorbed(Q.w)) continue;   // left through an absorbing wall
         const int inst = tag_inst(b, R<T>::bits(P.w));
         const InstDev& I = b.inst[inst];
+        if (inst != inst_c) {
+            inst_c = inst;
+            sv = pow2_of(b.dyn[inst].mom_e[0], T());
+            s2 = pow2_of(b.dyn[inst].mom_e[1], T());
+            sw = pow2_of(b.dyn[inst].mom_e[2], T());
+        }
         const T x[3] = {P.x, P.y, P.z};
         uint32_t skey, bin;
         keys_of<T, DIM>(G, I, x, skey, bin);
         if (bin != cur && cnt > 0) {   // rare: the thread's particles span two bins
-            double* a = b.acc + (size_t)cur * kAccFields;
-            atomicAdd(a + 0, (double)cnt);
+            unsigned long long* a = b.acc + (size_t)cur * kAccFields;
+            atomicAdd(a + 0, (unsigned long long)cnt);
 #pragma unroll
-            for (int q = 0; q < 7; ++q) atomicAdd(a + 1 + q, (double)f[q]);
-            if (coll) atomicAdd(a + 8, (double)coll);
+            for (int q = 0; q < 7; ++q) atomicAdd(a + 1 + q, (unsigned long long)f[q]);
+            if (coll) atomicAdd(a + 8, (unsigned long long)coll);
 #pragma unroll
-            for (int q = 0; q < 7; ++q) f[q] = (T)0;
+            for (int q = 0; q < 7; ++q) f[q] = 0ll;
             cnt = coll = 0;
         }
         cur = bin;
         const bool collided = use_virial && Q.w != R<T>::inf();
-        f[0] += Q.x; f[1] += Q.y; f[2] += Q.z;
-        f[3] += Q.x * Q.x; f[4] += Q.y * Q.y; f[5] += Q.z * Q.z;
-        if (collided) f[6] += Q.w;
+        f[0] += fixed_of(Q.x, sv); f[1] += fixed_of(Q.y, sv); f[2] += fixed_of(Q.z, sv);
+        f[3] += fixed_of(Q.x * Q.x, s2); f[4] += fixed_of(Q.y * Q.y, s2); f[5] += fixed_of(Q.z * Q.z, s2);
+        if (collided) f[6] += fixed_of(Q.w, sw);
         cnt += 1;
         coll += collided ? 1 : 0;
     }
-    block_moment_partials<T>(S, b.acc, cnt > 0, cur, f, cnt, coll);
+    block_moment_partials(S, b.acc, cnt > 0, cur, f, cnt, coll);
 }
 
 // Candidates each particle of A examines (the sizes of its search window), summed
@@ -2000,10 +2081,14 @@ cudaError_t launch_search(const Bufs<T>& b, cudaStream_t s) {
     }
     // always launched: besides the direct search it records slot_of for every particle
     KMC_DIM_DISPATCH(b.geo.dim, search_kernel, b);
-    if (b.any_tiled && b.n_keys > 0) {
-        if (b.geo.dim == 3) tile_search_kernel<T, 3><<<b.n_keys, kTileThreads, 0, s>>>(b);
-        else tile_search_kernel<T, 2><<<b.n_keys, kTileThreads, 0, s>>>(b);
-    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_tile_search(const Bufs<T>& b, cudaStream_t s) {
+    if (b.n == 0 || !b.any_tiled || b.n_keys == 0) return cudaSuccess;
+    if (b.geo.dim == 3) tile_search_kernel<T, 3><<<b.n_keys, kTileThreads, 0, s>>>(b);
+    else tile_search_kernel<T, 2><<<b.n_keys, kTileThreads, 0, s>>>(b);
     return cudaGetLastError();
 }
 
@@ -2023,7 +2108,15 @@ cudaError_t launch_move(const Bufs<T>& b, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_scatter(const Bufs<T>& b, cudaStream_t s) {
     if (b.n == 0) return cudaSuccess;
+    scatter_tags_kernel<T><<<blocks_for(b.n), kThreads, 0, s>>>(b);
     scatter_kernel<T><<<blocks_for(b.n), kThreads, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_perm(const Bufs<T>& b, int32_t* perm, cudaStream_t s) {
+    if (b.n == 0) return cudaSuccess;
+    perm_kernel<T><<<blocks_for(b.n), kThreads, 0, s>>>(b, perm);
     return cudaGetLastError();
 }
 
@@ -2069,6 +2162,7 @@ cudaError_t launch_window_count(const Bufs<T>& b, unsigned long long* total, cud
     template cudaError_t launch_pack<T>(const Bufs<T>&, const T*, const T*, uint32_t*, cudaStream_t); \
     template cudaError_t launch_bin_init<T>(const Bufs<T>&, cudaStream_t);                         \
     template cudaError_t launch_search<T>(const Bufs<T>&, cudaStream_t);                           \
+    template cudaError_t launch_tile_search<T>(const Bufs<T>&, cudaStream_t);                      \
     template cudaError_t prepare_staged<T>(const Bufs<T>&);                                        \
     template size_t stage_smem_bytes<T>(const Bufs<T>&);                                           \
     template cudaError_t launch_move<T>(const Bufs<T>&, cudaStream_t);                             \
@@ -2077,6 +2171,7 @@ cudaError_t launch_window_count(const Bufs<T>& b, unsigned long long* total, cud
     template cudaError_t launch_cell_keys<T>(const Bufs<T>&, int32_t*, cudaStream_t);              \
     template cudaError_t launch_moments<T>(const Bufs<T>&, int, cudaStream_t);                     \
     template cudaError_t launch_cbin_hist<T>(const Bufs<T>&, uint32_t*, unsigned long long*, cudaStream_t); \
-    template cudaError_t launch_window_count<T>(const Bufs<T>&, unsigned long long*, cudaStream_t);
+    template cudaError_t launch_window_count<T>(const Bufs<T>&, unsigned long long*, cudaStream_t);   \
+    template cudaError_t launch_perm<T>(const Bufs<T>&, int32_t*, cudaStream_t);
 
 }  // namespace kmc

@@ -52,6 +52,10 @@ __device__ __forceinline__ uint32_t tag_of(double w) {
     return (uint32_t)(unsigned long long)__double_as_longlong(w);
 }
 
+// The instance table, passed by value (kernel parameters live with the launch,
+// so no host buffer has to outlive the call).
+__global__ void put_instance(InstDev* dst, InstDev I) { *dst = I; }
+
 // Closest candidate per particle (its tag is the low half of the partner
 // key; one instance, so tag = id), by id.
 template <typename T>
@@ -93,6 +97,10 @@ int run(const kmc_config* cfg, int64_t n, const void* pos, const void* vel, int3
     I.dtf = (float)I.dt;
     I.seed_lo = (uint32_t)(cfg->seed & 0xffffffffu);
     I.seed_hi = (uint32_t)(cfg->seed >> 32);
+    // adaptive timestep as a handle's first step takes it (set by the scan's step bookkeeping)
+    I.adaptive = (cfg->flags & KMC_FLAG_ADAPTIVE_DT) ? 1 : 0;
+    I.dx_min = INFINITY;
+    for (int d = 0; d < g.dim; ++d) I.dx_min = fmin(I.dx_min, g.L[d] / g.n[d]);
     uint64_t keys = 1;
     for (int d = 0; d < 3; ++d) {
         I.s[d] = (d < g.dim && cfg->sub_cells[d] > 0) ? cfg->sub_cells[d] : 1;
@@ -138,7 +146,8 @@ int run(const kmc_config* cfg, int64_t n, const void* pos, const void* vel, int3
     b.id_bits = 32;
     b.id_mask = 0xffffffffu;
     // the array keeps the last call's contents: clear what must start at zero
-    if (cudaMemcpyAsync((void*)b.inst, &I, sizeof(InstDev), cudaMemcpyHostToDevice, s) != cudaSuccess) return KMC_ECUDA;
+    put_instance<<<1, 1, 0, s>>>((InstDev*)b.inst, I);
+    if (cudaGetLastError() != cudaSuccess) return KMC_ECUDA;
     if (cudaMemsetAsync(b.st, 0, sizeof(DevState), s) != cudaSuccess) return KMC_ECUDA;
     if (cudaMemsetAsync(b.dyn, 0, sizeof(InstDyn), s) != cudaSuccess) return KMC_ECUDA;
     if (cudaMemsetAsync(bad, 0, sizeof(uint32_t), s) != cudaSuccess) return KMC_ECUDA;
@@ -150,7 +159,7 @@ int run(const kmc_config* cfg, int64_t n, const void* pos, const void* vel, int3
     if (launch_scan(b.count, b.start, n_keys, n_tiles, b.scan_status, b.dyn, b.inst, 1, b.st, g, 0, s) != cudaSuccess)
         return KMC_ECUDA;
     if (launch_scatter<T>(b, s) != cudaSuccess) return KMC_ECUDA;
-    if (launch_search<T>(b, s) != cudaSuccess) return KMC_ECUDA;
+    if (launch_search<T>(b, s) != cudaSuccess) return KMC_ECUDA;   // per particle (no instance is tiled here)
     best_by_id<T><<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(b, best);
     return cudaGetLastError() == cudaSuccess ? KMC_OK : KMC_ECUDA;
 }
@@ -166,11 +175,19 @@ extern "C" KMC_API int kmc_find_partners_noalloc(const kmc_config* cfg, int64_t 
     if (n < 0) return KMC_EINVAL;
     if (n > KMC_STATIC_MAX_PARTICLES) return KMC_ERANGE;
     if (n > 0 && (!pos || !vel || !best)) return KMC_EINVAL;
+    // the checks of kmc_init
     if (!(cfg->dt > 0) || !isfinite(cfg->dt)) return KMC_EINVAL;
     if (!(cfg->sigma > 0) && !(cfg->lambda > 0)) return KMC_EINVAL;
+    if (cfg->sigma > 0 && !isfinite(cfg->sigma)) return KMC_EINVAL;
+    if (cfg->flags & ~(KMC_FLAG_RECORD | KMC_FLAG_NO_GRAPH | KMC_FLAG_STAGED_SEARCH | KMC_FLAG_NO_TILE_SEARCH |
+                       KMC_FLAG_ADAPTIVE_DT | KMC_FLAG_VELOCITY_2D))
+        return KMC_EINVAL;
+    if ((cfg->flags & KMC_FLAG_VELOCITY_2D) && cfg->dim_pos != 2) return KMC_EINVAL;
     for (int d = 0; d < cfg->dim_pos; ++d) {
         if (cfg->n_cells[d] < 1 || !(cfg->hi[d] > cfg->lo[d])) return KMC_EINVAL;
-        if (cfg->bc[d] != KMC_BC_PERIODIC && cfg->bc[d] != KMC_BC_WALL) return KMC_EINVAL;
+        if (!isfinite(cfg->lo[d]) || !isfinite(cfg->hi[d])) return KMC_EINVAL;
+        if (cfg->bc[d] != KMC_BC_PERIODIC && cfg->bc[d] != KMC_BC_WALL && cfg->bc[d] != KMC_BC_ABSORB)
+            return KMC_EINVAL;
         if (cfg->sub_cells[d] < 0) return KMC_EINVAL;
     }
     void* base = nullptr;

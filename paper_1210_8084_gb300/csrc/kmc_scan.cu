@@ -12,7 +12,8 @@
 // k_d = ceil(D' / w_d) with D' = 1.001 (R + 2 v_max dt) + 1e-5 L_d is derived
 // from it.  Any pair that passes the acceptance test is closer than
 // R + |v_rel| t_poca <= R + 2 v_max dt at the start of the step, so the window
-// never drops a candidate of the 3^D c-bin neighbourhood.
+// never drops a candidate of the 3^D c-bin neighbourhood.  The same block sets
+// the fixed-point exponents of the moment sums from the largest speed.
 #include <math.h>
 
 #include "kmc_internal.h"
@@ -26,6 +27,14 @@ constexpr unsigned long long kFlagInc = 2ull << 32;
 
 __device__ __forceinline__ unsigned long long load_status(const unsigned long long* p) {
     return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+// Largest e (within [-120, 120]) with m 2^e < 2^62: a sum of terms bounded by
+// m in total stays inside a signed 64-bit integer with a factor 2 to spare.
+__device__ __forceinline__ int fixed_exponent(double m) {
+    if (!(m > 0.0) || !isfinite(m)) return 0;
+    const int e = 61 - ilogb(m);
+    return e < -120 ? -120 : (e > 120 ? 120 : e);
 }
 
 __device__ void step_bookkeeping(InstDyn* dyn, const InstDev* inst, int n_inst, DevState* st, const Geo& geo,
@@ -56,6 +65,17 @@ __device__ void step_bookkeeping(InstDyn* dyn, const InstDev* inst, int n_inst, 
             if (r < (double)inst[i].M[d]) k = (int)ceil(r);
             dyn[i].k[d] = k < 1 ? 1 : k;
         }
+        // Moment sums (fixed point): over the instance's n particles |v_d| <= v_max,
+        // v_d^2 <= v_max^2, and a collided particle's |W| = |r_ij(t_poca) . dv| <=
+        // R (1 + sqrt 2) v_max (the pair's PoCA distance is at most R, and the
+        // pair's energy bounds the pre-collision speed by sqrt 2 v_max); the
+        // factors 1 + 1e-6 and 4 cover the rounding of |v|^2 and of W.
+        const double nn = (double)(inst[i].n > 0 ? inst[i].n : 1);
+        const double vm = vmax * (1.0 + 1e-6);
+        dyn[i].mom_e[0] = vm > 0.0 ? fixed_exponent(nn * vm) : 120;
+        dyn[i].mom_e[1] = vm > 0.0 ? fixed_exponent(nn * vm * vm) : 120;
+        const double wm = nn * 4.0 * sqrt(inst[i].R2) * vm;
+        dyn[i].mom_e[2] = wm > 0.0 ? fixed_exponent(wm) : 120;
     }
     if (threadIdx.x == 0 && bump) st->step += 1u;
 }
@@ -72,6 +92,9 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(uint32_t* __restrict
     __syncthreads();
     const uint32_t tile = s_tile;
     if (tile == 0) step_bookkeeping(dyn, inst, n_inst, st, geo, bump);
+    // the test of the bounded wait lowers the cap and holds back one tile's status
+    const uint32_t cap = st->spin_cap ? st->spin_cap : kSpinCap;
+    const bool publish = st->hold_tile1 != tile + 1u;
 
     const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     const size_t base = (size_t)tile * kScanTile + (size_t)threadIdx.x * kScanItems;
@@ -111,9 +134,9 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(uint32_t* __restrict
         // decoupled look-back
         uint32_t prefix = 0;
         if (tile == 0) {
-            if (lane == 0) atomicExch(&status[1], kFlagInc | (unsigned long long)aggregate);
+            if (lane == 0 && publish) atomicExch(&status[1], kFlagInc | (unsigned long long)aggregate);
         } else {
-            if (lane == 0) atomicExch(&status[1 + tile], kFlagAgg | (unsigned long long)aggregate);
+            if (lane == 0 && publish) atomicExch(&status[1 + tile], kFlagAgg | (unsigned long long)aggregate);
             long long pred = (long long)tile - 1;
             bool done = false;
             while (!done) {
@@ -124,7 +147,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(uint32_t* __restrict
                     for (;;) {
                         sv = load_status(&status[1 + t]);
                         if ((sv >> 32) != 0ull) break;
-                        if (++spins > kSpinCap) {
+                        if (++spins > cap) {
                             atomicOr(&st->error, kErrScanTimeout);
                             sv = kFlagInc;
                             break;
@@ -148,7 +171,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(uint32_t* __restrict
                 for (int o = 16; o > 0; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
                 prefix += contrib;
             }
-            if (lane == 0) atomicExch(&status[1 + tile], kFlagInc | (unsigned long long)(prefix + aggregate));
+            if (lane == 0 && publish)
+                atomicExch(&status[1 + tile], kFlagInc | (unsigned long long)(prefix + aggregate));
         }
         if (lane == 0) s_prefix = prefix;
     }
@@ -163,63 +187,93 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(uint32_t* __restrict
     }
 }
 
+// Fixed-point sum -> binary64 (exact below 2^53, correctly rounded above).
+__device__ __forceinline__ double unfix(unsigned long long a, int e) { return ldexp((double)(long long)a, -e); }
+
 // Derived per-c-bin moments (Eqs. vel_b, stress, 18, 19 with the readings
-// u = Sum v / N, v_rms^2 = <|v - u|^2>, T = v_rms^2 / 3, p = n T + virial).
-__global__ void finalize_bins_kernel(const InstDev* __restrict__ inst, const InstDyn* __restrict__ dyn, Geo geo,
-                                     const double* __restrict__ acc, double* __restrict__ mom, int64_t n_bins,
-                                     int64_t bins_per_inst) {
+// u = Sum v / N, v_rms^2 = <|v - u|^2>, T = v_rms^2 / 3, p = n T + virial),
+// and the per-instance integer totals of the fixed-point sums (exact, so the
+// order of the atomics does not matter): a warp whose bins belong to one
+// instance reduces with shuffles and adds once.
+__global__ void __launch_bounds__(256) finalize_bins_kernel(const InstDev* __restrict__ inst,
+                                                            const InstDyn* __restrict__ dyn, Geo geo,
+                                                            const unsigned long long* __restrict__ acc,
+                                                            double* __restrict__ mom, unsigned long long* gacc,
+                                                            int64_t n_bins, int64_t bins_per_inst) {
     const int64_t bidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (bidx >= n_bins) return;
-    const double* a = acc + bidx * kAccFields;
-    double* o = mom + bidx * 16;
-    for (int k = 0; k < 8; ++k) o[k] = a[k];
-    double Vc = 1.0;
-    for (int d = 0; d < geo.dim; ++d) Vc *= geo.L[d] / (double)geo.n[d];
-    const double N = a[0];
-    if (N <= 0.0) {
-        for (int k = 8; k < 16; ++k) o[k] = 0.0;
-        return;
+    const bool valid = bidx < n_bins;
+    const int i = valid ? (int)(bidx / bins_per_inst) : 0;
+    unsigned long long t[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (valid) {
+        const InstDyn& D = dyn[i];
+        const unsigned long long* a = acc + bidx * kAccFields;
+        unsigned long long ai[9];
+        for (int k = 0; k < 9; ++k) ai[k] = a[k];
+        t[0] = ai[0];
+        t[1] = ai[4] + ai[5] + ai[6];
+        t[2] = ai[1];
+        t[3] = ai[2];
+        t[4] = ai[3];
+        t[5] = ai[7];
+        t[6] = ai[8];
+        double* o = mom + bidx * 16;
+        double r[8];
+        r[0] = (double)(long long)ai[0];
+        for (int k = 1; k <= 3; ++k) r[k] = unfix(ai[k], D.mom_e[0]);
+        for (int k = 4; k <= 6; ++k) r[k] = unfix(ai[k], D.mom_e[1]);
+        r[7] = unfix(ai[7], D.mom_e[2]);
+        for (int k = 0; k < 8; ++k) o[k] = r[k];
+        double Vc = 1.0;
+        for (int d = 0; d < geo.dim; ++d) Vc *= geo.L[d] / (double)geo.n[d];
+        const double N = r[0];
+        if (N <= 0.0) {
+            for (int k = 8; k < 16; ++k) o[k] = 0.0;
+        } else {
+            const double dt = D.dt_prev;   // the step whose collisions W sums
+            const double ux = r[1] / N, uy = r[2] / N, uz = r[3] / N;
+            const double c2 = (r[4] + r[5] + r[6]) / N - (ux * ux + uy * uy + uz * uz);
+            const double T = c2 / (geo.vdim == 2 ? 2.0 : 3.0);   // f velocity degrees of freedom
+            const double nd = N / Vc;
+            const double pkin = nd * T;
+            const double pvir = r[7] / (2.0 * geo.dim * Vc * dt);
+            o[8] = nd; o[9] = ux; o[10] = uy; o[11] = uz;
+            o[12] = T; o[13] = pkin; o[14] = pvir; o[15] = pkin + pvir;
+        }
     }
-    const double dt = dyn[bidx / bins_per_inst].dt_prev;   // the step whose collisions W sums
-    const double ux = a[1] / N, uy = a[2] / N, uz = a[3] / N;
-    const double c2 = (a[4] + a[5] + a[6]) / N - (ux * ux + uy * uy + uz * uz);
-    const double T = c2 / (geo.vdim == 2 ? 2.0 : 3.0);   // f velocity degrees of freedom
-    const double nd = N / Vc;
-    const double pkin = nd * T;
-    const double pvir = a[7] / (2.0 * geo.dim * Vc * dt);
-    o[8] = nd; o[9] = ux; o[10] = uy; o[11] = uz;
-    o[12] = T; o[13] = pkin; o[14] = pvir; o[15] = pkin + pvir;
+    const int i0 = __shfl_sync(0xffffffffu, i, 0);
+    if (__all_sync(0xffffffffu, !valid || i == i0)) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
+        }
+        if ((threadIdx.x & 31u) == 0 && __shfl_sync(0xffffffffu, (int)valid, 0))
+            for (int k = 0; k < 7; ++k)
+                if (t[k]) atomicAdd(gacc + (size_t)i0 * 8 + k, t[k]);
+    } else if (valid) {
+        for (int k = 0; k < 7; ++k)
+            if (t[k]) atomicAdd(gacc + (size_t)i * 8 + k, t[k]);
+    }
 }
 
-// Per-instance totals (N, energy, momentum, virial, pairs) in a fixed order.
-__global__ void __launch_bounds__(256) finalize_glob_kernel(const double* __restrict__ acc,
-                                                            double* __restrict__ glob, int64_t bins_per_inst) {
-    __shared__ double sh[7][256];
-    const int i = blockIdx.x;
-    double s[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int64_t b = threadIdx.x; b < bins_per_inst; b += blockDim.x) {
-        const double* a = acc + ((int64_t)i * bins_per_inst + b) * kAccFields;
-        s[0] += a[0];
-        s[1] += 0.5 * (a[4] + a[5] + a[6]);
-        s[2] += a[1];
-        s[3] += a[2];
-        s[4] += a[3];
-        s[5] += a[7];
-        s[6] += a[8];
-    }
-    for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] = s[k];
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w)
-            for (int k = 0; k < 7; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        double* g = glob + (int64_t)i * 8;
-        for (int k = 0; k < 6; ++k) g[k] = sh[k][0];
-        g[6] = 0.5 * sh[6][0];  // collided particles / 2 = pairs
-        g[7] = 0.0;
-    }
+// Per-instance totals (N, energy, momentum, virial, pairs) from the integer
+// totals, converted once; the totals are cleared for the next reduction.
+__global__ void finalize_glob_kernel(const InstDyn* __restrict__ dyn, unsigned long long* gacc,
+                                     double* __restrict__ glob, int n_inst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_inst) return;
+    const InstDyn& D = dyn[i];
+    unsigned long long* t = gacc + (size_t)i * 8;
+    double* g = glob + (int64_t)i * 8;
+    g[0] = (double)(long long)t[0];
+    g[1] = 0.5 * unfix(t[1], D.mom_e[1]);
+    g[2] = unfix(t[2], D.mom_e[0]);
+    g[3] = unfix(t[3], D.mom_e[0]);
+    g[4] = unfix(t[4], D.mom_e[0]);
+    g[5] = unfix(t[5], D.mom_e[2]);
+    g[6] = 0.5 * (double)(long long)t[6];  // collided particles / 2 = pairs
+    g[7] = 0.0;
+    for (int k = 0; k < 8; ++k) t[k] = 0ull;
 }
 
 }  // namespace
@@ -234,12 +288,14 @@ cudaError_t launch_scan(uint32_t* count, uint32_t* start, uint32_t n_keys, uint3
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const InstDev* inst, const InstDyn* dyn, int n_inst, Geo geo, const double* acc,
-                            double* mom, double* glob, int64_t n_bins, cudaStream_t s) {
+cudaError_t launch_finalize(const InstDev* inst, const InstDyn* dyn, int n_inst, Geo geo,
+                            const unsigned long long* acc, double* mom, double* glob, unsigned long long* gacc,
+                            int64_t n_bins, cudaStream_t s) {
     if (n_bins == 0 || n_inst == 0) return cudaSuccess;
     const int64_t per = n_bins / n_inst;
-    finalize_bins_kernel<<<(unsigned)((n_bins + 255) / 256), 256, 0, s>>>(inst, dyn, geo, acc, mom, n_bins, per);
-    finalize_glob_kernel<<<n_inst, 256, 0, s>>>(acc, glob, per);
+    finalize_bins_kernel<<<(unsigned)((n_bins + 255) / 256), 256, 0, s>>>(inst, dyn, geo, acc, mom, gacc, n_bins,
+                                                                         per);
+    finalize_glob_kernel<<<(n_inst + 127) / 128, 128, 0, s>>>(dyn, gacc, glob, n_inst);
     return cudaGetLastError();
 }
 

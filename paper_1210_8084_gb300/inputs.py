@@ -22,6 +22,8 @@ Recipes (units m = 1, k_B = 1, v_th = sqrt(T_left / m) = 1):
     random directions, v_blast inside r_blast of the centre, absorbing walls.
 """
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -33,10 +35,63 @@ def _rng(seed, stream):
     return np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(seed), int(stream)])))
 
 
+# Above this many particles a Sod tube is drawn in blocks of CHUNK particles,
+# block k from its own stream (seed, stream, k), on all host cores; smaller
+# tubes keep the single-stream recipe.
+CHUNKED_ABOVE = 1 << 25
+CHUNK = 1 << 22
+
+
+def _sod_tube_chunked(n, seed, lo, hi, split, rho, p, dim_pos, vel_dim, dtype):
+    vol_l = (split - lo[0]) / (hi[0] - lo[0])
+    w_l, w_r = rho[0] * vol_l, rho[1] * (1.0 - vol_l)
+    n_l = int(round(n * w_l / (w_l + w_r)))
+    T = (p[0] / rho[0], p[1] / rho[1])
+    pos = np.empty((n, 3), dtype=dtype)
+    vel = np.empty((n, 3), dtype=dtype)
+
+    def block(k):
+        a, b = k * CHUNK, min(n, (k + 1) * CHUNK)
+        idx = np.arange(a, b)
+        left = idx < n_l
+        g = np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(seed), 1, k])))
+        x = np.where(left, g.uniform(lo[0], split, b - a), g.uniform(split, hi[0], b - a))
+        x = np.clip(x, lo[0], hi[0])
+        P = np.empty((b - a, 3))
+        P[:, 0] = x
+        for d in (1, 2):
+            y = g.uniform(lo[d], hi[d], b - a)
+            P[:, d] = np.where(y >= hi[d], lo[d], y)
+        if dim_pos == 2:
+            P[:, 2] = 0.0
+        gv = np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(seed), 2, k])))
+        V = gv.normal(0.0, 1.0, (b - a, 3)) * np.where(left, math.sqrt(T[0]), math.sqrt(T[1]))[:, None]
+        if vel_dim == 2:
+            V[:, 2] = 0.0
+        Pc = P.astype(dtype)
+        for d in (1, 2):   # a periodic coordinate that rounds up to hi is the point lo
+            Pc[:, d] = np.where(Pc[:, d] >= dtype(hi[d]), dtype(lo[d]), Pc[:, d])
+        pos[a:b] = Pc
+        vel[a:b] = V.astype(dtype)
+
+    n_blocks = (n + CHUNK - 1) // CHUNK
+    with ThreadPoolExecutor(max_workers=min(n_blocks, os.cpu_count() or 1)) as ex:
+        list(ex.map(block, range(n_blocks)))
+    return pos, vel
+
+
 def sod_tube(n, seed=0, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), split=0.5, rho=(1.0, 0.125), p=(1.0, 0.1),
-             dim_pos=3, vel_dim=3):
-    """(pos, vel) float64 arrays of shape (n, 3), left particles first.
-    vel_dim = 2: velocities in the (x, y) plane (v_z = 0)."""
+             dim_pos=3, vel_dim=3, dtype=np.float64):
+    """(pos, vel) arrays of shape (n, 3), left particles first, in dtype
+    (rounded from binary64 as cast_state rounds, y and z periodic).
+    vel_dim = 2: velocities in the (x, y) plane (v_z = 0).  Tubes of more than
+    CHUNKED_ABOVE particles are drawn in independent blocks in parallel."""
+    if n > CHUNKED_ABOVE:
+        return _sod_tube_chunked(n, seed, np.asarray(lo, dtype=np.float64), np.asarray(hi, dtype=np.float64),
+                                 split, rho, p, dim_pos, vel_dim, dtype)
+    if dtype is not np.float64:
+        pos, vel = sod_tube(n, seed, lo, hi, split, rho, p, dim_pos, vel_dim)
+        return cast_state(pos, vel, dtype, lo, hi, (WALL, PERIODIC, PERIODIC))
     lo = np.asarray(lo, dtype=np.float64)
     hi = np.asarray(hi, dtype=np.float64)
     vol_l = (split - lo[0]) / (hi[0] - lo[0])
@@ -187,12 +242,15 @@ WORKLOADS = {
 }
 
 
-def make_state(w, n=None, seed=None):
-    """Initial (pos, vel) float64 of a workload dict (optionally resized)."""
+def make_state(w, n=None, seed=None, dtype=np.float64):
+    """Initial (pos, vel) of a workload dict (optionally resized), in dtype
+    (rounded as cast_state rounds)."""
     n = w["n"] if n is None else n
     seed = w["seed"] if seed is None else seed
     if w["kind"] == "sod":
-        return sod_tube(n, seed, lo=w["lo"], hi=w["hi"], dim_pos=w["dim_pos"])
+        return sod_tube(n, seed, lo=w["lo"], hi=w["hi"], dim_pos=w["dim_pos"], dtype=dtype)
+    if dtype is not np.float64:
+        return cast_state(*make_state(w, n, seed), dtype, w["lo"], w["hi"], w["bc"])
     if w["kind"] == "quadrants":
         return quadrants_2d(n, seed)
     raise ValueError(w["kind"])

@@ -76,7 +76,9 @@ def _run(workload, cells, steps_before=2):
                         seed=w["seed"], precision=w["precision"], occupancy_target=0.0)
     sim = k.Simulation(cfg, pos, vel)
     del pos, vel
-    R2 = sim.info().R2
+    # contact distance on the oracle side (Eq. 7, Eq. reff_lambda; n = N / V)
+    V = float(np.prod([w["hi"][d] - w["lo"][d] for d in range(dim)]))
+    R2 = oracle.contact_R2(w["lam"], 0.0, n / V)
     sim.step(steps_before, want_moments=1)
     p0, v0 = sim.state()
     e0 = sim.moments()[2][0, 1]

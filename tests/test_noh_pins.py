@@ -5,7 +5,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import noh
+from analytic import noh
 
 
 def _shell_volume(r0, r1, d):

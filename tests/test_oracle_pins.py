@@ -497,7 +497,7 @@ def test_deterministic_given_seed_and_step():
 
 
 def _sod_l1(raw, n, t, nb):
-    from oracle import riemann
+    from analytic import riemann
     k = raw.shape[0] // nb
     R = raw.reshape(nb, k, 8).sum(1)
     N = R[:, 0]
@@ -671,3 +671,43 @@ def test_absorbing_walls_remove_exactly_the_particles_that_leave():
     assert np.all(np.isnan(p2[out, 0]))
     assert np.all(best2[out] == -1)
     assert not np.isin(best2[best2 >= 0], np.nonzero(out)[0]).any()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_virial_pressure_of_one_hand_placed_pair(dim):
+    """The collisional pressure of a single pair, from the stress definition
+    (Eq. stress, collisional part r_ij . dp_i at the point of closest approach,
+    Eq. 18: p = trace / (d V)), with the pair's impulse counted once for each
+    partner and divided by the step (the reading of the garbled virial).  Two
+    particles pass each other along x with speeds +-u and impact parameter b
+    (along y), so r_ij(t_poca) = (0, b, 0) exactly, whatever the outgoing
+    direction: p_vir = 2 b u n_y / (2 d V_c dt) with n = v_i' / u read off the
+    oracle's own post-collision velocity.  A virial taken at the start of the
+    step (r_ij = (-2a, b, 0)), a dropped partner, a wrong sign or a wrong
+    normalisation all change it.  Kinetic part: T = u^2 / f, p_kin = n T."""
+    a, b, u = 0.125, 0.0625, 2.0
+    dt = 2 * a / u
+    lo, hi = (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)
+    P = params(dim=dim, n_cells=(1, 1, 1), lo=lo, hi=hi, bc=(0, 0, 0), R2=4 * b * b, dt=dt, seed=77)
+    pos = np.array([[0.5 - a, 0.5 + b / 2, 0.5], [0.5 + a, 0.5 - b / 2, 0.5]])
+    vel = np.array([[u, 0.0, 0.0], [-u, 0.0, 0.0]])
+    seen = 0
+    for step in range(6):
+        P.step = step
+        best = oracle.best_partners(P, pos, vel)
+        assert list(best) == [1, 0]
+        po, vo, W, paired = oracle.collide_move(P, pos, vel, best)
+        assert list(paired) == [1, 0]
+        n_hat = vo[0] / u
+        assert np.allclose(vo[1], -vo[0], atol=1e-15) and abs(np.linalg.norm(n_hat) - 1) < 1e-14
+        raw, der, glob = oracle.moments(P, po, vo, W)
+        Vc = 1.0
+        expect_w = 2 * b * u * n_hat[1]
+        assert raw[0, 7] == pytest.approx(expect_w, abs=1e-14)
+        assert der[0, 6] == pytest.approx(expect_w / (2 * dim * Vc * dt), abs=1e-13)
+        # kinetic part: bulk velocity 0, v_rms^2 = u^2, f = 3 velocity components
+        assert der[0, 4] == pytest.approx(u * u / 3, rel=1e-14)
+        assert der[0, 5] == pytest.approx(2 / Vc * u * u / 3, rel=1e-14)
+        assert der[0, 7] == pytest.approx(der[0, 5] + der[0, 6], rel=1e-14)
+        seen += abs(n_hat[1]) > 0.1
+    assert seen >= 2   # the draws give outgoing directions with a real y component

@@ -10,7 +10,7 @@ import math
 import numpy as np
 import pytest
 
-from oracle import riemann
+from analytic import riemann
 
 SOD = ((1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
 

@@ -3,7 +3,7 @@ conservation laws the integration does not use."""
 import numpy as np
 import pytest
 
-from oracle import sedov
+from analytic import sedov
 
 CASES = [(3, 5.0 / 3.0), (2, 5.0 / 3.0), (2, 2.0), (1, 1.4), (3, 1.4)]
 
