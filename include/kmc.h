@@ -65,12 +65,22 @@ extern "C" {
                             * input of kmc_init / kmc_set_state marks a particle already absorbed) */
 
 #define KMC_FLAG_RECORD 1   /* keep each particle's closest candidate and partner of the last step */
-#define KMC_FLAG_NO_GRAPH 2 /* launch kernels directly instead of replaying a captured CUDA graph */
+#define KMC_FLAG_NO_GRAPH 2 /* launch kernels directly instead of replaying a captured CUDA graph (by default
+                             * kmc_step launches one graph that loops over all its steps on the device) */
 #define KMC_FLAG_STAGED_SEARCH 4 /* stage tile neighbourhoods in shared memory (3-D; same results as the direct search) */
 #define KMC_FLAG_NO_TILE_SEARCH 8 /* search unsubdivided grids per particle too (default: one block per c-bin; same results) */
 #define KMC_FLAG_VELOCITY_2D 32  /* dim_pos = 2 only: velocities in the (x, y) plane (the paper's 2-D runs, f = 2,
                                   * gamma = 2): v_z must be 0, outgoing directions isotropic in the plane
                                   * (azimuth 2 pi u2 of the pair's draw), T = m v_rms^2 / 2 */
+#define KMC_FLAG_DSMC 64   /* comparison variant, not the paper's method: the classic random-partner DSMC
+                            * collisions the paper contrasts with PoCA (Sect. "Direct Simulation Monte Carlo
+                            * Technique"), in Bird's no-time-counter form, instead of the closest-approach search:
+                            * per c-bin of N particles and volume V_c, floor(N (N-1) sigma g_max dt / (2 V_c) + u)
+                            * random candidate pairs (sigma of Eq. 7, g_max = 2 v_max), each accepted with
+                            * probability |v_i - v_j| / g_max and scattered as the PoCA pairs are, one after
+                            * another, then free flight for all.  The collision cells are the c-bins (sub_cells
+                            * must be 0 or 1).  Collided particles count as paired in the moments (zero virial);
+                            * kmc_get_partners reports -1 */
 #define KMC_FLAG_ADAPTIVE_DT 16  /* timestep dt(t) = dx_min / v_max(t) of each step's start state (Sect. "Simulation
                                   * setup"; dx_min the smallest c-bin width, v_max the largest speed of the instance,
                                   * |v|^2 = fma(vz, vz, fma(vy, vy, vx vx)) in the state precision, the quotient in
@@ -80,6 +90,9 @@ extern "C" {
 #define KMC_MOM_RAW 1       /* per c-bin: N, Sum vx, Sum vy, Sum vz, Sum vx^2, Sum vy^2, Sum vz^2, Sum W */
 #define KMC_MOM_DERIVED 2   /* per c-bin: n, ux, uy, uz, T, p_kin, p_vir, p */
 #define KMC_MOM_GLOBAL 4    /* per instance: N, E = 1/2 Sum |v|^2, Px, Py, Pz, Sum W, pairs, 0 */
+#define KMC_MOM_RADIAL 8    /* per c-bin: Sum v.r_hat, v_r = Sum v.r_hat / N (Eq. vel_r; the Noh and Sedov tests),
+                             * r_hat the unit vector from kmc_config.radial_center to the particle over the
+                             * position dimensions (no periodic image; 0 for a particle at the centre) */
 
 typedef struct kmc_handle kmc_handle;
 
@@ -111,6 +124,7 @@ typedef struct kmc_config {
     int sub_cells[3];   /* search-grid subdivision of each c-bin per dimension; 0 = automatic */
     double occupancy_target; /* automatic subdivision: particles per search cell aimed at (0 = 0.5) */
     int flags;          /* KMC_FLAG_* */
+    double radial_center[3]; /* centre of the radial velocity moment (KMC_MOM_RADIAL), finite */
 } kmc_config;
 
 /* Mean number of candidates a particle of the current state examines in the
@@ -140,6 +154,9 @@ typedef struct kmc_info {
     int n_scan_tiles;        /* tiles of the key scan (kmc_test_hold_scan) */
     int kernels_per_step;    /* kernels one kmc_step launches per step without moments */
     int kernels_moments;     /* kernels added per step when moments are wanted */
+    int graph_mode;          /* how the last kmc_step ran: 2 = one CUDA graph for all its steps (a device-side
+                              * loop counter drives a conditional while node), 1 = one graph per step,
+                              * 0 = kernel by kernel (KMC_FLAG_NO_GRAPH, or before the first kmc_step) */
 } kmc_info;
 
 /* Create a simulation.  pos and vel are n x 3 row-major arrays of float
@@ -178,7 +195,7 @@ KMC_API int kmc_step_profiled(kmc_handle* h, int nsteps, int want_moments, doubl
 
 /* Copy moments into out (caller-allocated doubles): the blocks selected by
  * fields_mask, in the order RAW (n_bins x 8), DERIVED (n_bins x 8),
- * GLOBAL (n_instances x 8).  Rows are c-bins with key c_x + n_x (c_y + n_y c_z),
+ * GLOBAL (n_instances x 8), RADIAL (n_bins x 2).  Rows are c-bins with key c_x + n_x (c_y + n_y c_z),
  * instance-major.  Moments are those accumulated by the last kmc_step with
  * want_moments != 0, or, if none since the state was last set, of the current
  * state with zero virial.  Synchronises the stream when where == HOST. */

@@ -68,6 +68,10 @@ def lib():
         L.orc_collide_move_ids.restype = None
         L.orc_moments.argtypes = [P, i64, dp, dp, dp, dp, dp, dp]
         L.orc_moments.restype = None
+        L.orc_dsmc_collide.argtypes = [P, i64, dp, dp, ip]
+        L.orc_dsmc_collide.restype = i64
+        L.orc_radial.argtypes = [P, i64, dp, dp, dp, dp]
+        L.orc_radial.restype = None
         L.orc_step.argtypes = [P, i64, dp, dp, ip, ip, dp, dp, dp]
         L.orc_step.restype = i64
         _lib = L
@@ -208,6 +212,34 @@ def moments(P, pos, vel, virial=None):
     W = None if virial is None else np.ascontiguousarray(virial, dtype=np.float64)
     lib().orc_moments(ctypes.byref(P), n, _d(pos), _d(vel), _d(W), _d(raw), _d(der), _d(glob))
     return raw, der, glob
+
+
+def dsmc_collide(P, pos, vel):
+    """DSMC comparison variant (random partners in a c-bin): returns
+    (new velocities, collided flags, accepted collisions); inputs unchanged."""
+    pos, vel = _state(pos, vel)
+    v = vel.copy()
+    n = pos.shape[0]
+    collided = np.zeros(n, dtype=np.int32)
+    acc = lib().orc_dsmc_collide(ctypes.byref(P), n, _d(pos), _d(v), _i(collided))
+    return v, collided, int(acc)
+
+
+def dsmc_step(P, pos, vel):
+    """One step of the DSMC variant: collisions, then free flight and walls.
+    Returns (pos, vel, collided, accepted)."""
+    v, collided, acc = dsmc_collide(P, pos, vel)
+    po, vo, _, _ = collide_move(P, pos, v, np.full(len(v), -1, dtype=np.int32))
+    return po, vo, collided, acc
+
+
+def radial(P, pos, vel, center=(0.0, 0.0, 0.0)):
+    """Per-c-bin [Sum v . r_hat, v_r] (Eq. vel_r) about `center`."""
+    pos, vel = _state(pos, vel)
+    c = np.ascontiguousarray(center, dtype=np.float64).reshape(3)
+    out = np.zeros((n_bins(P), 2))
+    lib().orc_radial(ctypes.byref(P), pos.shape[0], _d(pos), _d(vel), _d(c), _d(out))
+    return out
 
 
 def step(P, pos, vel):

@@ -559,6 +559,126 @@ void orc_collide_move_ids(const orc_params* P, int64_t n, const double* pos,
     }
 }
 
+/* ------------------------------------------------------------ DSMC variant */
+
+/* The classic DSMC collision step the paper contrasts with its method (Sect.
+ * "Direct Simulation Monte Carlo Technique": collisions only between particles
+ * of the same scattering cell, partners picked at random), in Bird's
+ * no-time-counter form with the cross-section of Eq. 7.  Cells are the
+ * c-bins; a cell's particles are taken in increasing id.  Per cell with N >= 2
+ * particles and volume V_c:
+ *   M = floor(1/2 N (N - 1) sigma g_max dt / V_c + u_0) candidate pairs, with
+ *       sigma = pi R^2 and g_max = 2 v_max (v_max the largest speed of the
+ *       state, so g_max bounds every relative speed);
+ *   candidate k: i, j distinct positions in the cell drawn uniformly, accepted
+ *       with probability g / g_max (g = |v_i - v_j|; sigma is the same for all
+ *       pairs), then scattered as the PoCA pairs are: isotropic in the CM
+ *       frame, v' = v_cm +- g/2 n.
+ * Collisions are applied in candidate order, each to the current velocities.
+ * Random numbers: Philox4x32-10 with key = seed and counter (cell, step, k,
+ * 0x44534D43) for the pair and the acceptance, (cell, step, k, 0x44534D44) for
+ * the direction, (cell, step, 0xFFFFFFFF, 0x44534D43) for u_0; cell = the
+ * c-bin's index with x slowest, (c_x n_y + c_y) n_z + c_z.  Position indices:
+ * i = floor(w0 N / 2^32), j = floor(w1 (N - 1) / 2^32), j += 1 when j >= i.
+ * All of it in binary64; with decide32 the new velocities are rounded to
+ * binary32 after every collision (the state precision).  Velocities are
+ * updated in place; collided[i] = 1 for a particle in at least one accepted
+ * pair.  Returns the number of accepted collisions. */
+int64_t orc_dsmc_collide(const orc_params* P, int64_t n, const double* pos, double* vel, int32_t* collided)
+{
+    const uint32_t key[2] = {(uint32_t)(P->seed & 0xffffffffu), (uint32_t)(P->seed >> 32)};
+    const uint32_t TAG_PAIR = 0x44534D43u, TAG_DIR = 0x44534D44u;
+    int C = n_bins(P);
+    int32_t* cidx = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)(n > 0 ? n : 1));
+    int32_t* kk = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    orc_cell_keys(P, n, pos, kk, cidx);
+    /* cell of every particle in the search order (x slowest); -1 when absorbed */
+    int64_t* cnt = (int64_t*)calloc((size_t)C + 1, sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) {
+        if (kk[i] < 0) continue;
+        const int32_t* c = cidx + 3 * i;
+        int32_t s = P->dim == 3 ? (c[0] * P->n_cells[1] + c[1]) * P->n_cells[2] + c[2] : c[0] * P->n_cells[1] + c[1];
+        kk[i] = s;
+        cnt[s + 1] += 1;
+    }
+    for (int c = 0; c < C; ++c) cnt[c + 1] += cnt[c];
+    /* ids of every cell in increasing order (a stable counting sort over ids) */
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(C > 0 ? C : 1));
+    int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int c = 0; c < C; ++c) fill[c] = cnt[c];
+    for (int64_t i = 0; i < n; ++i)
+        if (kk[i] >= 0) order[fill[kk[i]]++] = i;
+    /* largest speed, |v|^2 as the adaptive timestep takes it */
+    double v2max = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (kk[i] < 0) continue;
+        const double* v = vel + 3 * i;
+        double v2;
+        if (P->decide32) {
+            float x = (float)v[0], y = (float)v[1], z = (float)v[2];
+            float xx = x * x;
+            v2 = (double)fmaf(z, z, fmaf(y, y, xx));
+        } else {
+            v2 = fma(v[2], v[2], fma(v[1], v[1], v[0] * v[0]));
+        }
+        if (v2 > v2max) v2max = v2;
+    }
+    const double gmax = 2.0 * sqrt(v2max);
+    const double sigma = M_PI * P->R2;
+    double Vc = 1.0;
+    for (int d = 0; d < P->dim; ++d) Vc *= (P->hi[d] - P->lo[d]) / P->n_cells[d];
+    for (int64_t i = 0; i < n; ++i) collided[i] = 0;
+    int64_t accepted = 0;
+    for (int c = 0; c < C; ++c) {
+        const int64_t N = cnt[c + 1] - cnt[c];
+        if (N < 2) continue;
+        const int64_t* ids = order + cnt[c];
+        uint32_t w[4];
+        uint32_t ctr0[4] = {(uint32_t)c, P->step, 0xFFFFFFFFu, TAG_PAIR};
+        orc_philox4x32_10(ctr0, key, w);
+        const double Nd = (double)N;
+        const double m_real = 0.5 * Nd * (Nd - 1.0) * sigma * gmax * P->dt / Vc;
+        const double m = floor(m_real + uniform64(w[0], w[1]));
+        const uint32_t M = m > 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)m;
+        for (uint32_t k = 0; k < M; ++k) {
+            uint32_t ctr[4] = {(uint32_t)c, P->step, k, TAG_PAIR};
+            orc_philox4x32_10(ctr, key, w);
+            uint32_t pi = (uint32_t)(((uint64_t)w[0] * (uint64_t)N) >> 32);
+            uint32_t pj = (uint32_t)(((uint64_t)w[1] * (uint64_t)(N - 1)) >> 32);
+            if (pj >= pi) pj += 1u;
+            double* va = vel + 3 * ids[pi];
+            double* vb = vel + 3 * ids[pj];
+            double dv0 = va[0] - vb[0], dv1 = va[1] - vb[1], dv2 = va[2] - vb[2];
+            double g = sqrt(dv0 * dv0 + dv1 * dv1 + dv2 * dv2);
+            if (!(uniform64(w[2], w[3]) * gmax < g)) continue;
+            uint32_t ctr2[4] = {(uint32_t)c, P->step, k, TAG_DIR};
+            orc_philox4x32_10(ctr2, key, w);
+            double u1 = uniform64(w[0], w[1]), u2 = uniform64(w[2], w[3]);
+            double cth = 1.0 - 2.0 * u1;
+            double sth = 2.0 * sqrt(u1 * (1.0 - u1));
+            double phi = 2.0 * M_PI * u2;
+            double nhat[3] = {sth * cos(phi), sth * sin(phi), cth};
+            if (P->vel_dim == 2) {
+                nhat[0] = cos(phi);
+                nhat[1] = sin(phi);
+                nhat[2] = 0.0;
+            }
+            double h = 0.5 * g;
+            for (int d = 0; d < 3; ++d) {
+                double vcm = 0.5 * (va[d] + vb[d]);
+                double a = vcm + h * nhat[d], b = vcm - h * nhat[d];
+                va[d] = P->decide32 ? (double)(float)a : a;
+                vb[d] = P->decide32 ? (double)(float)b : b;
+            }
+            collided[ids[pi]] = 1;
+            collided[ids[pj]] = 1;
+            ++accepted;
+        }
+    }
+    free(cidx); free(kk); free(cnt); free(fill); free(order);
+    return accepted;
+}
+
 /* ---------------------------------------------------------------- moments */
 
 void orc_moments(const orc_params* P, int64_t n, const double* pos, const double* vel,
@@ -608,6 +728,34 @@ void orc_moments(const orc_params* P, int64_t n, const double* pos, const double
     }
     if (glob) for (int k = 0; k < 8; ++k) glob[k] = G[k];
     free(acc);
+}
+
+void orc_radial(const orc_params* P, int64_t n, const double* pos, const double* vel,
+                const double* center, double* out)
+{
+    int C = n_bins(P);
+    for (int c = 0; c < 2 * C; ++c) out[c] = 0.0;
+    double* cnt = (double*)calloc((size_t)C, sizeof(double));
+    int32_t* key = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    orc_cell_keys(P, n, pos, key, NULL);
+    for (int64_t i = 0; i < n; ++i) {
+        if (key[i] < 0) continue;   /* absorbed */
+        double r[3] = {0.0, 0.0, 0.0};
+        double r2 = 0.0;
+        for (int d = 0; d < P->dim; ++d) {
+            r[d] = pos[3 * i + d] - center[d];
+            r2 += r[d] * r[d];
+        }
+        cnt[key[i]] += 1.0;
+        if (r2 <= 0.0) continue;
+        double len = sqrt(r2), vr = 0.0;
+        for (int d = 0; d < P->dim; ++d) vr += vel[3 * i + d] * (r[d] / len);
+        out[2 * (size_t)key[i]] += vr;
+    }
+    for (int c = 0; c < C; ++c)
+        if (cnt[c] > 0.0) out[2 * (size_t)c + 1] = out[2 * (size_t)c] / cnt[c];
+    free(cnt);
+    free(key);
 }
 
 /* ------------------------------------------------------------------- step */

@@ -103,12 +103,26 @@ void orc_collide_move_ids(const orc_params* P, int64_t n, const double* pos,
                           double* pos_out, double* vel_out, double* virial_out,
                           int32_t* paired_out);
 
+/* The DSMC comparison variant's collisions (random partners inside a c-bin,
+ * Bird's no-time-counter scheme with sigma of Eq. 7): velocities updated in
+ * place, collided[i] = 1 for particles in an accepted pair; returns the number
+ * of accepted collisions.  The definition is restated in kmc_oracle.c.  The
+ * move that follows is orc_collide_move with no pairs (free flight, walls). */
+int64_t orc_dsmc_collide(const orc_params* P, int64_t n, const double* pos, double* vel, int32_t* collided);
+
 /* Per-c-bin moments of the given state.  raw: C x 8 =
  * [N, Sum vx, Sum vy, Sum vz, Sum vx^2, Sum vy^2, Sum vz^2, Sum W];
  * derived: C x 8 = [n, ux, uy, uz, T, p_kin, p_vir, p];
  * glob: 8 = [N, E, Px, Py, Pz, Sum W, 0, 0].  Any output may be NULL. */
 void orc_moments(const orc_params* P, int64_t n, const double* pos, const double* vel,
                  const double* virial, double* raw, double* derived, double* glob);
+
+/* Radial velocity per c-bin (Eq. vel_r, the Noh and Sedov tests):
+ * v_r = (1/N) Sum_i v_i . r_hat_i, r_hat_i the unit vector from `center` to
+ * particle i over the position dimensions (a particle at the centre adds 0).
+ * out: C x 2 = [Sum v . r_hat, v_r] (v_r = 0 in an empty c-bin). */
+void orc_radial(const orc_params* P, int64_t n, const double* pos, const double* vel,
+                const double* center, double* out);
 
 /* One full step in place.  best_out (n), paired_out (n), raw/derived/glob
  * as in orc_moments; any may be NULL.  Returns the number of pairs. */

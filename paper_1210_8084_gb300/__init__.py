@@ -37,9 +37,11 @@ KMC_FLAG_STAGED_SEARCH = 4
 KMC_FLAG_NO_TILE_SEARCH = 8
 KMC_FLAG_ADAPTIVE_DT = 16
 KMC_FLAG_VELOCITY_2D = 32
+KMC_FLAG_DSMC = 64
 KMC_MOM_RAW = 1
 KMC_MOM_DERIVED = 2
 KMC_MOM_GLOBAL = 4
+KMC_MOM_RADIAL = 8
 KMC_NPHASES = 7
 PHASES = ("search", "tile", "move", "scan", "scatter", "moments", "finalize")
 
@@ -80,6 +82,7 @@ class KmcConfig(ctypes.Structure):
         ("sub_cells", ctypes.c_int * 3),
         ("occupancy_target", ctypes.c_double),
         ("flags", ctypes.c_int),
+        ("radial_center", ctypes.c_double * 3),
     ]
 
 
@@ -105,6 +108,7 @@ class KmcInfo(ctypes.Structure):
         ("n_scan_tiles", ctypes.c_int),
         ("kernels_per_step", ctypes.c_int),
         ("kernels_moments", ctypes.c_int),
+        ("graph_mode", ctypes.c_int),
     ]
 
 
@@ -207,7 +211,7 @@ def _check(rc, h=None):
 def make_config(dim_pos=3, n_cells=(1, 1, 1), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
                 bc=(KMC_BC_WALL, KMC_BC_PERIODIC, KMC_BC_PERIODIC), lam=1e-3, sigma=0.0, dt=1e-3,
                 seed=0, precision=32, instances=None, stream=None, sub_cells=(0, 0, 0),
-                occupancy_target=0.0, flags=0):
+                occupancy_target=0.0, flags=0, radial_center=(0.0, 0.0, 0.0)):
     """Fill a KmcConfig.  `instances` is a list of dicts with keys n, lam, sigma, dt, seed;
     the returned object keeps the instance array alive."""
     c = KmcConfig()
@@ -218,6 +222,7 @@ def make_config(dim_pos=3, n_cells=(1, 1, 1), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 
         c.hi[d] = float(hi[d]) if d < len(hi) else 1.0
         c.bc[d] = int(bc[d]) if d < len(bc) else KMC_BC_PERIODIC
         c.sub_cells[d] = int(sub_cells[d]) if d < len(sub_cells) else 0
+        c.radial_center[d] = float(radial_center[d]) if d < len(radial_center) else 0.0
     c.lambda_ = float(lam)
     c.sigma = float(sigma)
     c.dt = float(dt)
@@ -413,6 +418,12 @@ class Simulation:
         partner = np.zeros(self.n, dtype=np.int32)
         kmc_get_partners(self.h, best, partner)
         return best, partner
+
+    def radial(self):
+        """[bins, 2]: Sum v.r_hat and the radial velocity v_r per c-bin (Eq. vel_r)."""
+        out = np.zeros(kmc_moments_size(self.h, KMC_MOM_RADIAL), dtype=np.float64)
+        kmc_moments(self.h, out, KMC_WHERE_HOST, KMC_MOM_RADIAL)
+        return out.reshape(-1, 2)
 
     def moments(self):
         """(raw [bins, 8], derived [bins, 8], glob [instances, 8])"""

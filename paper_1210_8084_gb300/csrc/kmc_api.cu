@@ -41,7 +41,7 @@ struct kmc_handle {
     void *posA = nullptr, *velA = nullptr, *posB = nullptr, *velB = nullptr;
     unsigned long long* bkey = nullptr;
     uint32_t* slot_of = nullptr;
-    uint32_t *key = nullptr, *slot = nullptr, *count = nullptr, *start = nullptr, *bad = nullptr;
+    uint32_t *key = nullptr, *slot = nullptr, *tagB = nullptr, *count = nullptr, *start = nullptr, *bad = nullptr;
     unsigned long long* scan_status = nullptr;
     InstDev* inst_d = nullptr;
     InstDyn* dyn_d = nullptr;
@@ -57,8 +57,10 @@ struct kmc_handle {
     int64_t n_bins = 0, bins_per_inst = 0;
     int64_t bytes = 0;
     int mom_state = 0;  // 1: acc/mom/glob describe the current state
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};       // one step (per want_moments)
+    cudaGraphExec_t loop_graph[2] = {nullptr, nullptr};  // all steps of a call: device-side loop
     bool graph_failed = false;
+    bool loop_failed = false;
     std::string err;
 };
 
@@ -114,6 +116,7 @@ Bufs<T> make_bufs(const kmc_handle* h) {
     b.slot_of = h->slot_of;
     b.key = h->key;
     b.slot = h->slot;
+    b.tagB = h->tagB;
     b.count = h->count;
     b.start = h->start;
     b.scan_status = h->scan_status;
@@ -133,6 +136,7 @@ Bufs<T> make_bufs(const kmc_handle* h) {
     b.stage_pair_cap = h->stage_pair_cap;
     b.any_direct = h->any_direct;
     b.any_tiled = h->any_tiled;
+    b.dsmc = (h->cfg.flags & KMC_FLAG_DSMC) ? 1 : 0;
     b.id_bits = h->id_bits;
     b.id_mask = h->id_bits >= 32 ? 0xffffffffu : ((1u << h->id_bits) - 1u);
     return b;
@@ -148,9 +152,13 @@ cudaError_t enqueue_step(kmc_handle* h, int want_moments, cudaEvent_t* ev = null
     cudaError_t e;
     auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], s) : cudaSuccess; };
     if ((e = mark(KMC_PHASE_SEARCH)) != cudaSuccess) return e;
-    if ((e = launch_search<T>(b, s)) != cudaSuccess) return e;
+    if (b.dsmc) {   // random partners inside each c-bin instead of the closest-approach search
+        if ((e = launch_dsmc<T>(b, s)) != cudaSuccess) return e;
+    } else if ((e = launch_search<T>(b, s)) != cudaSuccess) {
+        return e;
+    }
     if ((e = mark(KMC_PHASE_TILE)) != cudaSuccess) return e;
-    if ((e = launch_tile_search<T>(b, s)) != cudaSuccess) return e;
+    if (!b.dsmc && (e = launch_tile_search<T>(b, s)) != cudaSuccess) return e;
     if ((e = mark(KMC_PHASE_MOVE)) != cudaSuccess) return e;
     if ((e = launch_move<T>(b, s)) != cudaSuccess) return e;
     if ((e = mark(KMC_PHASE_SCAN)) != cudaSuccess) return e;
@@ -281,7 +289,7 @@ void choose_subdivision(const kmc_handle* h, InstDev& I, double vmax, uint32_t m
     }
     for (int d = 0; d < 3; ++d) {
         if (d < h->dim && h->cfg.sub_cells[d] > 0) s[d] = h->cfg.sub_cells[d];
-        if (d >= h->dim) s[d] = 1;
+        if (d >= h->dim || (h->cfg.flags & KMC_FLAG_DSMC)) s[d] = 1;   // DSMC: collision cells are the c-bins
         I.s[d] = s[d];
         I.M[d] = h->geo.n[d] * s[d];
         I.w[d] = h->geo.L[d] / (double)I.M[d];
@@ -357,6 +365,7 @@ int validate_config(const kmc_config* c, int64_t n) {
         if (c->n_cells[d] < 1) return fail(nullptr, KMC_EINVAL, "n_cells must be >= 1");
         if (!(c->hi[d] > c->lo[d]) || !isfinite(c->lo[d]) || !isfinite(c->hi[d]))
             return fail(nullptr, KMC_EINVAL, "box must satisfy lo < hi, finite");
+        if (!isfinite(c->radial_center[d])) return fail(nullptr, KMC_EINVAL, "radial_center must be finite");
         if (c->bc[d] != KMC_BC_PERIODIC && c->bc[d] != KMC_BC_WALL && c->bc[d] != KMC_BC_ABSORB)
             return fail(nullptr, KMC_EINVAL, "bc must be KMC_BC_PERIODIC or KMC_BC_WALL");
         if (c->sub_cells[d] < 0) return fail(nullptr, KMC_EINVAL, "sub_cells must be >= 0");
@@ -365,8 +374,13 @@ int validate_config(const kmc_config* c, int64_t n) {
     if (c->n_instances > 1 && !c->instances) return fail(nullptr, KMC_EINVAL, "instances is NULL");
     if (c->flags &
         ~(KMC_FLAG_RECORD | KMC_FLAG_NO_GRAPH | KMC_FLAG_STAGED_SEARCH | KMC_FLAG_NO_TILE_SEARCH | KMC_FLAG_ADAPTIVE_DT |
-          KMC_FLAG_VELOCITY_2D))
+          KMC_FLAG_VELOCITY_2D | KMC_FLAG_DSMC))
         return fail(nullptr, KMC_EINVAL, "unknown flags");
+    if (c->flags & KMC_FLAG_DSMC) {
+        for (int d = 0; d < c->dim_pos; ++d)
+            if (c->sub_cells[d] > 1) return fail(nullptr, KMC_EINVAL, "KMC_FLAG_DSMC: the collision cells are the c-bins");
+        if (c->flags & KMC_FLAG_STAGED_SEARCH) return fail(nullptr, KMC_EINVAL, "KMC_FLAG_DSMC has no search to stage");
+    }
     if ((c->flags & KMC_FLAG_VELOCITY_2D) && c->dim_pos != 2)
         return fail(nullptr, KMC_EINVAL, "2-D velocities need dim_pos = 2");
     return KMC_OK;
@@ -385,6 +399,8 @@ void release(kmc_handle* h) {
     if (!h) return;
     for (int g = 0; g < 2; ++g)
         if (h->graph[g]) cudaGraphExecDestroy(h->graph[g]);
+    for (int g = 0; g < 2; ++g)
+        if (h->loop_graph[g]) cudaGraphExecDestroy(h->loop_graph[g]);
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (auto& a : h->allocs) cudaFree(a.p);
     h->allocs.clear();
@@ -402,6 +418,53 @@ int sort_packed(kmc_handle* h, uint32_t step) {
     KMC_CUDA(h, e);
     h->mom_state = 0;
     return check_device_error(h);
+}
+
+// Device side of the graph-resident step loop: the body of a conditional
+// while node is one step followed by this kernel, which counts the step and
+// clears the loop's condition after the last one.
+__global__ void loop_control(DevState* st, cudaGraphConditionalHandle loop) {
+    const uint32_t left = st->steps_left > 0u ? st->steps_left - 1u : 0u;
+    st->steps_left = left;
+    cudaGraphSetConditional(loop, left > 0u ? 1u : 0u);
+}
+
+__global__ void set_steps_left(DevState* st, uint32_t n) { st->steps_left = n; }
+
+// One executable graph that runs steps_left steps of the handle: a while node
+// (condition 1 at every launch) whose body is the step's launch sequence plus
+// loop_control.  Returns an error (the caller falls back to one graph per
+// step) where conditional nodes are not available.
+cudaError_t build_loop_graph(kmc_handle* h, int want_moments, cudaGraphExec_t* out) {
+    *out = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle loop;
+    e = cudaGraphConditionalHandleCreate(&loop, g, 1u, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};   // the rest zero
+    p.conditional.handle = loop;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = p.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = enqueue_step_any(h, want_moments);
+            if (e1 == cudaSuccess) {
+                loop_control<<<1, 1, 0, h->stream>>>(h->st_d, loop);
+                e1 = cudaGetLastError();
+            }
+            cudaError_t e2 = cudaStreamEndCapture(h->stream, &body);
+            e = e1 != cudaSuccess ? e1 : e2;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    if (e != cudaSuccess) *out = nullptr;
+    cudaGraphDestroy(g);
+    return e;
 }
 
 }  // namespace
@@ -447,6 +510,7 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
     g.vdim = (cfg->flags & KMC_FLAG_VELOCITY_2D) ? 2 : 3;
     for (int d = 0; d < 3; ++d) {
         const bool used = d < h->dim;
+        g.rc[d] = used ? cfg->radial_center[d] : 0.0;
         g.n[d] = used ? cfg->n_cells[d] : 1;
         g.bc[d] = used ? cfg->bc[d] : KMC_BC_PERIODIC;
         g.lo[d] = used ? cfg->lo[d] : 0.0;
@@ -533,13 +597,14 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
     if ((rc = dev_alloc(h, (void**)&h->slot_of, nv * sizeof(uint32_t)))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->key, nv * sizeof(uint32_t)))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->slot, nv * sizeof(uint32_t)))) return bail(rc);
+    if ((rc = dev_alloc(h, (void**)&h->tagB, nv * sizeof(uint32_t)))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->inst_d, sizeof(InstDev) * h->n_inst))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->dyn_d, sizeof(InstDyn) * h->n_inst))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->st_d, sizeof(DevState)))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->bad, sizeof(uint32_t) * 4))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->acc, sizeof(unsigned long long) * kAccFields * (size_t)h->n_bins)))
         return bail(rc);
-    if ((rc = dev_alloc(h, (void**)&h->mom, sizeof(double) * 16 * (size_t)h->n_bins))) return bail(rc);
+    if ((rc = dev_alloc(h, (void**)&h->mom, sizeof(double) * kMomStride * (size_t)h->n_bins))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->glob, sizeof(double) * 8 * (size_t)h->n_inst))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->gacc, sizeof(unsigned long long) * 8 * (size_t)h->n_inst))) return bail(rc);
     if (cudaMemsetAsync(h->gacc, 0, sizeof(unsigned long long) * 8 * (size_t)h->n_inst, h->stream) != cudaSuccess)
@@ -605,10 +670,17 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
         plan_staged_search(h, max_occ);
         // search cells that are the c-bins themselves: one block per cell
         h->any_tiled = 0;
+        h->any_direct = 0;
+        const bool dsmc = (h->cfg.flags & KMC_FLAG_DSMC) != 0;
         for (auto& I : h->inst_h) {
+            if (dsmc) {   // no closest-approach search at all
+                I.staged = I.tiled = 0;
+                continue;
+            }
             I.tiled = !I.staged && I.n > 0 && I.s[0] == 1 && I.s[1] == 1 && I.s[2] == 1 &&
                       !(h->cfg.flags & KMC_FLAG_NO_TILE_SEARCH);
             h->any_tiled |= I.tiled;
+            h->any_direct |= !I.tiled && !I.staged;   // searched one thread per particle
         }
         if (cudaMemcpyAsync(h->inst_d, h->inst_h.data(), sizeof(InstDev) * h->n_inst, cudaMemcpyHostToDevice,
                             h->stream) != cudaSuccess)
@@ -645,6 +717,20 @@ int kmc_step(kmc_handle* h, int nsteps, int want_moments) {
         return KMC_OK;
     }
     const bool use_graph = !(h->cfg.flags & KMC_FLAG_NO_GRAPH) && !h->graph_failed;
+    // all steps in one graph launch: the loop runs on the device
+    if (use_graph && !h->loop_failed) {
+        if (!h->loop_graph[want_moments] && build_loop_graph(h, want_moments, &h->loop_graph[want_moments]) != cudaSuccess) {
+            cudaGetLastError();
+            h->loop_failed = true;
+        }
+        if (h->loop_graph[want_moments]) {
+            set_steps_left<<<1, 1, 0, h->stream>>>(h->st_d, (uint32_t)nsteps);
+            KMC_CUDA(h, cudaGetLastError());
+            KMC_CUDA(h, cudaGraphLaunch(h->loop_graph[want_moments], h->stream));
+            h->mom_state = want_moments;
+            return KMC_OK;
+        }
+    }
     if (use_graph && !h->graph[want_moments]) {
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
@@ -721,6 +807,7 @@ int64_t kmc_moments_size(const kmc_handle* h, int mask) {
     if (mask & KMC_MOM_RAW) s += 8 * h->n_bins;
     if (mask & KMC_MOM_DERIVED) s += 8 * h->n_bins;
     if (mask & KMC_MOM_GLOBAL) s += 8 * (int64_t)h->n_inst;
+    if (mask & KMC_MOM_RADIAL) s += 2 * h->n_bins;
     return s;
 }
 
@@ -728,7 +815,8 @@ int kmc_moments(kmc_handle* h, double* out, int where, int mask) {
     if (!h) return fail(nullptr, KMC_EINVAL, "handle is NULL");
     if (!out) return fail(h, KMC_EINVAL, "out is NULL");
     if (where != KMC_WHERE_HOST && where != KMC_WHERE_DEVICE) return fail(h, KMC_EINVAL, "bad where");
-    if (mask & ~(KMC_MOM_RAW | KMC_MOM_DERIVED | KMC_MOM_GLOBAL)) return fail(h, KMC_EINVAL, "bad fields_mask");
+    if (mask & ~(KMC_MOM_RAW | KMC_MOM_DERIVED | KMC_MOM_GLOBAL | KMC_MOM_RADIAL))
+        return fail(h, KMC_EINVAL, "bad fields_mask");
     if (!h->mom_state) {
         KMC_CUDA(h, cudaMemsetAsync(h->acc, 0, sizeof(unsigned long long) * kAccFields * (size_t)h->n_bins,
                                     h->stream));
@@ -742,17 +830,22 @@ int kmc_moments(kmc_handle* h, double* out, int where, int mask) {
     const cudaMemcpyKind kind = where == KMC_WHERE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     double* o = out;
     if (h->n_bins > 0 && (mask & KMC_MOM_RAW)) {
-        KMC_CUDA(h, cudaMemcpy2DAsync(o, 8 * sizeof(double), h->mom, 16 * sizeof(double), 8 * sizeof(double),
+        KMC_CUDA(h, cudaMemcpy2DAsync(o, 8 * sizeof(double), h->mom, kMomStride * sizeof(double), 8 * sizeof(double),
                                       (size_t)h->n_bins, kind, h->stream));
         o += 8 * h->n_bins;
     }
     if (h->n_bins > 0 && (mask & KMC_MOM_DERIVED)) {
-        KMC_CUDA(h, cudaMemcpy2DAsync(o, 8 * sizeof(double), h->mom + 8, 16 * sizeof(double), 8 * sizeof(double),
+        KMC_CUDA(h, cudaMemcpy2DAsync(o, 8 * sizeof(double), h->mom + 8, kMomStride * sizeof(double), 8 * sizeof(double),
                                       (size_t)h->n_bins, kind, h->stream));
         o += 8 * h->n_bins;
     }
     if (mask & KMC_MOM_GLOBAL) {
         KMC_CUDA(h, cudaMemcpyAsync(o, h->glob, sizeof(double) * 8 * h->n_inst, kind, h->stream));
+        o += 8 * h->n_inst;
+    }
+    if (h->n_bins > 0 && (mask & KMC_MOM_RADIAL)) {
+        KMC_CUDA(h, cudaMemcpy2DAsync(o, 2 * sizeof(double), h->mom + 16, kMomStride * sizeof(double),
+                                      2 * sizeof(double), (size_t)h->n_bins, kind, h->stream));
     }
     if (where == KMC_WHERE_HOST) return check_device_error(h);
     return KMC_OK;
@@ -770,7 +863,7 @@ int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, const void* 
     std::vector<Trial> trials;
     for (double occ : {0.25, 0.35, 0.5, 0.7, 1.0, 1.5}) trials.push_back({occ, keep});
     trials.push_back({0.0, keep | KMC_FLAG_NO_TILE_SEARCH});
-    if (cfg->dim_pos == 3) trials.push_back({0.0, keep | KMC_FLAG_STAGED_SEARCH});
+    if (cfg->dim_pos == 3 && !(cfg->flags & KMC_FLAG_DSMC)) trials.push_back({0.0, keep | KMC_FLAG_STAGED_SEARCH});
     double best_ms = -1.0;
     kmc_config pick = *cfg;
     int first_rc = KMC_OK;
@@ -860,10 +953,15 @@ int kmc_get_info(kmc_handle* h, kmc_info* info) {
     info->tile_rows = I.staged ? I.tile_rows : 0;
     info->stage_cap = h->stage_cap;
     info->n_scan_tiles = (int)h->n_tiles;
-    // search (always), tile search, staged search, move, scan, two scatter passes,
+    // per-particle search (also records slot_of outside tiled instances), tile
+    // search, staged search, move, scan, two scatter passes,
     // then moments and two finalize kernels when moments are wanted
-    info->kernels_per_step = 1 + (h->any_tiled ? 1 : 0) + (h->n_stage_tiles > 0 ? 1 : 0) + 4;
+    info->kernels_per_step = ((h->any_direct || h->n_stage_tiles > 0) ? 1 : 0) + (h->any_tiled ? 1 : 0) +
+                             (h->n_stage_tiles > 0 ? 1 : 0) + ((h->cfg.flags & KMC_FLAG_DSMC) ? 1 : 0) + 4;
     info->kernels_moments = 3;
+    info->graph_mode = (h->cfg.flags & KMC_FLAG_NO_GRAPH) || h->graph_failed
+                           ? 0
+                           : ((h->loop_graph[0] || h->loop_graph[1]) ? 2 : (h->loop_failed ? 1 : 0));
     return KMC_OK;
 }
 

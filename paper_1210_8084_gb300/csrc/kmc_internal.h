@@ -18,7 +18,9 @@ constexpr int kScanItems = 16;         // scan: keys per thread (4 x uint4)
 constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr uint32_t kSpinCap = 1u << 22;  // bounded waits: iterations before giving up
 constexpr int kFoldCap = 64;           // wall folds per coordinate per step
-constexpr int kAccFields = 9;          // per c-bin accumulator: 8 moment sums + collided count
+constexpr int kAccFields = 10;         // per c-bin accumulator: N, Sum v (3), Sum v^2 (3), Sum W, collided
+                                       // count, Sum v.r_hat
+constexpr int kMomStride = 18;         // per c-bin output: 8 raw, 8 derived, Sum v.r_hat, v_r
 constexpr uint32_t kCanonMax = 16384;  // search cells up to this many particles are put in id order
 
 // device error flags (DevState::error)
@@ -73,6 +75,7 @@ struct Geo {
     int n[3];
     int bc[3];
     double lo[3], hi[3], L[3], inv_dx[3];
+    double rc[3];   // centre of the radial velocity moment
 };
 
 struct DevState {
@@ -80,8 +83,9 @@ struct DevState {
     uint32_t error;       // kErr* bits
     uint32_t spin_cap;    // bounded waits: polls before giving up (0: kSpinCap)
     uint32_t hold_tile1;  // test of the bounded wait: scan tile hold_tile1 - 1 never publishes its
-                          // status (0: none); set only through kmc_debug_hold_scan
-    unsigned long long pad;
+                          // status (0: none); set only through kmc_test_hold_scan
+    uint32_t steps_left;  // steps still to take in the current graph-resident step loop
+    uint32_t pad;
 };
 
 template <typename T>
@@ -114,6 +118,7 @@ struct Bufs {
     uint32_t* slot_of;       // [n] by global id: sorted position in A (written by the search);
                              // the scatter reuses it for the tags of shared search cells
     uint32_t* key;           // [n] search key of B
+    uint32_t* tagB;          // [n] tag of B[p], written with B (read coalesced by the scatter)
     uint32_t* slot;          // [n] rank of B[p] within its search cell
     uint32_t* count;         // [n_keys + 1] histogram (zero outside the step)
     uint32_t* start;         // [n_keys + 1] exclusive scan of count
@@ -121,7 +126,7 @@ struct Bufs {
     uint32_t n_keys;
     uint32_t n_tiles;
     unsigned long long* acc; // [n_bins * kAccFields] moment sums, fixed point (two's complement)
-    double* mom;             // [n_bins * 16] raw + derived
+    double* mom;             // [n_bins * kMomStride] raw, derived, radial
     double* glob;            // [n_inst * 8]
     int64_t n_bins;
     int32_t* rec_best;       // RECORD: [n] by global id
@@ -135,6 +140,7 @@ struct Bufs {
     int stage_pair_cap;      // entries of the binary32 pair list
     int any_direct;          // some instance uses the direct (per-thread) search
     int any_tiled;           // some instance uses the tile search (one block per c-bin)
+    int dsmc;                // the random-partner comparison variant instead of the PoCA search
     // particle tag = (instance << id_bits) | instance-local id
     uint32_t id_bits;        // 32 when there is one instance
     uint32_t id_mask;
@@ -167,6 +173,8 @@ template <typename T>
 cudaError_t launch_window_count(const Bufs<T>& b, unsigned long long* total, cudaStream_t s);
 template <typename T>
 cudaError_t launch_perm(const Bufs<T>& b, int32_t* perm, cudaStream_t s);
+template <typename T>
+cudaError_t launch_dsmc(const Bufs<T>& b, cudaStream_t s);     // random-partner collisions per c-bin
 template <typename T>
 cudaError_t launch_cbin_hist(const Bufs<T>& b, uint32_t* hist, unsigned long long* vmax2, cudaStream_t s);
 

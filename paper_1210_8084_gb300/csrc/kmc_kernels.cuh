@@ -111,7 +111,7 @@ __device__ __forceinline__ void sincos_2pi(double u, double* s, double* c) { sin
 // half length is +inf so the minimum-image shift never fires.
 template <typename T>
 struct GeoT {
-    T lo[3], hi[3], inv[3], L[3], hL[3];
+    T lo[3], hi[3], inv[3], L[3], hL[3], rc[3];
     int n[3];
     bool wall[3];     // no periodic wrap: reflective or absorbing
     bool absorb[3];   // absorbing: a particle that ends a step outside is removed
@@ -127,6 +127,7 @@ struct GeoT {
             wall[d] = g.bc[d] != 0;
             absorb[d] = g.bc[d] == 2;
             hL[d] = wall[d] ? R<T>::inf() : (T)0.5 * L[d];
+            rc[d] = (T)g.rc[d];
             n[d] = g.n[d];
         }
     }
@@ -275,10 +276,14 @@ __device__ __forceinline__ void warp_vmax(InstDyn* dyn, bool valid, int inst, T 
 // shared-memory slot list; after a block barrier the first slot of every
 // distinct bin adds up its duplicates and issues the global atomics.  All
 // threads of the block must call this; a lane contributes its partial sums
-// (v, v^2, W), particle count and collided count.
+// (v, v^2, W, v.r_hat), particle count and collided count.
+constexpr int kMomSums = 8;
+// accumulator index of partial sum k: Sum v (3), Sum v^2 (3), Sum W, then Sum v.r_hat after the collided count
+__device__ __forceinline__ int acc_field(int k) { return k < 7 ? 1 + k : 9; }
+
 struct MomentSlots {
     uint32_t bin[kThreads];
-    long long f[7][kThreads];
+    long long f[kMomSums][kThreads];
     int cnt[kThreads];
     int coll[kThreads];
     int n;
@@ -293,7 +298,7 @@ __device__ __forceinline__ long long fixed_of(float x, float scale) { return __f
 __device__ __forceinline__ long long fixed_of(double x, double scale) { return __double2ll_rn(x * scale); }
 
 __device__ __forceinline__ void block_moment_partials(MomentSlots& S, unsigned long long* acc, bool valid,
-                                                      uint32_t bin, const long long fl[7], int cnt_l,
+                                                      uint32_t bin, const long long fl[kMomSums], int cnt_l,
                                                       int coll_l) {
     unsigned todo = __ballot_sync(kFull, valid);
     while (todo) {
@@ -301,15 +306,15 @@ __device__ __forceinline__ void block_moment_partials(MomentSlots& S, unsigned l
         const uint32_t gb = __shfl_sync(kFull, bin, leader);
         const bool mine = valid && bin == gb;
         const unsigned grp = __ballot_sync(kFull, mine);
-        long long f[7];
+        long long f[kMomSums];
 #pragma unroll
-        for (int k = 0; k < 7; ++k) f[k] = mine ? fl[k] : 0ll;
+        for (int k = 0; k < kMomSums; ++k) f[k] = mine ? fl[k] : 0ll;
         int c = mine ? cnt_l : 0, cc = mine ? coll_l : 0;
         if (grp != (1u << leader)) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-                for (int k = 0; k < 7; ++k) f[k] += __shfl_xor_sync(kFull, f[k], o);
+                for (int k = 0; k < kMomSums; ++k) f[k] += __shfl_xor_sync(kFull, f[k], o);
             }
             c = __reduce_add_sync(kFull, (unsigned)c);
             cc = __reduce_add_sync(kFull, (unsigned)cc);
@@ -318,7 +323,7 @@ __device__ __forceinline__ void block_moment_partials(MomentSlots& S, unsigned l
             const int slot = atomicAdd(&S.n, 1);
             S.bin[slot] = gb;
 #pragma unroll
-            for (int k = 0; k < 7; ++k) S.f[k][slot] = f[k];
+            for (int k = 0; k < kMomSums; ++k) S.f[k][slot] = f[k];
             S.cnt[slot] = c;
             S.coll[slot] = cc;
         }
@@ -332,20 +337,20 @@ __device__ __forceinline__ void block_moment_partials(MomentSlots& S, unsigned l
         for (int u = 0; u < t; ++u)
             if (S.bin[u] == mb) { first = false; break; }
         if (!first) continue;
-        long long tot[7] = {0, 0, 0, 0, 0, 0, 0};
+        long long tot[kMomSums] = {0, 0, 0, 0, 0, 0, 0, 0};
         long long c = 0, cc = 0;
         for (int u = t; u < ns; ++u) {
             if (S.bin[u] != mb) continue;
 #pragma unroll
-            for (int k = 0; k < 7; ++k) tot[k] += S.f[k][u];
+            for (int k = 0; k < kMomSums; ++k) tot[k] += S.f[k][u];
             c += S.cnt[u];
             cc += S.coll[u];
         }
         unsigned long long* a = acc + (size_t)mb * kAccFields;
         atomicAdd(a + 0, (unsigned long long)c);
 #pragma unroll
-        for (int k = 0; k < 7; ++k)
-            if (tot[k]) atomicAdd(a + 1 + k, (unsigned long long)tot[k]);
+        for (int k = 0; k < kMomSums; ++k)
+            if (tot[k]) atomicAdd(a + acc_field(k), (unsigned long long)tot[k]);
         if (cc) atomicAdd(a + 8, (unsigned long long)cc);
     }
 }
@@ -423,6 +428,7 @@ __global__ void __launch_bounds__(kThreads) bin_kernel(Bufs<T> b) {
         const uint32_t slot = aggregated_increment(b.count, skey, active);
         b.key[p] = skey;
         b.slot[p] = slot;
+        b.tagB[p] = R<T>::bits(P.w);
     }
     warp_vmax<T>(b.dyn, valid && !gone, inst, speed2<T>(Q.x, Q.y, Q.z));
 }
@@ -809,9 +815,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) search_kerne
     const uint32_t tag = R<T>::bits(P.w);
     const int inst = tag_inst(b, tag);
     const InstDev& I = b.inst[inst];
+    if (I.tiled) return;   // searched, and its slot_of recorded, by the tile search
     // sorted position by id, read by the move kernel to find a partner
     b.slot_of[I.p_off + (int64_t)tag_id(b, tag)] = (uint32_t)p;
-    if (I.staged || I.tiled || absorbed(Q.w)) return;   // searched elsewhere, or gone
+    if (I.staged || absorbed(Q.w)) return;   // searched by the staged kernel, or gone
     const int* kk = b.dyn[inst].k;
     const T xi[3] = {P.x, P.y, P.z};
     const T vi[3] = {Q.x, Q.y, Q.z};
@@ -1039,6 +1046,9 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
         const T xi[3] = {P.x, P.y, P.z};
         const T vi[3] = {Q.x, Q.y, Q.z};
         const uint32_t tag = R<T>::bits(P.w);
+        // sorted position by id, read by the move kernel to find a partner (every
+        // home is visited in exactly one chunk of homes)
+        if (home) b.slot_of[I.p_off + (int64_t)tag_id(b, tag)] = (uint32_t)p;
         T bd = R<T>::inf();
         uint32_t bid = 0xffffffffu;
         // binary32: a home tests only higher positions; binary64: the whole
@@ -1770,11 +1780,15 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 1) move_kernel(
         V Pn, Qn;
         Pn.x = xn[0]; Pn.y = xn[1]; Pn.z = xn[2]; Pn.w = P.w;
         Qn.x = vn[0]; Qn.y = vn[1]; Qn.z = vn[2];
-        Qn.w = gone ? -R<T>::inf() : (paired ? W : R<T>::inf());
+        // W of the step (+inf: no collision); the random-partner variant marked its
+        // collided particles with 0 (point collisions carry no virial)
+        const bool hit = paired || (b.dsmc && Q.w == (T)0);
+        Qn.w = gone ? -R<T>::inf() : (hit ? W : R<T>::inf());
         b.posB[p] = Pn;
         b.velB[p] = Qn;
         b.key[p] = skey;
         b.slot[p] = slot;
+        b.tagB[p] = tag;
         if (b.record) {
             const int64_t gid = I.p_off + (int64_t)tag_id(b, tag);
             b.rec_best[gid] = (kp != kNoPartner) ? (int32_t)tag_id(b, tagj) : -1;
@@ -1804,7 +1818,23 @@ __global__ void __launch_bounds__(kThreads) scatter_tags_kernel(Bufs<T> b) {
     if (s1 <= s0 + 1u || s1 - s0 > kCanonMax) return;
     const uint32_t dst = s0 + b.slot[p];
     if (dst >= s1 || dst >= (uint32_t)b.n) return;   // only after a failed scan (flagged by the scatter)
-    b.slot_of[dst] = R<T>::bits(b.posB[p].w);
+    b.slot_of[dst] = b.tagB[p];
+}
+
+// Tags of [q, q1) below `tag`: scalar up to a 16-byte boundary, then four per load.
+__device__ __forceinline__ uint32_t tags_below(const uint32_t* __restrict__ t, uint32_t q, uint32_t q1,
+                                               uint32_t tag) {
+    uint32_t r = 0;
+    for (; q < q1 && (q & 3u); ++q) r += t[q] < tag ? 1u : 0u;
+    const uint4* t4 = reinterpret_cast<const uint4*>(t + q);
+    const uint32_t n4 = (q1 - q) >> 2;
+#pragma unroll 4
+    for (uint32_t i = 0; i < n4; ++i) {
+        const uint4 v = t4[i];
+        r += (v.x < tag ? 1u : 0u) + (v.y < tag ? 1u : 0u) + (v.z < tag ? 1u : 0u) + (v.w < tag ? 1u : 0u);
+    }
+    for (q += n4 << 2; q < q1; ++q) r += t[q] < tag ? 1u : 0u;
+    return r;
 }
 
 template <typename T>
@@ -1816,12 +1846,8 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(Bufs<T> b) {
     uint32_t rank = b.slot[p];
     if (k < b.n_keys) {
         const uint32_t s1 = b.start[k + 1];
-        if (s1 > s0 + 1u && s1 - s0 <= kCanonMax && s1 <= (uint32_t)b.n) {
-            const uint32_t tag = R<T>::bits(b.posB[p].w);
-            uint32_t r = 0;
-            for (uint32_t q = s0; q < s1; ++q) r += b.slot_of[q] < tag ? 1u : 0u;
-            rank = r;
-        }
+        if (s1 > s0 + 1u && s1 - s0 <= kCanonMax && s1 <= (uint32_t)b.n)
+            rank = tags_below(b.slot_of, s0, s1, b.tagB[p]);
     }
     const uint32_t dst = s0 + rank;
     if (dst >= (uint32_t)b.n) {  // only after a failed scan; reported as a device error
@@ -1841,6 +1867,97 @@ __global__ void __launch_bounds__(kThreads) perm_kernel(Bufs<T> b, int32_t* __re
     if (p >= b.n) return;
     const uint32_t tag = R<T>::bits(b.posA[p].w);
     perm[p] = (int32_t)(b.inst[tag_inst(b, tag)].p_off + (int64_t)tag_id(b, tag));
+}
+
+// ------------------------------------------------------------ DSMC variant
+// The classic random-partner collisions the paper contrasts with PoCA (Sect.
+// "Direct Simulation Monte Carlo Technique"), in Bird's no-time-counter form:
+// collision cells are the c-bins (the search grid of a DSMC handle is the
+// c-bins, so a cell is one contiguous range of A, its particles in id order).
+// Per cell of N >= 2 particles: M = floor(1/2 N (N - 1) sigma g_max dt / V_c
+// + u_0) candidate pairs, sigma = pi R^2 (Eq. 7), g_max = 2 v_max; candidate k
+// takes positions i != j of the cell from Philox (cell, step, k, kDsmcPairTag)
+// and is accepted when u g_max < g = |v_i - v_j|; an accepted pair scatters
+// isotropically in its CM frame with the direction from (cell, step, k,
+// kDsmcDirTag).  Candidates are applied one after another by one thread per
+// cell; arithmetic in binary64 in a fixed order, new velocities stored in the
+// state precision after every collision, collided particles marked with
+// vel.w = 0 for the move and the moments.
+constexpr uint32_t kDsmcPairTag = 0x44534D43u;
+constexpr uint32_t kDsmcDirTag = 0x44534D44u;
+
+__device__ __forceinline__ double uniform53(uint32_t hi, uint32_t lo) {
+    const unsigned long long m = ((unsigned long long)hi << 20) | (unsigned long long)(lo >> 12);
+    return (double)(2ull * m + 1ull) * 0x1p-53;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) dsmc_kernel(Bufs<T> b) {
+    using V = typename Vec4<T>::type;
+    const int64_t kc64 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (kc64 >= (int64_t)b.n_keys) return;
+    const uint32_t kc = (uint32_t)kc64;
+    const uint32_t nmax = (uint32_t)b.n;
+    const uint32_t s0 = min(b.start[kc], nmax), s1 = min(b.start[kc + 1], nmax);
+    if (s1 <= s0) return;
+    for (uint32_t q = s0; q < s1; ++q) b.velA[q].w = R<T>::inf();   // not collided (yet)
+    const uint32_t N = s1 - s0;
+    if (N < 2) return;
+    int lo = 0, hi = b.n_inst - 1;   // instance of the cell (consecutive key ranges)
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.inst[mid].key_base <= kc) lo = mid;
+        else hi = mid - 1;
+    }
+    const InstDev& I = b.inst[lo];
+    const InstDyn& D = b.dyn[lo];
+    const uint32_t cell = kc - I.key_base;
+    const uint32_t step = b.st->step;
+    const double gmax = __dmul_rn(2.0, __dsqrt_rn(__longlong_as_double((long long)D.vmax2_cur)));
+    const double sigma = __dmul_rn(M_PI, I.R2);
+    double Vc = 1.0;
+    for (int d = 0; d < b.geo.dim; ++d) Vc = __dmul_rn(Vc, __ddiv_rn(b.geo.L[d], (double)b.geo.n[d]));
+    const double Nd = (double)N;
+    double m = __dmul_rn(__dmul_rn(0.5, Nd), __dsub_rn(Nd, 1.0));
+    m = __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(m, sigma), gmax), D.dt), Vc);
+    uint4 w = philox4x32_10(make_uint4(cell, step, 0xFFFFFFFFu, kDsmcPairTag), I.seed_lo, I.seed_hi);
+    m = floor(__dadd_rn(m, uniform53(w.x, w.y)));
+    const uint32_t M = m > 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)m;
+    V* vel = b.velA + s0;
+    for (uint32_t k = 0; k < M; ++k) {
+        w = philox4x32_10(make_uint4(cell, step, k, kDsmcPairTag), I.seed_lo, I.seed_hi);
+        const uint32_t pi = (uint32_t)(((unsigned long long)w.x * (unsigned long long)N) >> 32);
+        uint32_t pj = (uint32_t)(((unsigned long long)w.y * (unsigned long long)(N - 1u)) >> 32);
+        if (pj >= pi) pj += 1u;
+        V A = vel[pi], B = vel[pj];
+        const double va[3] = {(double)A.x, (double)A.y, (double)A.z};
+        const double vb[3] = {(double)B.x, (double)B.y, (double)B.z};
+        const double d0 = __dsub_rn(va[0], vb[0]), d1 = __dsub_rn(va[1], vb[1]), d2 = __dsub_rn(va[2], vb[2]);
+        const double g = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2)));
+        if (!(__dmul_rn(uniform53(w.z, w.w), gmax) < g)) continue;
+        w = philox4x32_10(make_uint4(cell, step, k, kDsmcDirTag), I.seed_lo, I.seed_hi);
+        const double u1 = uniform53(w.x, w.y), u2 = uniform53(w.z, w.w);
+        double sphi, cphi;
+        sincospi(__dmul_rn(2.0, u2), &sphi, &cphi);
+        const double cth = __dsub_rn(1.0, __dmul_rn(2.0, u1));
+        const double sth = __dmul_rn(2.0, __dsqrt_rn(__dmul_rn(u1, __dsub_rn(1.0, u1))));
+        const bool plane = b.geo.vdim == 2;
+        const double nh[3] = {plane ? cphi : __dmul_rn(sth, cphi), plane ? sphi : __dmul_rn(sth, sphi),
+                              plane ? 0.0 : cth};
+        const double h = __dmul_rn(0.5, g);
+        double na[3], nb[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const double vcm = __dmul_rn(0.5, __dadd_rn(va[d], vb[d]));
+            const double t = __dmul_rn(h, nh[d]);
+            na[d] = __dadd_rn(vcm, t);
+            nb[d] = __dsub_rn(vcm, t);
+        }
+        A.x = (T)na[0]; A.y = (T)na[1]; A.z = (T)na[2]; A.w = (T)0;
+        B.x = (T)nb[0]; B.y = (T)nb[1]; B.z = (T)nb[2]; B.w = (T)0;
+        vel[pi] = A;
+        vel[pj] = B;
+    }
 }
 
 // State of A in id order.
@@ -1903,7 +2020,7 @@ __global__ void __launch_bounds__(kThreads) moments_kernel(Bufs<T> b, int use_vi
     __syncthreads();
     const int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kMomItems;
     uint32_t cur = 0xffffffffu;
-    long long f[7] = {0, 0, 0, 0, 0, 0, 0};
+    long long f[kMomSums] = {0, 0, 0, 0, 0, 0, 0, 0};
     int cnt = 0, coll = 0;
     V Ps[kMomItems], Qs[kMomItems];   // all loads in flight before the sums
 #pragma unroll
@@ -1937,10 +2054,10 @@ __global__ void __launch_bounds__(kThreads) moments_kernel(Bufs<T> b, int use_vi
             unsigned long long* a = b.acc + (size_t)cur * kAccFields;
             atomicAdd(a + 0, (unsigned long long)cnt);
 #pragma unroll
-            for (int q = 0; q < 7; ++q) atomicAdd(a + 1 + q, (unsigned long long)f[q]);
+            for (int q = 0; q < kMomSums; ++q) atomicAdd(a + acc_field(q), (unsigned long long)f[q]);
             if (coll) atomicAdd(a + 8, (unsigned long long)coll);
 #pragma unroll
-            for (int q = 0; q < 7; ++q) f[q] = 0ll;
+            for (int q = 0; q < kMomSums; ++q) f[q] = 0ll;
             cnt = coll = 0;
         }
         cur = bin;
@@ -1948,6 +2065,19 @@ __global__ void __launch_bounds__(kThreads) moments_kernel(Bufs<T> b, int use_vi
         f[0] += fixed_of(Q.x, sv); f[1] += fixed_of(Q.y, sv); f[2] += fixed_of(Q.z, sv);
         f[3] += fixed_of(Q.x * Q.x, s2); f[4] += fixed_of(Q.y * Q.y, s2); f[5] += fixed_of(Q.z * Q.z, s2);
         if (collided) f[6] += fixed_of(Q.w, sw);
+        // radial velocity (Eq. vel_r): v . r_hat, r_hat from the configured centre
+        // over the position dimensions (0 at the centre itself); |v . r_hat| <= v_max
+        {
+            const T v3[3] = {Q.x, Q.y, Q.z};
+            T r2 = (T)0, vd = (T)0;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                const T dx = x[d] - G.rc[d];
+                r2 += dx * dx;
+                vd += v3[d] * dx;
+            }
+            if (r2 > (T)0) f[7] += fixed_of(vd / R<T>::sqrt_(r2), sv);
+        }
         cnt += 1;
         coll += collided ? 1 : 0;
     }
@@ -2079,8 +2209,9 @@ cudaError_t launch_search(const Bufs<T>& b, cudaStream_t s) {
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    // always launched: besides the direct search it records slot_of for every particle
-    KMC_DIM_DISPATCH(b.geo.dim, search_kernel, b);
+    // besides the direct search it records slot_of for the particles of every
+    // instance that is not tiled (staged ones included)
+    if (b.any_direct || b.n_stage_tiles > 0) KMC_DIM_DISPATCH(b.geo.dim, search_kernel, b);
     return cudaGetLastError();
 }
 
@@ -2110,6 +2241,13 @@ cudaError_t launch_scatter(const Bufs<T>& b, cudaStream_t s) {
     if (b.n == 0) return cudaSuccess;
     scatter_tags_kernel<T><<<blocks_for(b.n), kThreads, 0, s>>>(b);
     scatter_kernel<T><<<blocks_for(b.n), kThreads, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dsmc(const Bufs<T>& b, cudaStream_t s) {
+    if (b.n == 0 || b.n_keys == 0) return cudaSuccess;
+    dsmc_kernel<T><<<(unsigned)((b.n_keys + kThreads - 1) / kThreads), kThreads, 0, s>>>(b);
     return cudaGetLastError();
 }
 
@@ -2172,6 +2310,7 @@ cudaError_t launch_window_count(const Bufs<T>& b, unsigned long long* total, cud
     template cudaError_t launch_moments<T>(const Bufs<T>&, int, cudaStream_t);                     \
     template cudaError_t launch_cbin_hist<T>(const Bufs<T>&, uint32_t*, unsigned long long*, cudaStream_t); \
     template cudaError_t launch_window_count<T>(const Bufs<T>&, unsigned long long*, cudaStream_t);   \
-    template cudaError_t launch_perm<T>(const Bufs<T>&, int32_t*, cudaStream_t);
+    template cudaError_t launch_perm<T>(const Bufs<T>&, int32_t*, cudaStream_t);                   \
+    template cudaError_t launch_dsmc<T>(const Bufs<T>&, cudaStream_t);
 
 }  // namespace kmc

@@ -136,6 +136,7 @@ int run(const kmc_config* cfg, int64_t n, const void* pos, const void* vel, int3
     b.slot_of = (uint32_t*)take(nv * sizeof(uint32_t));
     b.key = (uint32_t*)take(nv * sizeof(uint32_t));
     b.slot = (uint32_t*)take(nv * sizeof(uint32_t));
+    b.tagB = (uint32_t*)take(nv * sizeof(uint32_t));
     b.count = (uint32_t*)take((size_t)n_tiles * kScanTile * sizeof(uint32_t));
     b.start = (uint32_t*)take((size_t)n_tiles * kScanTile * sizeof(uint32_t));
     b.scan_status = (unsigned long long*)take((1 + (size_t)n_tiles) * sizeof(unsigned long long));
@@ -181,7 +182,7 @@ extern "C" KMC_API int kmc_find_partners_noalloc(const kmc_config* cfg, int64_t 
     if (cfg->sigma > 0 && !isfinite(cfg->sigma)) return KMC_EINVAL;
     if (cfg->flags & ~(KMC_FLAG_RECORD | KMC_FLAG_NO_GRAPH | KMC_FLAG_STAGED_SEARCH | KMC_FLAG_NO_TILE_SEARCH |
                        KMC_FLAG_ADAPTIVE_DT | KMC_FLAG_VELOCITY_2D))
-        return KMC_EINVAL;
+        return KMC_EINVAL;   // KMC_FLAG_DSMC included: that variant has no closest candidates
     if ((cfg->flags & KMC_FLAG_VELOCITY_2D) && cfg->dim_pos != 2) return KMC_EINVAL;
     for (int d = 0; d < cfg->dim_pos; ++d) {
         if (cfg->n_cells[d] < 1 || !(cfg->hi[d] > cfg->lo[d])) return KMC_EINVAL;

@@ -207,8 +207,8 @@ __global__ void __launch_bounds__(256) finalize_bins_kernel(const InstDev* __res
     if (valid) {
         const InstDyn& D = dyn[i];
         const unsigned long long* a = acc + bidx * kAccFields;
-        unsigned long long ai[9];
-        for (int k = 0; k < 9; ++k) ai[k] = a[k];
+        unsigned long long ai[kAccFields];
+        for (int k = 0; k < kAccFields; ++k) ai[k] = a[k];
         t[0] = ai[0];
         t[1] = ai[4] + ai[5] + ai[6];
         t[2] = ai[1];
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(256) finalize_bins_kernel(const InstDev* __res
         t[4] = ai[3];
         t[5] = ai[7];
         t[6] = ai[8];
-        double* o = mom + bidx * 16;
+        double* o = mom + bidx * kMomStride;
         double r[8];
         r[0] = (double)(long long)ai[0];
         for (int k = 1; k <= 3; ++k) r[k] = unfix(ai[k], D.mom_e[0]);
@@ -226,6 +226,9 @@ __global__ void __launch_bounds__(256) finalize_bins_kernel(const InstDev* __res
         double Vc = 1.0;
         for (int d = 0; d < geo.dim; ++d) Vc *= geo.L[d] / (double)geo.n[d];
         const double N = r[0];
+        const double svr = unfix(ai[9], D.mom_e[0]);
+        o[16] = svr;
+        o[17] = N > 0.0 ? svr / N : 0.0;   // Eq. vel_r
         if (N <= 0.0) {
             for (int k = 8; k < 16; ++k) o[k] = 0.0;
         } else {

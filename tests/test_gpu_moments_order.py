@@ -13,9 +13,10 @@ binary64.  Bounds used below, per c-bin b with N_b particles:
              binary32 path (the device squares in binary32);
   * Sum W (collisional virial, Eq. stress): the device evaluates r_ij(t_poca)
     . dp_i in the state precision from the same state; its error is a few
-    units of rounding of the separation times |dp|, bounded here by
-    1e-6 (binary32) or 1e-14 (binary64) x reach x Sum |v' - v| over the bin's
-    collided particles, reach = R + 2 v_max dt.
+    units of rounding of the separation times |dp| and of dp times the
+    separation, bounded here by 1e-6 (binary32) or 1e-13 (binary64) x reach x
+    Sum (|v' - v| + |v| + |v'|) over the bin's collided particles, reach =
+    R + 2 v_max dt.
 """
 import math
 
@@ -173,8 +174,11 @@ def test_moments_after_one_step_match_oracle(geom, prec):
     assert coll.sum() > n // 20
     Vc = float(np.prod([(hi[d] - lo[d]) / n_cells[d] for d in range(dim)]))
     reach = math.sqrt(P.R2) + 2 * np.linalg.norm(vel, axis=1).max() * dt
-    dvel = np.where(coll, np.linalg.norm(vo - vel, axis=1), 0.0)
-    rel_w = 1e-6 if prec == 32 else 1e-14
+    # scale of a collided particle's W: its velocity change and both speeds (the
+    # rounding of v' is relative to the speeds, that of r_ij(t_poca) to the reach)
+    dvel = np.where(coll, np.linalg.norm(vo - vel, axis=1) + np.linalg.norm(vo, axis=1)
+                    + np.linalg.norm(vel, axis=1), 0.0)
+    rel_w = 1e-6 if prec == 32 else 1e-13
 
     # (a) the reduction on the device's own end state
     raw_a, der_a, _ = oracle.moments(P, p_d, v_d, W)
@@ -345,6 +349,8 @@ def test_bounded_scan_wait_times_out_and_recovers():
     import paper_1210_8084_gb300 as k
     pos, vel = _state("slab", 32)
     cfg = _config(k, "slab", 32)
+    for d, s in enumerate((1, 40, 40)):   # 96,000 search cells: many scan tiles
+        cfg.sub_cells[d] = s
     sim = k.Simulation(cfg, pos, vel)
     info = sim.info()
     assert info.n_scan_tiles >= 3
@@ -366,3 +372,46 @@ def test_bounded_scan_wait_times_out_and_recovers():
     ref.close()
     assert np.array_equal(p_a, p_b) and np.array_equal(v_a, v_b)
     assert np.array_equal(raw_a, raw_b)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_radial_velocity_matches_oracle(prec, dim):
+    """KMC_MOM_RADIAL (Eq. vel_r) after one step of a Noh inflow, about the
+    corner the gas falls towards and about an off-corner centre: per c-bin
+    Sum v . r_hat within the fixed-point bound plus the rounding of r_hat in the
+    state precision (2^-20 or 2^-48 of Sum |v|), and v_r = Sum / N."""
+    _setup()
+    import oracle
+    import paper_1210_8084_gb300 as k
+    from paper_1210_8084_gb300 import inputs
+    n, nc = 40_000, (16, 16, 16) if dim == 3 else (40, 40, 1)
+    lo, hi, bc = (0, 0, 0), (1, 1, 1), (WALL, WALL, WALL)
+    pos, vel = inputs.noh(n, seed=9, dim_pos=dim, v0=1.0, T0=0.01)
+    if prec == 32:
+        pos, vel = inputs.cast_state(pos, vel, np.float32, lo, hi, bc)
+    pos, vel = pos.astype(np.float64), vel.astype(np.float64)
+    for center in ((0.0, 0.0, 0.0), (0.3, 0.45, 0.55)):
+        cfg = k.make_config(dim_pos=dim, n_cells=nc, lo=lo, hi=hi, bc=bc, lam=1e-3, dt=0.01, seed=2, precision=prec,
+                            radial_center=center)
+        sim = k.Simulation(cfg, pos, vel)
+        sim.step(1, want_moments=1)
+        p1, v1 = sim.state()
+        rad = sim.radial()
+        raw = sim.moments()[0]
+        sim.close()
+        p1, v1 = p1.astype(np.float64), v1.astype(np.float64)
+        P = oracle.make_params(dim, nc, lo, hi, bc, R2=_oracle_R2(1e-3, n, dim, lo, hi), dt=0.01, seed=2,
+                               decide32=prec == 32)
+        ro = oracle.radial(P, p1, v1, center)
+        N = raw[:, 0]
+        vmax = np.linalg.norm(v1, axis=1).max() * (1 + 1e-6)
+        abs_v = _bin_sum(P, p1, v1, np.linalg.norm(v1, axis=1))
+        tol = N * n * vmax * 2.0 ** -61 + (2.0 ** -20 if prec == 32 else 2.0 ** -48) * abs_v
+        assert np.all(np.abs(rad[:, 0] - ro[:, 0]) <= tol), center
+        ok = N > 0
+        assert np.all(np.abs(rad[ok, 1] - ro[ok, 1]) <= tol[ok] / N[ok] + 1e-15)
+        assert np.all(rad[~ok] == 0)
+        if center[0] == 0.0:
+            # the cold inflow towards the corner: v_r close to -v0 away from the corner
+            assert np.median(rad[ok, 1]) < -0.8

@@ -562,3 +562,83 @@ def test_absorbing_walls_match_oracle(prec):
         assert glob[0, 0] == np.isfinite(p1[:, 0]).sum()
     assert np.isnan(p1[:, 0]).sum() > 1000
     sim.close()
+
+
+def test_graph_resident_step_loop_equals_kernel_by_kernel():
+    """kmc_step runs all its steps in one CUDA graph (a conditional while node
+    driven by a device-side step counter).  Calls of 3 + 4 steps, one of 7, and
+    7 steps launched kernel by kernel (KMC_FLAG_NO_GRAPH) give the same state,
+    moments and step counter bit for bit; a batched handle too."""
+    _setup()
+    import paper_1210_8084_gb300 as k
+    from paper_1210_8084_gb300 import inputs
+    pos, vel = f32_state(*inputs.sod_tube(80_000, seed=31), (0, 0, 0), (1, 1, 1), (WALL, PER, PER))
+    base = dict(dim_pos=3, n_cells=(80, 1, 1), bc=(WALL, PER, PER), lam=1e-3, dt=0.2 / 80, seed=17, precision=32)
+    insts = [dict(n=30_000, lam=1e-3, dt=0.0025, seed=1), dict(n=50_000, lam=1e-2, dt=0.0025, seed=2)]
+    for kw in (base, dict(dim_pos=3, n_cells=(80, 1, 1), bc=(WALL, PER, PER), precision=32, instances=insts)):
+        out = []
+        for flags, calls in ((0, (3, 4)), (0, (7,)), (k.KMC_FLAG_NO_GRAPH, (7,))):
+            sim = k.Simulation(k.make_config(**kw, flags=flags), pos, vel)
+            for c in calls:
+                sim.step(c, want_moments=1)
+            info = sim.info()
+            assert info.step == 7
+            assert info.graph_mode == (0 if flags else 2)
+            out.append((sim.state(), sim.moments()))
+            sim.close()
+        for (s, m) in out[1:]:
+            assert np.array_equal(s[0], out[0][0][0]) and np.array_equal(s[1], out[0][0][1])
+            for a, b in zip(m, out[0][1]):
+                assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_dsmc_variant_matches_oracle(prec, dim):
+    """KMC_FLAG_DSMC, the random-partner comparison variant (Sect. "Direct
+    Simulation Monte Carlo Technique", Bird's no-time-counter scheme): two
+    steps from the same state on both sides.  The collisions are computed in
+    binary64 on both sides from the same draws, the cell's particles in id
+    order, so the accepted pairs are the same: the number of collided
+    particles matches exactly and the end velocities agree to 1e-12 (binary64)
+    or to one binary32 rounding (binary32, most of them bit for bit)."""
+    _setup()
+    import oracle
+    import paper_1210_8084_gb300 as k
+    from paper_1210_8084_gb300 import inputs
+    if dim == 3:
+        n, n_cells, lo, hi, bc = 60_000, (60, 1, 1), (0, 0, 0), (1, 1, 1), (WALL, PER, PER)
+        pos, vel = inputs.sod_tube(n, seed=13)
+        lam, dt = 1e-3, 0.2 / 60
+    else:
+        n, n_cells, lo, hi, bc = 40_000, (20, 20, 1), (0, 0, 0), (1, 1, 1), (WALL, WALL, PER)
+        pos, vel = inputs.sod_tube(n, seed=13, dim_pos=2, vel_dim=2)
+        lam, dt = 1e-3, 0.2 / 20
+    if prec == 32:
+        pos, vel = f32_state(pos, vel, lo, hi, bc)
+    flags = k.KMC_FLAG_DSMC | (k.KMC_FLAG_VELOCITY_2D if dim == 2 else 0)
+    cfg = k.make_config(dim_pos=dim, n_cells=n_cells, lo=lo, hi=hi, bc=bc, lam=lam, dt=dt, seed=23, precision=prec,
+                        flags=flags)
+    sim = k.Simulation(cfg, pos, vel)
+    assert list(sim.info().sub_cells)[:dim] == [1] * dim
+    P = oracle.make_params(dim, n_cells, lo, hi, bc, R2=oracle_R2(lam, n, dim, lo, hi), dt=dt, seed=23,
+                           decide32=prec == 32, vel_dim=dim)
+    p, v = pos, vel
+    for s in range(2):
+        sim.step(1, want_moments=1)
+        pd, vd = sim.state()
+        glob = sim.moments()[2]
+        P.step = s
+        p, v, collided, acc = oracle.dsmc_step(P, p, v)
+        assert acc > n // 50
+        assert glob[0, 6] * 2 == collided.sum(), (s, glob[0, 6] * 2, collided.sum())
+        scale = np.linalg.norm(v, axis=1)[:, None] + 1e-300
+        err = np.abs(vd - v) / scale
+        if prec == 64:
+            assert err.max() <= 1e-12, (s, err.max())
+        else:
+            assert err.max() <= 2.0 ** -22 and (err == 0).mean() > 0.999, (s, err.max(), (err == 0).mean())
+        tol_x = 1e-12 if prec == 64 else 4e-6
+        assert np.abs(pd[:, :dim] - p[:, :dim]).max() <= tol_x
+        p, v = pd.astype(np.float64), vd.astype(np.float64)   # the next step from the device state
+    sim.close()

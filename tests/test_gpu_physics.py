@@ -271,6 +271,42 @@ def test_ensemble_means_match_oracle_fp32_config1_reduction():
     assert np.abs(fc[:, 3] - fc[:, 0] * fc[:, 2]).max() > 0
 
 
+def test_dsmc_variant_against_exact_riemann_and_poca():
+    """The random-partner comparison variant (KMC_FLAG_DSMC; Sect. "Direct
+    Simulation Monte Carlo Technique") and the paper's method on the same slab
+    Sod tube (4M particles, 2000 c-bins, lambda/L = 1e-3, t = 0.1): relative L1
+    of n, p, T against the exact Riemann solution for both.  With collision
+    cells half a mean free path wide the random-partner scheme is a consistent
+    Boltzmann solver here; the slab geometry penalises the closest-approach
+    search (its candidates lie mostly beside a particle, design notes R19).
+    The numbers are printed; the bounds guard both."""
+    _setup()
+    import paper_1210_8084_gb300 as k
+    from paper_1210_8084_gb300 import inputs
+    from analytic import riemann
+    n, nc, lam = 4_000_000, 2000, 1e-3
+    dt = 0.2 / nc
+    steps = int(round(0.1 / dt))
+    pos, vel = inputs.cast_state(*inputs.sod_tube(n, seed=77), np.float32, (0, 0, 0), (1, 1, 1), (WALL, PER, PER))
+    nb = 200
+    ex = riemann.sod_profile(np.linspace(0, 1, nb + 1), steps * dt, 0.5, 1.0, 1.0)
+    out = {}
+    for name, flags in (("dsmc", k.KMC_FLAG_DSMC), ("poca", 0)):
+        sim = k.Simulation(k.make_config(dim_pos=3, n_cells=(nc, 1, 1), bc=(WALL, PER, PER), lam=lam, dt=dt, seed=5,
+                                         precision=32, flags=flags), pos, vel)
+        e0 = sim.moments()[2][0, 1]
+        sim.step(steps, want_moments=1)
+        raw, _, glob = sim.moments()
+        sim.close()
+        dn, u, pp, T = _profiles(raw, nb, n * 8 / 9 / 0.5)
+        out[name] = [float(np.abs(q - qe).sum() / np.abs(qe).sum()) for q, qe in ((dn, ex[:, 0]), (pp, ex[:, 2]),
+                                                                                (T, ex[:, 3]))]
+        assert abs(glob[0, 1] / e0 - 1) < 1e-5
+        print(name, "L1 n, p, T:", ["%.4f" % x for x in out[name]])
+    assert max(out["dsmc"]) < 0.03, out
+    assert max(out["poca"]) < 0.065, out
+
+
 def test_mono_energetic_gas_relaxes_to_maxwell_on_device():
     _setup()
     from scipy import stats
@@ -312,6 +348,7 @@ def test_noh_spherical_implosion_against_exact_solution():
     e0 = sim.moments()[2][0, 1]
     sim.step(steps, want_moments=1)
     raw, der, glob = sim.moments()
+    rad = sim.radial()   # Eq. vel_r about the corner the gas falls towards
     sim.close()
     t = steps * dt
     g = 5.0 / 3.0
@@ -333,6 +370,12 @@ def test_noh_spherical_implosion_against_exact_solution():
     assert abs(n_in / n0 / noh.shocked_density(1.0, g, 3) - 1) < 0.15
     assert abs(T_in / ((g - 1) * 0.5 * v0 ** 2) - 1) < 0.15
     assert abs(n_ahead - 1) < 0.1
+    # radial velocity (Eq. vel_r): at rest inside the shock, -v0 in the infall ahead of it
+    vr_in = rad[inner, 0].sum() / N[inner].sum()
+    vr_ahead = rad[ahead, 0].sum() / N[ahead].sum()
+    print(f"Noh: v_r inside {vr_in:.4f} (0), ahead {vr_ahead:.4f} ({-v0})")
+    assert abs(vr_in) < 0.05 * v0
+    assert abs(vr_ahead / -v0 - 1) < 0.05
     # shock position: the density falls below half of the plateau between 0.8 and 1.25 r_s
     shells = np.linspace(0.0, 2 * rs, 41)
     idx = np.digitize(r, shells) - 1
@@ -461,6 +504,7 @@ def test_noh_cylindrical_2d_reaches_nine_times_n0():
                                      flags=k.KMC_FLAG_VELOCITY_2D), pos, vel)
     sim.step(steps, want_moments=1)
     raw = sim.moments()[0]
+    rad = sim.radial()   # Eq. vel_r about the corner (the cylinder axis)
     sim.close()
     t = steps * dt
     g = 2.0
@@ -481,3 +525,8 @@ def test_noh_cylindrical_2d_reaches_nine_times_n0():
     assert abs(n_in / noh.shocked_density(1.0, g, 2) - 1) < 0.1
     assert abs(T_in / ((g - 1) * 0.5 * v0 ** 2) - 1) < 0.1
     assert abs(n_ahead - 1) < 0.05
+    vr_in = rad[inner, 0].sum() / N[inner].sum()
+    vr_ahead = rad[ahead, 0].sum() / N[ahead].sum()
+    print(f"Noh 2-D: v_r inside {vr_in:.4f} (0), ahead {vr_ahead:.4f} ({-v0})")
+    assert abs(vr_in) < 0.05 * v0
+    assert abs(vr_ahead / -v0 - 1) < 0.05

@@ -711,3 +711,92 @@ def test_virial_pressure_of_one_hand_placed_pair(dim):
         assert der[0, 7] == pytest.approx(der[0, 5] + der[0, 6], rel=1e-14)
         seen += abs(n_hat[1]) > 0.1
     assert seen >= 2   # the draws give outgoing directions with a real y component
+
+
+def test_radial_velocity_closed_forms():
+    """Eq. vel_r, v_r = (1/N) Sum v . r_hat: a cold radial inflow -v0 r_hat
+    gives v_r = -v0 in every occupied c-bin; a rigid rotation about the centre
+    gives 0; one hand-placed particle gives v . r / |r| over the position
+    dimensions only (z ignored in 2-D)."""
+    c = np.array([0.2, 0.3, 0.6])
+    P = params(dim=3, n_cells=(4, 4, 4), bc=(1, 1, 1))
+    g = np.random.default_rng(5)
+    pos = g.random((5000, 3))
+    r = pos - c
+    rhat = r / np.linalg.norm(r, axis=1, keepdims=True)
+    out = oracle.radial(P, pos, -2.5 * rhat, c)
+    occ = oracle.moments(P, pos, rhat)[0][:, 0] > 0
+    assert np.allclose(out[occ, 1], -2.5, rtol=0, atol=1e-13)
+    assert np.allclose(out[occ, 0], -2.5 * oracle.moments(P, pos, rhat)[0][occ, 0], rtol=1e-13)
+    omega = np.array([0.3, -1.1, 0.7])
+    out = oracle.radial(P, pos, np.cross(omega, r), c)
+    assert np.abs(out[:, 1]).max() < 1e-13
+    P2 = params(dim=2, n_cells=(2, 2, 1), bc=(1, 1, 0))
+    one = oracle.radial(P2, np.array([[0.3, 0.8, 0.9]]), np.array([[1.0, 2.0, 3.0]]), np.array([0.1, 0.4, 0.0]))
+    key, _ = oracle.cell_keys(P2, np.array([[0.3, 0.8, 0.9]]))
+    assert one[key[0], 1] == pytest.approx((0.2 * 1.0 + 0.4 * 2.0) / math.sqrt(0.2 ** 2 + 0.4 ** 2), rel=1e-15)
+    assert np.count_nonzero(one[:, 0]) == 1
+
+
+# ------------------------------------------------- DSMC comparison variant
+
+def _dsmc_params(n, nc=(8, 8, 8), lam=1e-2, dt=2e-3, T=1.0, seed=4, dim=3):
+    P = params(dim=dim, n_cells=nc, bc=(0, 0, 0), R2=oracle.contact_R2(lam, 0, n), dt=dt, seed=seed)
+    pos, vel = inputs.periodic_box(n, seed=seed, T=T)
+    return P, pos, vel
+
+
+def test_dsmc_collisions_conserve_momentum_and_energy():
+    """Every accepted pair of the random-partner variant scatters in its CM
+    frame: total momentum and kinetic energy of the box are unchanged (to
+    rounding), and particles that took part have new velocities."""
+    P, pos, vel = _dsmc_params(30_000)
+    v, collided, acc = oracle.dsmc_collide(P, pos, vel)
+    assert acc > 1000
+    assert np.abs(v.sum(0) - vel.sum(0)).max() < 1e-10
+    assert abs((v * v).sum() / (vel * vel).sum() - 1) < 1e-13
+    assert np.all((v != vel).any(1) == (collided == 1))
+
+
+def test_dsmc_collision_rate_is_the_kinetic_rate():
+    """Bird's no-time-counter scheme accepts, per c-bin and step, on average
+    1/2 N (N - 1) sigma <g> dt / V_c pairs (<g> the mean relative speed of the
+    cell's pairs), i.e. a collision frequency n sigma <g> per particle pair
+    density; sigma from Eq. 7.  Summed over the c-bins of a homogeneous box and
+    several steps, the accepted count agrees with the brute-force expectation
+    within 4 Poisson standard deviations."""
+    P, pos, vel = _dsmc_params(6_000, nc=(4, 4, 4), lam=0.02, dt=1.5e-3)
+    key, _ = oracle.cell_keys(P, pos)
+    sigma = math.pi * P.R2
+    Vc = 1.0 / 64
+    expect, got = 0.0, 0
+    p, v = pos, vel
+    for step in range(6):
+        P.step = step
+        for c in range(64):
+            vc = v[key == c]
+            N = len(vc)
+            g = np.linalg.norm(vc[:, None, :] - vc[None, :, :], axis=2)
+            mean_g = g.sum() / (N * (N - 1))
+            expect += 0.5 * N * (N - 1) * sigma * mean_g * P.dt / Vc
+        v, collided, acc = oracle.dsmc_collide(P, p, v)
+        got += acc
+    assert expect > 2000
+    assert abs(got - expect) < 4 * math.sqrt(expect), (got, expect)
+
+
+def test_dsmc_mono_energetic_gas_relaxes_to_maxwell():
+    """A gas with one speed relaxes under the random-partner collisions to the
+    Maxwell speed law at T = v_in^2 / 3 (Kolmogorov-Smirnov)."""
+    from scipy import stats
+    n = 20_000
+    P = params(dim=3, n_cells=(6, 6, 6), bc=(0, 0, 0), R2=oracle.contact_R2(1e-2, 0, n), dt=5e-3, seed=8)
+    pos, vel = inputs.periodic_box(n, seed=8, v_in=1.0)
+    p, v = pos, vel
+    for step in range(40):
+        P.step = step
+        p, v, collided, acc = oracle.dsmc_step(P, p, v)
+    s = np.linalg.norm(v, axis=1)
+    T = 1.0 / 3.0
+    ks = stats.kstest(s / math.sqrt(T), stats.maxwell.cdf)
+    assert ks.pvalue > 1e-3, ks
