@@ -207,7 +207,8 @@ def nbar_of(w, n=None):
 PHASE_NAMES = ("search", "tile", "move", "scan", "scatter", "moments", "finalize")
 
 
-def run_device(k, w, seed, steps, warmup, stream, occ=0.0, clocks=None, barrier=None, flags=0, state=None):
+def run_device(k, w, seed, steps, warmup, stream, occ=0.0, clocks=None, barrier=None, flags=0, state=None,
+               tile=(0, 0)):
     """One handle on a workload: warm-up, then `steps` timed steps launched
     kernel by kernel with events on the handle's stream.  Returns a dict of
     the timings, the handle's description and a few diagnostics."""
@@ -217,7 +218,7 @@ def run_device(k, w, seed, steps, warmup, stream, occ=0.0, clocks=None, barrier=
     pos, vel = state if state is not None else inputs.make_state(w, seed=seed, dtype=dtype)
     cfg = k.make_config(dim_pos=w["dim_pos"], n_cells=w["n_cells"], lo=w["lo"], hi=w["hi"], bc=w["bc"],
                         lam=w["lam"], dt=w["dt"], seed=seed, precision=w["precision"], stream=stream.cuda_stream,
-                        occupancy_target=occ, flags=flags)
+                        occupancy_target=occ, flags=flags, tile_threads=tile[0], tile_cap=tile[1])
     sim = k.Simulation(cfg, pos, vel)
     info = sim.info()
     e_start = sim.moments()[2][0, 1]
@@ -316,7 +317,7 @@ def ours(args):
 
     # ---------------- device-resident throughput (inputs already in HBM)
     r = run_device(k, w, seed, args.steps, args.warmup, stream, occ=args.occ, clocks=ClockSampler(local),
-                   barrier=barrier)
+                   barrier=barrier, tile=(args.tile_threads, args.tile_cap))
     elapsed_ms = max_over_ranks([r["prof"]["total"]], world, "cuda")[0]
     pos, vel, cfg = r.pop("pos"), r.pop("vel"), r["cfg"]
 
@@ -365,6 +366,7 @@ def ours(args):
                    "n_cells": list(w["n_cells"]), "box": [list(w["lo"]), list(w["hi"])], "dt": w["dt"],
                    "precision": w["precision"], "search_cells": int(info.n_search_cells),
                    "sub_cells": list(info.sub_cells), "occupancy_target": args.occ,
+                   "tile_threads": info.tile_threads, "tile_cap": info.tile_cap,
                    "l2": "no flush: state 2 x %.2f GB > 129 MB L2" % (n * 32 / 1e9),
                    "parallelism": f"replicas x{world}", "n_sm": n_sm},
         "phase_ms_per_step": {p: round(v, 4) for p, v in phases.items()},
@@ -674,6 +676,8 @@ def main():
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--occ", type=float, default=0.0, help="particles per search cell (0: library default)")
     ap.add_argument("--instances", type=int, default=0, help="batched workload: number of instances")
+    ap.add_argument("--tile-threads", type=int, default=0, help="tile search threads per c-bin block (0: default)")
+    ap.add_argument("--tile-cap", type=int, default=0, help="tile search staging capacity (0: default)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

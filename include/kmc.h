@@ -125,6 +125,10 @@ typedef struct kmc_config {
     double occupancy_target; /* automatic subdivision: particles per search cell aimed at (0 = 0.5) */
     int flags;          /* KMC_FLAG_* */
     double radial_center[3]; /* centre of the radial velocity moment (KMC_MOM_RADIAL), finite */
+    int tile_threads;   /* search of unsubdivided grids (one block per c-bin): threads per block, 64, 128
+                         * or 256 (0 = 256); speed only, never results */
+    int tile_cap;       /* the same: candidates staged in shared memory at once, even, 64 ... 6144 in
+                         * binary32, 64 ... 3072 in binary64 (0 = 1536 / 768, 48 KiB); speed only */
 } kmc_config;
 
 /* Mean number of candidates a particle of the current state examines in the
@@ -154,6 +158,8 @@ typedef struct kmc_info {
     int n_scan_tiles;        /* tiles of the key scan (kmc_test_hold_scan) */
     int kernels_per_step;    /* kernels one kmc_step launches per step without moments */
     int kernels_moments;     /* kernels added per step when moments are wanted */
+    int tile_threads;        /* tile search threads per c-bin block */
+    int tile_cap;            /* tile search staging capacity (candidates) */
     int graph_mode;          /* how the last kmc_step ran: 2 = one CUDA graph for all its steps (a device-side
                               * loop counter drives a conditional while node), 1 = one graph per step,
                               * 0 = kernel by kernel (KMC_FLAG_NO_GRAPH, or before the first kmc_step) */
@@ -247,14 +253,16 @@ KMC_API int kmc_get_partners(kmc_handle* h, int32_t* best, int32_t* partner, int
 /* Pick the implementation parameters of the search for a configuration by
  * measurement (the paper has no counterpart: these parameters change speed
  * only, never results).  For each candidate setting -- automatic subdivision
- * at several occupancy targets, the per-c-bin tile search or the per-particle
- * search where the grid is not subdivided, and the shared-memory staged search
- * for 3-D grids -- a handle is created from (cfg, n, pos, vel, where) as in
+ * at several occupancy targets, the per-c-bin tile search (with several
+ * threads per c-bin block and staging capacities) or the per-particle search
+ * where the grid is not subdivided, and the shared-memory staged search for
+ * 3-D grids -- a handle is created from (cfg, n, pos, vel, where) as in
  * kmc_init, warmed up for one step and timed over trial_steps >= 1 steps with
  * CUDA events on its stream, then freed; the caller's data are only read.
- * *best receives a copy of *cfg with occupancy_target and flags (the
- * KMC_FLAG_NO_TILE_SEARCH / KMC_FLAG_STAGED_SEARCH bits) of the fastest
- * setting and sub_cells = 0 (automatic); *ms_per_step (may be NULL) its time.
+ * *best receives a copy of *cfg with occupancy_target, tile_threads, tile_cap
+ * and flags (the KMC_FLAG_NO_TILE_SEARCH / KMC_FLAG_STAGED_SEARCH bits) of the
+ * fastest setting and sub_cells = 0 (automatic); *ms_per_step (may be NULL)
+ * its time.
  * Device memory: one handle at a time.  Synchronises cfg->stream.  Returns
  * KMC_EINVAL for an invalid configuration or state; a setting whose handle
  * cannot be created (e.g. KMC_ENOMEM) is skipped, and its error is returned

@@ -54,6 +54,7 @@ struct kmc_handle {
     uint32_t id_bits = 32;
     uint32_t n_stage_tiles = 0;
     int stage_cap = 0, stage_rows = 0, stage_stride = 0, stage_pair_cap = 0, any_direct = 1, any_tiled = 0;
+    int tile_threads = 256, tile_cap = 1536;
     int64_t n_bins = 0, bins_per_inst = 0;
     int64_t bytes = 0;
     int mom_state = 0;  // 1: acc/mom/glob describe the current state
@@ -137,6 +138,8 @@ Bufs<T> make_bufs(const kmc_handle* h) {
     b.any_direct = h->any_direct;
     b.any_tiled = h->any_tiled;
     b.dsmc = (h->cfg.flags & KMC_FLAG_DSMC) ? 1 : 0;
+    b.tile_threads = h->tile_threads;
+    b.tile_cap = h->tile_cap;
     b.id_bits = h->id_bits;
     b.id_mask = h->id_bits >= 32 ? 0xffffffffu : ((1u << h->id_bits) - 1u);
     return b;
@@ -376,6 +379,10 @@ int validate_config(const kmc_config* c, int64_t n) {
         ~(KMC_FLAG_RECORD | KMC_FLAG_NO_GRAPH | KMC_FLAG_STAGED_SEARCH | KMC_FLAG_NO_TILE_SEARCH | KMC_FLAG_ADAPTIVE_DT |
           KMC_FLAG_VELOCITY_2D | KMC_FLAG_DSMC))
         return fail(nullptr, KMC_EINVAL, "unknown flags");
+    if (c->tile_threads != 0 && c->tile_threads != 64 && c->tile_threads != 128 && c->tile_threads != 256)
+        return fail(nullptr, KMC_EINVAL, "tile_threads must be 0, 64, 128 or 256");
+    if (c->tile_cap != 0 && (c->tile_cap < 64 || (c->tile_cap & 1) || c->tile_cap > (c->precision == 64 ? 3072 : 6144)))
+        return fail(nullptr, KMC_EINVAL, "tile_cap must be 0 or even, 64 ... 6144 (binary32) / 3072 (binary64)");
     if (c->flags & KMC_FLAG_DSMC) {
         for (int d = 0; d < c->dim_pos; ++d)
             if (c->sub_cells[d] > 1) return fail(nullptr, KMC_EINVAL, "KMC_FLAG_DSMC: the collision cells are the c-bins");
@@ -504,6 +511,8 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
     h->dim = cfg->dim_pos;
     h->n = n;
     h->n_inst = (int)insts.size();
+    h->tile_threads = cfg->tile_threads > 0 ? cfg->tile_threads : 256;
+    h->tile_cap = cfg->tile_cap > 0 ? cfg->tile_cap : (h->precision == 64 ? 768 : 1536);
 
     Geo& g = h->geo;
     g.dim = h->dim;
@@ -696,6 +705,11 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
                                                  : prepare_staged<float>(make_bufs<float>(h));
         if (e != cudaSuccess) return bail(fail(h, KMC_ECUDA, std::string("staged search set-up: ") + cudaGetErrorString(e)));
     }
+    if (h->any_tiled) {
+        const cudaError_t e = h->precision == 64 ? prepare_tile<double>(make_bufs<double>(h))
+                                                 : prepare_tile<float>(make_bufs<float>(h));
+        if (e != cudaSuccess) return bail(fail(h, KMC_ECUDA, std::string("tile search set-up: ") + cudaGetErrorString(e)));
+    }
     if ((rc = sort_packed(h, 0u))) return bail(rc);
     *out = h;
     return KMC_OK;
@@ -858,12 +872,18 @@ int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, const void* 
     struct Trial {
         double occ;
         int flags;
+        int tile_threads, tile_cap;
     };
     const int keep = cfg->flags & ~(KMC_FLAG_NO_TILE_SEARCH | KMC_FLAG_STAGED_SEARCH);
+    const int cap0 = cfg->precision == 64 ? 768 : 1536;
     std::vector<Trial> trials;
-    for (double occ : {0.25, 0.35, 0.5, 0.7, 1.0, 1.5}) trials.push_back({occ, keep});
-    trials.push_back({0.0, keep | KMC_FLAG_NO_TILE_SEARCH});
-    if (cfg->dim_pos == 3 && !(cfg->flags & KMC_FLAG_DSMC)) trials.push_back({0.0, keep | KMC_FLAG_STAGED_SEARCH});
+    for (double occ : {0.25, 0.35, 0.5, 0.7, 1.0, 1.5}) trials.push_back({occ, keep, 0, 0});
+    // threads per c-bin block and staging capacity of the tile search (these
+    // trials are skipped as duplicates where the grid is subdivided)
+    const int tile_opts[][2] = {{128, cap0}, {256, 2 * cap0}, {128, cap0 / 2}, {256, cap0 / 2}, {64, cap0 / 2}};
+    for (const auto& t : tile_opts) trials.push_back({0.0, keep, t[0], t[1]});
+    trials.push_back({0.0, keep | KMC_FLAG_NO_TILE_SEARCH, 0, 0});
+    if (cfg->dim_pos == 3 && !(cfg->flags & KMC_FLAG_DSMC)) trials.push_back({0.0, keep | KMC_FLAG_STAGED_SEARCH, 0, 0});
     double best_ms = -1.0;
     kmc_config pick = *cfg;
     int first_rc = KMC_OK;
@@ -873,6 +893,8 @@ int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, const void* 
         c.sub_cells[0] = c.sub_cells[1] = c.sub_cells[2] = 0;
         c.occupancy_target = t.occ;
         c.flags = t.flags;
+        c.tile_threads = t.tile_threads;
+        c.tile_cap = t.tile_cap;
         kmc_handle* h = nullptr;
         const int rc = kmc_init(&c, n, pos, vel, where, &h);
         if (rc != KMC_OK) {
@@ -884,6 +906,8 @@ int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, const void* 
         // search kernel for every instance) are not timed again
         std::vector<int> setup;
         for (const InstDev& I : h->inst_h) setup.insert(setup.end(), {I.s[0], I.s[1], I.s[2], I.tiled, I.staged});
+        setup.push_back(h->any_tiled ? h->tile_threads : 0);
+        setup.push_back(h->any_tiled ? h->tile_cap : 0);
         if (std::find(tried.begin(), tried.end(), setup) != tried.end()) {
             kmc_free(h);
             continue;
@@ -959,6 +983,8 @@ int kmc_get_info(kmc_handle* h, kmc_info* info) {
     info->kernels_per_step = ((h->any_direct || h->n_stage_tiles > 0) ? 1 : 0) + (h->any_tiled ? 1 : 0) +
                              (h->n_stage_tiles > 0 ? 1 : 0) + ((h->cfg.flags & KMC_FLAG_DSMC) ? 1 : 0) + 4;
     info->kernels_moments = 3;
+    info->tile_threads = h->tile_threads;
+    info->tile_cap = h->tile_cap;
     info->graph_mode = (h->cfg.flags & KMC_FLAG_NO_GRAPH) || h->graph_failed
                            ? 0
                            : ((h->loop_graph[0] || h->loop_graph[1]) ? 2 : (h->loop_failed ? 1 : 0));

@@ -141,6 +141,8 @@ struct Bufs {
     int any_direct;          // some instance uses the direct (per-thread) search
     int any_tiled;           // some instance uses the tile search (one block per c-bin)
     int dsmc;                // the random-partner comparison variant instead of the PoCA search
+    int tile_threads;        // tile search: threads per c-bin block (64, 128 or 256)
+    int tile_cap;            // tile search: candidates staged in shared memory at once (even)
     // particle tag = (instance << id_bits) | instance-local id
     uint32_t id_bits;        // 32 when there is one instance
     uint32_t id_mask;
@@ -159,6 +161,10 @@ template <typename T>
 cudaError_t prepare_staged(const Bufs<T>& b);
 template <typename T>
 size_t stage_smem_bytes(const Bufs<T>& b);
+template <typename T>
+cudaError_t prepare_tile(const Bufs<T>& b);
+template <typename T>
+size_t tile_smem_bytes(const Bufs<T>& b);
 template <typename T>
 cudaError_t launch_move(const Bufs<T>& b, cudaStream_t s);
 template <typename T>

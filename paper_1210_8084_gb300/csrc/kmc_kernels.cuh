@@ -900,16 +900,18 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) search_kerne
 // the direct search: rows of the window as key ranges with their periodic
 // images, binary32 symmetric (a home tests only candidates at higher sorted
 // positions and offers the outcome to both keys), binary64 full window.
-constexpr int kTileThreads = 256;
+constexpr int kTileThreads = 256;   // largest block of the tile search (the launch may use fewer)
 constexpr int kTileRanges = 18;   // 3 x 3 rows x 2 parts (a periodic fast dimension may split)
 
+// Default staging capacity: candidates (pos + vel) held in shared memory at
+// once, 48 KiB in either precision; a handle may choose another (tile_cap).
 template <typename T>
 struct TileCap {
-    static constexpr int value = 1536;   // staged candidates (pos + vel): 48 KiB in binary32
+    static constexpr int value = 1536;
 };
 template <>
 struct TileCap<double> {
-    static constexpr int value = 768;    // 48 KiB in binary64
+    static constexpr int value = 768;
 };
 
 template <typename T, int DIM, bool MINIMG>
@@ -919,7 +921,7 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
                                                  T (*rsh)[3], int& nr_s, int& tot_s) {
     using V = typename Vec4<T>::type;
     constexpr bool kSym = sizeof(T) == 4;
-    constexpr int CAP = TileCap<T>::value;
+    const int CAP = b.tile_cap;   // even
     const int tid = threadIdx.x;
     // cell coordinates from the key (x slowest)
     uint32_t rel = kc - I.key_base;
@@ -1216,10 +1218,10 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kTileThreads) tile_search_kernel(Bufs<T> b) {
     using V = typename Vec4<T>::type;
-    constexpr int CAP = TileCap<T>::value;
+    extern __shared__ __align__(32) unsigned char tile_smem[];   // 2 x tile_cap vectors
+    V* sp = reinterpret_cast<V*>(tile_smem);
+    V* sv = sp + b.tile_cap;
     __shared__ GeoT<T> G;
-    __shared__ V sp[CAP];
-    __shared__ V sv[CAP];
     __shared__ int rq0[kTileRanges], rlen[kTileRanges], rpre[kTileRanges];
     __shared__ T rsh[kTileRanges][3];
     __shared__ int nr_s, tot_s, inst_s;
@@ -2218,9 +2220,24 @@ cudaError_t launch_search(const Bufs<T>& b, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_tile_search(const Bufs<T>& b, cudaStream_t s) {
     if (b.n == 0 || !b.any_tiled || b.n_keys == 0) return cudaSuccess;
-    if (b.geo.dim == 3) tile_search_kernel<T, 3><<<b.n_keys, kTileThreads, 0, s>>>(b);
-    else tile_search_kernel<T, 2><<<b.n_keys, kTileThreads, 0, s>>>(b);
+    const size_t smem = tile_smem_bytes(b);
+    if (b.geo.dim == 3) tile_search_kernel<T, 3><<<b.n_keys, b.tile_threads, smem, s>>>(b);
+    else tile_search_kernel<T, 2><<<b.n_keys, b.tile_threads, smem, s>>>(b);
     return cudaGetLastError();
+}
+
+template <typename T>
+size_t tile_smem_bytes(const Bufs<T>& b) {
+    return (size_t)b.tile_cap * 2 * sizeof(typename Vec4<T>::type);
+}
+
+// Dynamic shared memory beyond 48 KiB must be allowed per kernel.
+template <typename T>
+cudaError_t prepare_tile(const Bufs<T>& b) {
+    const int bytes = (int)tile_smem_bytes(b);
+    cudaError_t e = cudaFuncSetAttribute(tile_search_kernel<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(tile_search_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
 
 template <typename T>
@@ -2302,6 +2319,8 @@ cudaError_t launch_window_count(const Bufs<T>& b, unsigned long long* total, cud
     template cudaError_t launch_search<T>(const Bufs<T>&, cudaStream_t);                           \
     template cudaError_t launch_tile_search<T>(const Bufs<T>&, cudaStream_t);                      \
     template cudaError_t prepare_staged<T>(const Bufs<T>&);                                        \
+    template cudaError_t prepare_tile<T>(const Bufs<T>&);                                          \
+    template size_t tile_smem_bytes<T>(const Bufs<T>&);                                            \
     template size_t stage_smem_bytes<T>(const Bufs<T>&);                                           \
     template cudaError_t launch_move<T>(const Bufs<T>&, cudaStream_t);                             \
     template cudaError_t launch_scatter<T>(const Bufs<T>&, cudaStream_t);                          \

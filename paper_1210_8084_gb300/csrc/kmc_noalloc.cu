@@ -144,6 +144,8 @@ int run(const kmc_config* cfg, int64_t n, const void* pos, const void* vel, int3
     b.n_keys = n_keys;
     b.n_tiles = n_tiles;
     b.any_direct = 1;
+    b.tile_threads = 256;   // no instance here is tiled
+    b.tile_cap = 1536;
     b.id_bits = 32;
     b.id_mask = 0xffffffffu;
     // the array keeps the last call's contents: clear what must start at zero

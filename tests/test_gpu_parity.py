@@ -642,3 +642,29 @@ def test_dsmc_variant_matches_oracle(prec, dim):
         assert np.abs(pd[:, :dim] - p[:, :dim]).max() <= tol_x
         p, v = pd.astype(np.float64), vd.astype(np.float64)   # the next step from the device state
     sim.close()
+
+
+@pytest.mark.parametrize("prec,tt,cap", [(32, 64, 64), (32, 128, 768), (32, 256, 6144), (64, 128, 3072),
+                                         (64, 64, 100)])
+def test_tile_search_parameters_do_not_change_results(prec, tt, cap):
+    """Threads per c-bin block and staging capacity of the tile search (the
+    autotuner's choices) change speed only: the closest candidates and pairs
+    equal the oracle's, from a capacity far below one neighbourhood (many
+    staging chunks) to one above it."""
+    _setup()
+    import paper_1210_8084_gb300 as k
+    name, n, dim, n_cells, lo, hi, bc, lam, dt, _ = TILE_CASES[0]
+    pos, vel = make_inputs(name, n, dim, lo, hi)
+    if prec == 32:
+        pos, vel = f32_state(pos, vel, lo, hi, bc)
+    cfg = k.make_config(dim_pos=dim, n_cells=n_cells, lo=lo, hi=hi, bc=bc, lam=lam, dt=dt, seed=5, precision=prec,
+                        flags=k.KMC_FLAG_RECORD, sub_cells=(1, 1, 1), tile_threads=tt, tile_cap=cap)
+    sim = k.Simulation(cfg, pos, vel)
+    info = sim.info()
+    assert (info.tile_threads, info.tile_cap) == (tt, cap)
+    sim.step(1)
+    best, partner = sim.partners()
+    sim.close()
+    o = oracle_step(pos, vel, dim, n_cells, lo, hi, bc, oracle_R2(lam, n, dim, lo, hi), dt, 5, 0, prec == 32)
+    assert (best >= 0).mean() > 0.05
+    assert np.array_equal(best, o["best"]) and np.array_equal(partner, o["partner"])
