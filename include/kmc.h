@@ -81,6 +81,7 @@ extern "C" {
                             * another, then free flight for all.  The collision cells are the c-bins (sub_cells
                             * must be 0 or 1).  Collided particles count as paired in the moments (zero virial);
                             * kmc_get_partners reports -1 */
+#define KMC_FLAG_RADIAL_MOMENT 128 /* also accumulate the radial velocity per c-bin (KMC_MOM_RADIAL, Eq. vel_r) */
 #define KMC_FLAG_ADAPTIVE_DT 16  /* timestep dt(t) = dx_min / v_max(t) of each step's start state (Sect. "Simulation
                                   * setup"; dx_min the smallest c-bin width, v_max the largest speed of the instance,
                                   * |v|^2 = fma(vz, vz, fma(vy, vy, vx vx)) in the state precision, the quotient in
@@ -90,7 +91,8 @@ extern "C" {
 #define KMC_MOM_RAW 1       /* per c-bin: N, Sum vx, Sum vy, Sum vz, Sum vx^2, Sum vy^2, Sum vz^2, Sum W */
 #define KMC_MOM_DERIVED 2   /* per c-bin: n, ux, uy, uz, T, p_kin, p_vir, p */
 #define KMC_MOM_GLOBAL 4    /* per instance: N, E = 1/2 Sum |v|^2, Px, Py, Pz, Sum W, pairs, 0 */
-#define KMC_MOM_RADIAL 8    /* per c-bin: Sum v.r_hat, v_r = Sum v.r_hat / N (Eq. vel_r; the Noh and Sedov tests),
+#define KMC_MOM_RADIAL 8    /* per c-bin (handles with KMC_FLAG_RADIAL_MOMENT; KMC_ESTATE otherwise):
+                             * Sum v.r_hat, v_r = Sum v.r_hat / N (Eq. vel_r; the Noh and Sedov tests),
                              * r_hat the unit vector from kmc_config.radial_center to the particle over the
                              * position dimensions (no periodic image; 0 for a particle at the centre) */
 

@@ -38,6 +38,7 @@ KMC_FLAG_NO_TILE_SEARCH = 8
 KMC_FLAG_ADAPTIVE_DT = 16
 KMC_FLAG_VELOCITY_2D = 32
 KMC_FLAG_DSMC = 64
+KMC_FLAG_RADIAL_MOMENT = 128
 KMC_MOM_RAW = 1
 KMC_MOM_DERIVED = 2
 KMC_MOM_GLOBAL = 4

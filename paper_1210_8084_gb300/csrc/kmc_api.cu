@@ -138,6 +138,7 @@ Bufs<T> make_bufs(const kmc_handle* h) {
     b.any_direct = h->any_direct;
     b.any_tiled = h->any_tiled;
     b.dsmc = (h->cfg.flags & KMC_FLAG_DSMC) ? 1 : 0;
+    b.radial = (h->cfg.flags & KMC_FLAG_RADIAL_MOMENT) ? 1 : 0;
     b.tile_threads = h->tile_threads;
     b.tile_cap = h->tile_cap;
     b.id_bits = h->id_bits;
@@ -377,7 +378,7 @@ int validate_config(const kmc_config* c, int64_t n) {
     if (c->n_instances > 1 && !c->instances) return fail(nullptr, KMC_EINVAL, "instances is NULL");
     if (c->flags &
         ~(KMC_FLAG_RECORD | KMC_FLAG_NO_GRAPH | KMC_FLAG_STAGED_SEARCH | KMC_FLAG_NO_TILE_SEARCH | KMC_FLAG_ADAPTIVE_DT |
-          KMC_FLAG_VELOCITY_2D | KMC_FLAG_DSMC))
+          KMC_FLAG_VELOCITY_2D | KMC_FLAG_DSMC | KMC_FLAG_RADIAL_MOMENT))
         return fail(nullptr, KMC_EINVAL, "unknown flags");
     if (c->tile_threads != 0 && c->tile_threads != 64 && c->tile_threads != 128 && c->tile_threads != 256)
         return fail(nullptr, KMC_EINVAL, "tile_threads must be 0, 64, 128 or 256");
@@ -857,6 +858,8 @@ int kmc_moments(kmc_handle* h, double* out, int where, int mask) {
         KMC_CUDA(h, cudaMemcpyAsync(o, h->glob, sizeof(double) * 8 * h->n_inst, kind, h->stream));
         o += 8 * h->n_inst;
     }
+    if ((mask & KMC_MOM_RADIAL) && !(h->cfg.flags & KMC_FLAG_RADIAL_MOMENT))
+        return fail(h, KMC_ESTATE, "KMC_MOM_RADIAL needs a handle created with KMC_FLAG_RADIAL_MOMENT");
     if (h->n_bins > 0 && (mask & KMC_MOM_RADIAL)) {
         KMC_CUDA(h, cudaMemcpy2DAsync(o, 2 * sizeof(double), h->mom + 16, kMomStride * sizeof(double),
                                       2 * sizeof(double), (size_t)h->n_bins, kind, h->stream));

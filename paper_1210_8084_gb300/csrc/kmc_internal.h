@@ -141,6 +141,7 @@ struct Bufs {
     int any_direct;          // some instance uses the direct (per-thread) search
     int any_tiled;           // some instance uses the tile search (one block per c-bin)
     int dsmc;                // the random-partner comparison variant instead of the PoCA search
+    int radial;              // accumulate Sum v.r_hat (KMC_FLAG_RADIAL_MOMENT)
     int tile_threads;        // tile search: threads per c-bin block (64, 128 or 256)
     int tile_cap;            // tile search: candidates staged in shared memory at once (even)
     // particle tag = (instance << id_bits) | instance-local id

@@ -1129,9 +1129,9 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
                 // (about one test in a thousand) leaves the paired path, for d^2.
                 // b > 0 needs no test of its own: a < 0 and fma(b, dt, a) > 0
                 // give b dt > -a > 0 exactly (the rounding keeps the sign).
-#pragma unroll 2
-                for (; e + 1 < e1; e += 2) {
-                    const int k = (e - c0) >> 1;
+                // the whole test of staged pair k (candidates 2k, 2k + 1 of the chunk);
+                // bit 0 / 1 of the result: candidate passes criteria 1-2
+                auto test2 = [&](int k, int32_t q, float2& rr, float2& a, float2& bb) -> unsigned {
                     const float4 A = pA[k], B = pB[k], C = pC[k];
                     float2 d0 = __fadd2_rn(xi0, make_float2(A.x, A.y));
                     float2 d1 = __fadd2_rn(xi1, make_float2(A.z, A.w));
@@ -1144,11 +1144,11 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
                     }
                     const float2 u0 = __fadd2_rn(vi0, make_float2(B.z, B.w));
                     const float2 u1 = __fadd2_rn(vi1, make_float2(C.x, C.y));
-                    float2 a = __fmul2_rn(d0, u0);
+                    a = __fmul2_rn(d0, u0);
                     a = __ffma2_rn(d1, u1, a);
-                    float2 bb = __fmul2_rn(u0, u0);
+                    bb = __fmul2_rn(u0, u0);
                     bb = __ffma2_rn(u1, u1, bb);
-                    float2 rr = __fmul2_rn(d0, d0);
+                    rr = __fmul2_rn(d0, d0);
                     rr = __ffma2_rn(d1, d1, rr);
                     if (DIM == 3) {
                         const float2 u2 = __fadd2_rn(vi2, make_float2(C.z, C.w));
@@ -1159,14 +1159,34 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
                     const float2 f = __ffma2_rn(bb, dt2, a);
                     const float2 y = __fmul2_rn(bb, __fadd2_rn(rr, mR2));
                     const float2 disc = __ffma2_rn(a, a, make_float2(-y.x, -y.y));
-                    const int32_t q = qoff + e;
                     const bool ok0 = (!CHK || q > lim) && a.x < 0.f && f.x > 0.f && disc.x >= 0.f;
                     const bool ok1 = (!CHK || q + 1 > lim) && a.y < 0.f && f.y > 0.f && disc.y >= 0.f;
-                    if (ok0 || ok1) {
-                        const uint2 tg = pT[k];
-                        if (ok0) close(rr.x, a.x, bb.x, tg.x, q);
-                        if (ok1) close(rr.y, a.y, bb.y, tg.y, q + 1);
+                    return (ok0 ? 1u : 0u) | (ok1 ? 2u : 0u);
+                };
+                auto take2 = [&](unsigned ok, int k, int32_t q, float2 rr, float2 a, float2 bb) {
+                    const uint2 tg = pT[k];
+                    if (ok & 1u) close(rr.x, a.x, bb.x, tg.x, q);
+                    if (ok & 2u) close(rr.y, a.y, bb.y, tg.y, q + 1);
+                };
+                // two staged pairs (four candidates) per step of the loop: the two
+                // tests interleave, and one branch covers all four
+                for (; e + 3 < e1; e += 4) {
+                    const int k = (e - c0) >> 1;
+                    const int32_t q = qoff + e;
+                    float2 rr0, a0, b0, rr1, a1, b1;
+                    const unsigned ok0 = test2(k, q, rr0, a0, b0);
+                    const unsigned ok1 = test2(k + 1, q + 2, rr1, a1, b1);
+                    if (ok0 | ok1) {
+                        if (ok0) take2(ok0, k, q, rr0, a0, b0);
+                        if (ok1) take2(ok1, k + 1, q + 2, rr1, a1, b1);
                     }
+                }
+                if (e + 1 < e1) {
+                    const int k = (e - c0) >> 1;
+                    float2 rr0, a0, b0;
+                    const unsigned ok0 = test2(k, qoff + e, rr0, a0, b0);
+                    if (ok0) take2(ok0, k, qoff + e, rr0, a0, b0);
+                    e += 2;
                 }
                 if (e < e1) one(e);
             }
@@ -1817,7 +1837,7 @@ __global__ void __launch_bounds__(kThreads) scatter_tags_kernel(Bufs<T> b) {
     const uint32_t k = b.key[p];
     if (k >= b.n_keys) return;
     const uint32_t s0 = b.start[k], s1 = b.start[k + 1];
-    if (s1 <= s0 + 1u || s1 - s0 > kCanonMax) return;
+    if (s1 <= s0 + 1u || s1 - s0 > kCanonMax) return;   // alone in its cell (most cells of a fine grid)
     const uint32_t dst = s0 + b.slot[p];
     if (dst >= s1 || dst >= (uint32_t)b.n) return;   // only after a failed scan (flagged by the scatter)
     b.slot_of[dst] = b.tagB[p];
@@ -1841,23 +1861,23 @@ __device__ __forceinline__ uint32_t tags_below(const uint32_t* __restrict__ t, u
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) scatter_kernel(Bufs<T> b) {
+    using V = typename Vec4<T>::type;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= b.n) return;
-    const uint32_t k = b.key[p];
+    // the particle's own words and state first (independent loads), then its cell's range
+    const uint32_t k = b.key[p], slot = b.slot[p], tag = b.tagB[p];
+    const V P = b.posB[p], Q = b.velB[p];
     const uint32_t s0 = b.start[k];
-    uint32_t rank = b.slot[p];
-    if (k < b.n_keys) {
-        const uint32_t s1 = b.start[k + 1];
-        if (s1 > s0 + 1u && s1 - s0 <= kCanonMax && s1 <= (uint32_t)b.n)
-            rank = tags_below(b.slot_of, s0, s1, b.tagB[p]);
-    }
+    const uint32_t s1 = k < b.n_keys ? b.start[k + 1] : s0;
+    uint32_t rank = slot;
+    if (s1 > s0 + 1u && s1 - s0 <= kCanonMax && s1 <= (uint32_t)b.n) rank = tags_below(b.slot_of, s0, s1, tag);
     const uint32_t dst = s0 + rank;
     if (dst >= (uint32_t)b.n) {  // only after a failed scan; reported as a device error
         atomicOr(&b.st->error, kErrKeyRange);
         return;
     }
-    b.posA[dst] = b.posB[p];
-    b.velA[dst] = b.velB[p];
+    b.posA[dst] = P;
+    b.velA[dst] = Q;
     b.bkey[dst] = kNoPartner;   // the next search starts from no partner
 }
 
@@ -2010,7 +2030,7 @@ __global__ void __launch_bounds__(kThreads) cellkey_kernel(Bufs<T> b, int32_t* _
 // block_moment_partials).  Each thread reduces kMomItems consecutive particles
 // (consecutive particles of A share a c-bin almost always), then warp and
 // block aggregation.  use_virial = 0 ignores vel.w (state not produced by a step).
-template <typename T, int DIM>
+template <typename T, int DIM, bool RADIAL>
 __global__ void __launch_bounds__(kThreads) moments_kernel(Bufs<T> b, int use_virial) {
     using V = typename Vec4<T>::type;
     __shared__ GeoT<T> G;
@@ -2069,7 +2089,7 @@ __global__ void __launch_bounds__(kThreads) moments_kernel(Bufs<T> b, int use_vi
         if (collided) f[6] += fixed_of(Q.w, sw);
         // radial velocity (Eq. vel_r): v . r_hat, r_hat from the configured centre
         // over the position dimensions (0 at the centre itself); |v . r_hat| <= v_max
-        {
+        if (RADIAL) {
             const T v3[3] = {Q.x, Q.y, Q.z};
             T r2 = (T)0, vd = (T)0;
 #pragma unroll
@@ -2294,8 +2314,13 @@ cudaError_t launch_moments(const Bufs<T>& b, int use_virial, cudaStream_t s) {
     if (b.n == 0) return cudaSuccess;
     const int64_t threads = (b.n + kMomItems - 1) / kMomItems;
     const unsigned blocks = (unsigned)((threads + kThreads - 1) / kThreads);
-    if (b.geo.dim == 3) moments_kernel<T, 3><<<blocks, kThreads, 0, s>>>(b, use_virial);
-    else moments_kernel<T, 2><<<blocks, kThreads, 0, s>>>(b, use_virial);
+    if (b.radial) {
+        if (b.geo.dim == 3) moments_kernel<T, 3, true><<<blocks, kThreads, 0, s>>>(b, use_virial);
+        else moments_kernel<T, 2, true><<<blocks, kThreads, 0, s>>>(b, use_virial);
+    } else {
+        if (b.geo.dim == 3) moments_kernel<T, 3, false><<<blocks, kThreads, 0, s>>>(b, use_virial);
+        else moments_kernel<T, 2, false><<<blocks, kThreads, 0, s>>>(b, use_virial);
+    }
     return cudaGetLastError();
 }
 

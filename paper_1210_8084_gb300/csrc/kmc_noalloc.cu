@@ -183,7 +183,7 @@ extern "C" KMC_API int kmc_find_partners_noalloc(const kmc_config* cfg, int64_t 
     if (!(cfg->sigma > 0) && !(cfg->lambda > 0)) return KMC_EINVAL;
     if (cfg->sigma > 0 && !isfinite(cfg->sigma)) return KMC_EINVAL;
     if (cfg->flags & ~(KMC_FLAG_RECORD | KMC_FLAG_NO_GRAPH | KMC_FLAG_STAGED_SEARCH | KMC_FLAG_NO_TILE_SEARCH |
-                       KMC_FLAG_ADAPTIVE_DT | KMC_FLAG_VELOCITY_2D))
+                       KMC_FLAG_ADAPTIVE_DT | KMC_FLAG_VELOCITY_2D | KMC_FLAG_RADIAL_MOMENT))
         return KMC_EINVAL;   // KMC_FLAG_DSMC included: that variant has no closest candidates
     if ((cfg->flags & KMC_FLAG_VELOCITY_2D) && cfg->dim_pos != 2) return KMC_EINVAL;
     for (int d = 0; d < cfg->dim_pos; ++d) {

@@ -393,7 +393,7 @@ def test_radial_velocity_matches_oracle(prec, dim):
     pos, vel = pos.astype(np.float64), vel.astype(np.float64)
     for center in ((0.0, 0.0, 0.0), (0.3, 0.45, 0.55)):
         cfg = k.make_config(dim_pos=dim, n_cells=nc, lo=lo, hi=hi, bc=bc, lam=1e-3, dt=0.01, seed=2, precision=prec,
-                            radial_center=center)
+                            radial_center=center, flags=k.KMC_FLAG_RADIAL_MOMENT)
         sim = k.Simulation(cfg, pos, vel)
         sim.step(1, want_moments=1)
         p1, v1 = sim.state()

@@ -345,7 +345,7 @@ def test_noh_spherical_implosion_against_exact_solution():
     wall3 = (1, 1, 1)
     pos, vel = inputs.cast_state(pos, vel, np.float32, (0, 0, 0), (1, 1, 1), wall3)
     sim = k.Simulation(k.make_config(dim_pos=3, n_cells=(nc, nc, nc), bc=wall3, lam=1e-3, dt=dt, seed=6,
-                                     precision=32), pos, vel)
+                                     precision=32, flags=k.KMC_FLAG_RADIAL_MOMENT), pos, vel)
     e0 = sim.moments()[2][0, 1]
     sim.step(steps, want_moments=1)
     raw, der, glob = sim.moments()
@@ -502,7 +502,7 @@ def test_noh_cylindrical_2d_reaches_nine_times_n0():
     bc = (1, 1, 0)
     pos, vel = inputs.cast_state(pos, vel, np.float32, (0, 0, 0), (1, 1, 1), bc)
     sim = k.Simulation(k.make_config(dim_pos=2, n_cells=(nc, nc, 1), bc=bc, lam=1e-3, dt=dt, seed=9, precision=32,
-                                     flags=k.KMC_FLAG_VELOCITY_2D), pos, vel)
+                                     flags=k.KMC_FLAG_VELOCITY_2D | k.KMC_FLAG_RADIAL_MOMENT), pos, vel)
     sim.step(steps, want_moments=1)
     raw = sim.moments()[0]
     rad = sim.radial()   # Eq. vel_r about the corner (the cylinder axis)
