@@ -1830,17 +1830,38 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 1) move_kernel(
 // the atomic order (the count is quadratic in the cell's size), and so do the
 // absorbed particles collected after the last cell.  The tags go to slot_of,
 // which is free between the move and the next search.
+// Both passes take kScatterItems particles per thread, a block's items apart
+// (coalesced), with every item's loads issued before any is used: each
+// particle costs two dependent round trips (its key, then its cell's range),
+// so a thread keeps several in flight.
+constexpr int kScatterItems = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) scatter_tags_kernel(Bufs<T> b) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= b.n) return;
-    const uint32_t k = b.key[p];
-    if (k >= b.n_keys) return;
-    const uint32_t s0 = b.start[k], s1 = b.start[k + 1];
-    if (s1 <= s0 + 1u || s1 - s0 > kCanonMax) return;   // alone in its cell (most cells of a fine grid)
-    const uint32_t dst = s0 + b.slot[p];
-    if (dst >= s1 || dst >= (uint32_t)b.n) return;   // only after a failed scan (flagged by the scatter)
-    b.slot_of[dst] = b.tagB[p];
+    const int64_t p0 = (int64_t)blockIdx.x * blockDim.x * kScatterItems + threadIdx.x;
+    uint32_t k[kScatterItems], s0[kScatterItems], s1[kScatterItems];
+#pragma unroll
+    for (int i = 0; i < kScatterItems; ++i) {
+        const int64_t p = p0 + (int64_t)i * blockDim.x;
+        k[i] = p < b.n ? b.key[p] : b.n_keys;
+    }
+#pragma unroll
+    for (int i = 0; i < kScatterItems; ++i) {
+        s0[i] = s1[i] = 0u;
+        if (k[i] < b.n_keys) {
+            s0[i] = b.start[k[i]];
+            s1[i] = b.start[k[i] + 1];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kScatterItems; ++i) {
+        const int64_t p = p0 + (int64_t)i * blockDim.x;
+        // alone in its cell (most cells of a fine grid), or outside every cell
+        if (s1[i] <= s0[i] + 1u || s1[i] - s0[i] > kCanonMax) continue;
+        const uint32_t dst = s0[i] + b.slot[p];
+        if (dst >= s1[i] || dst >= (uint32_t)b.n) continue;   // only after a failed scan (flagged by the scatter)
+        b.slot_of[dst] = b.tagB[p];
+    }
 }
 
 // Tags of [q, q1) below `tag`: scalar up to a 16-byte boundary, then four per load.
@@ -1861,24 +1882,37 @@ __device__ __forceinline__ uint32_t tags_below(const uint32_t* __restrict__ t, u
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) scatter_kernel(Bufs<T> b) {
-    using V = typename Vec4<T>::type;
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= b.n) return;
-    // the particle's own words and state first (independent loads), then its cell's range
-    const uint32_t k = b.key[p], slot = b.slot[p], tag = b.tagB[p];
-    const V P = b.posB[p], Q = b.velB[p];
-    const uint32_t s0 = b.start[k];
-    const uint32_t s1 = k < b.n_keys ? b.start[k + 1] : s0;
-    uint32_t rank = slot;
-    if (s1 > s0 + 1u && s1 - s0 <= kCanonMax && s1 <= (uint32_t)b.n) rank = tags_below(b.slot_of, s0, s1, tag);
-    const uint32_t dst = s0 + rank;
-    if (dst >= (uint32_t)b.n) {  // only after a failed scan; reported as a device error
-        atomicOr(&b.st->error, kErrKeyRange);
-        return;
+    const int64_t p0 = (int64_t)blockIdx.x * blockDim.x * kScatterItems + threadIdx.x;
+    uint32_t k[kScatterItems], s0[kScatterItems], s1[kScatterItems];
+#pragma unroll
+    for (int i = 0; i < kScatterItems; ++i) {
+        const int64_t p = p0 + (int64_t)i * blockDim.x;
+        k[i] = p < b.n ? b.key[p] : 0xffffffffu;
     }
-    b.posA[dst] = P;
-    b.velA[dst] = Q;
-    b.bkey[dst] = kNoPartner;   // the next search starts from no partner
+#pragma unroll
+    for (int i = 0; i < kScatterItems; ++i) {
+        s0[i] = s1[i] = 0u;
+        if (k[i] != 0xffffffffu) {
+            s0[i] = b.start[k[i]];
+            s1[i] = k[i] < b.n_keys ? b.start[k[i] + 1] : s0[i];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kScatterItems; ++i) {
+        const int64_t p = p0 + (int64_t)i * blockDim.x;
+        if (p >= b.n) break;
+        uint32_t rank = b.slot[p];
+        if (s1[i] > s0[i] + 1u && s1[i] - s0[i] <= kCanonMax && s1[i] <= (uint32_t)b.n)
+            rank = tags_below(b.slot_of, s0[i], s1[i], b.tagB[p]);
+        const uint32_t dst = s0[i] + rank;
+        if (dst >= (uint32_t)b.n) {  // only after a failed scan; reported as a device error
+            atomicOr(&b.st->error, kErrKeyRange);
+            continue;
+        }
+        b.posA[dst] = b.posB[p];
+        b.velA[dst] = b.velB[p];
+        b.bkey[dst] = kNoPartner;   // the next search starts from no partner
+    }
 }
 
 // Index (position in the input arrays, p_off + local id) of every particle of
@@ -2053,6 +2087,7 @@ __global__ void __launch_bounds__(kThreads) moments_kernel(Bufs<T> b, int use_vi
         }
     }
     int inst_c = -1;
+    uint32_t bin_base = 0;
     T sv = (T)0, s2 = (T)0, sw = (T)0;   // 2^e of the instance's three fields
 #pragma unroll
     for (int k = 0; k < kMomItems; ++k) {
@@ -2062,16 +2097,20 @@ __global__ void __launch_bounds__(kThreads) moments_kernel(Bufs<T> b, int use_vi
         const V Q = Qs[k];
         if (absorbed(Q.w)) continue;   // left through an absorbing wall
         const int inst = tag_inst(b, R<T>::bits(P.w));
-        const InstDev& I = b.inst[inst];
-        if (inst != inst_c) {
+        if (inst != inst_c) {   // the instance's constants, once per run of one instance
             inst_c = inst;
+            bin_base = b.inst[inst].bin_base;
             sv = pow2_of(b.dyn[inst].mom_e[0], T());
             s2 = pow2_of(b.dyn[inst].mom_e[1], T());
             sw = pow2_of(b.dyn[inst].mom_e[2], T());
         }
         const T x[3] = {P.x, P.y, P.z};
-        uint32_t skey, bin;
-        keys_of<T, DIM>(G, I, x, skey, bin);
+        // the c-bin (the search cell is not needed here)
+        int c[3] = {0, 0, 0}, g[3];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) cell_and_search<T>(x[d], G.lo[d], G.inv[d], G.n[d], 1, c[d], g[d]);
+        const uint32_t bin = bin_base + (uint32_t)c[0] +
+                             (uint32_t)G.n[0] * ((uint32_t)c[1] + (DIM == 3 ? (uint32_t)G.n[1] * (uint32_t)c[2] : 0u));
         if (bin != cur && cnt > 0) {   // rare: the thread's particles span two bins
             unsigned long long* a = b.acc + (size_t)cur * kAccFields;
             atomicAdd(a + 0, (unsigned long long)cnt);
@@ -2276,8 +2315,9 @@ cudaError_t launch_move(const Bufs<T>& b, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_scatter(const Bufs<T>& b, cudaStream_t s) {
     if (b.n == 0) return cudaSuccess;
-    scatter_tags_kernel<T><<<blocks_for(b.n), kThreads, 0, s>>>(b);
-    scatter_kernel<T><<<blocks_for(b.n), kThreads, 0, s>>>(b);
+    const unsigned blocks = (unsigned)((b.n + (int64_t)kThreads * kScatterItems - 1) / ((int64_t)kThreads * kScatterItems));
+    scatter_tags_kernel<T><<<blocks, kThreads, 0, s>>>(b);
+    scatter_kernel<T><<<blocks, kThreads, 0, s>>>(b);
     return cudaGetLastError();
 }
 
