@@ -131,6 +131,8 @@ typedef struct kmc_config {
                          * or 256 (0 = 256); speed only, never results */
     int tile_cap;       /* the same: candidates staged in shared memory at once, even, 64 ... 6144 in
                          * binary32, 64 ... 3072 in binary64 (0 = 1536 / 768, 48 KiB); speed only */
+    int tile_split;     /* the same, binary32: blocks that share one c-bin's candidates, 1 ... 8 (0 = 1);
+                         * speed only */
 } kmc_config;
 
 /* Mean number of candidates a particle of the current state examines in the
@@ -162,6 +164,7 @@ typedef struct kmc_info {
     int kernels_moments;     /* kernels added per step when moments are wanted */
     int tile_threads;        /* tile search threads per c-bin block */
     int tile_cap;            /* tile search staging capacity (candidates) */
+    int tile_split;          /* tile search blocks per c-bin */
     int graph_mode;          /* how the last kmc_step ran: 2 = one CUDA graph for all its steps (a device-side
                               * loop counter drives a conditional while node), 1 = one graph per step,
                               * 0 = kernel by kernel (KMC_FLAG_NO_GRAPH, or before the first kmc_step) */
@@ -261,8 +264,8 @@ KMC_API int kmc_get_partners(kmc_handle* h, int32_t* best, int32_t* partner, int
  * 3-D grids -- a handle is created from (cfg, n, pos, vel, where) as in
  * kmc_init, warmed up for one step and timed over trial_steps >= 1 steps with
  * CUDA events on its stream, then freed; the caller's data are only read.
- * *best receives a copy of *cfg with occupancy_target, tile_threads, tile_cap
- * and flags (the KMC_FLAG_NO_TILE_SEARCH / KMC_FLAG_STAGED_SEARCH bits) of the
+ * *best receives a copy of *cfg with occupancy_target, tile_threads, tile_cap,
+ * tile_split and flags (the KMC_FLAG_NO_TILE_SEARCH / KMC_FLAG_STAGED_SEARCH bits) of the
  * fastest setting and sub_cells = 0 (automatic); *ms_per_step (may be NULL)
  * its time.
  * Device memory: one handle at a time.  Synchronises cfg->stream.  Returns

@@ -86,6 +86,7 @@ class KmcConfig(ctypes.Structure):
         ("radial_center", ctypes.c_double * 3),
         ("tile_threads", ctypes.c_int),
         ("tile_cap", ctypes.c_int),
+        ("tile_split", ctypes.c_int),
     ]
 
 
@@ -113,6 +114,7 @@ class KmcInfo(ctypes.Structure):
         ("kernels_moments", ctypes.c_int),
         ("tile_threads", ctypes.c_int),
         ("tile_cap", ctypes.c_int),
+        ("tile_split", ctypes.c_int),
         ("graph_mode", ctypes.c_int),
     ]
 
@@ -216,7 +218,8 @@ def _check(rc, h=None):
 def make_config(dim_pos=3, n_cells=(1, 1, 1), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0),
                 bc=(KMC_BC_WALL, KMC_BC_PERIODIC, KMC_BC_PERIODIC), lam=1e-3, sigma=0.0, dt=1e-3,
                 seed=0, precision=32, instances=None, stream=None, sub_cells=(0, 0, 0),
-                occupancy_target=0.0, flags=0, radial_center=(0.0, 0.0, 0.0), tile_threads=0, tile_cap=0):
+                occupancy_target=0.0, flags=0, radial_center=(0.0, 0.0, 0.0), tile_threads=0, tile_cap=0,
+                tile_split=0):
     """Fill a KmcConfig.  `instances` is a list of dicts with keys n, lam, sigma, dt, seed;
     the returned object keeps the instance array alive."""
     c = KmcConfig()
@@ -238,6 +241,7 @@ def make_config(dim_pos=3, n_cells=(1, 1, 1), lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 
     c.flags = int(flags)
     c.tile_threads = int(tile_threads)
     c.tile_cap = int(tile_cap)
+    c.tile_split = int(tile_split)
     if instances:
         arr = (KmcInstance * len(instances))()
         for i, inst in enumerate(instances):

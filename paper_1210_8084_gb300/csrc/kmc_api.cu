@@ -54,7 +54,7 @@ struct kmc_handle {
     uint32_t id_bits = 32;
     uint32_t n_stage_tiles = 0;
     int stage_cap = 0, stage_rows = 0, stage_stride = 0, stage_pair_cap = 0, any_direct = 1, any_tiled = 0;
-    int tile_threads = 256, tile_cap = 1536;
+    int tile_threads = 256, tile_cap = 1536, tile_split = 1;
     int64_t n_bins = 0, bins_per_inst = 0;
     int64_t bytes = 0;
     int mom_state = 0;  // 1: acc/mom/glob describe the current state
@@ -141,6 +141,7 @@ Bufs<T> make_bufs(const kmc_handle* h) {
     b.radial = (h->cfg.flags & KMC_FLAG_RADIAL_MOMENT) ? 1 : 0;
     b.tile_threads = h->tile_threads;
     b.tile_cap = h->tile_cap;
+    b.tile_split = h->tile_split;
     b.id_bits = h->id_bits;
     b.id_mask = h->id_bits >= 32 ? 0xffffffffu : ((1u << h->id_bits) - 1u);
     return b;
@@ -382,6 +383,7 @@ int validate_config(const kmc_config* c, int64_t n) {
         return fail(nullptr, KMC_EINVAL, "unknown flags");
     if (c->tile_threads != 0 && c->tile_threads != 64 && c->tile_threads != 128 && c->tile_threads != 256)
         return fail(nullptr, KMC_EINVAL, "tile_threads must be 0, 64, 128 or 256");
+    if (c->tile_split < 0 || c->tile_split > 8) return fail(nullptr, KMC_EINVAL, "tile_split must be 0 ... 8");
     if (c->tile_cap != 0 && (c->tile_cap < 64 || (c->tile_cap & 1) || c->tile_cap > (c->precision == 64 ? 3072 : 6144)))
         return fail(nullptr, KMC_EINVAL, "tile_cap must be 0 or even, 64 ... 6144 (binary32) / 3072 (binary64)");
     if (c->flags & KMC_FLAG_DSMC) {
@@ -514,6 +516,7 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
     h->n_inst = (int)insts.size();
     h->tile_threads = cfg->tile_threads > 0 ? cfg->tile_threads : 256;
     h->tile_cap = cfg->tile_cap > 0 ? cfg->tile_cap : (h->precision == 64 ? 768 : 1536);
+    h->tile_split = h->precision == 64 ? 1 : (cfg->tile_split > 0 ? cfg->tile_split : 1);
 
     Geo& g = h->geo;
     g.dim = h->dim;
@@ -875,18 +878,19 @@ int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, const void* 
     struct Trial {
         double occ;
         int flags;
-        int tile_threads, tile_cap;
+        int tile_threads, tile_cap, tile_split;
     };
     const int keep = cfg->flags & ~(KMC_FLAG_NO_TILE_SEARCH | KMC_FLAG_STAGED_SEARCH);
     const int cap0 = cfg->precision == 64 ? 768 : 1536;
     std::vector<Trial> trials;
-    for (double occ : {0.25, 0.35, 0.5, 0.7, 1.0, 1.5}) trials.push_back({occ, keep, 0, 0});
+    for (double occ : {0.25, 0.35, 0.5, 0.7, 1.0, 1.5}) trials.push_back({occ, keep, 0, 0, 0});
     // threads per c-bin block and staging capacity of the tile search (these
     // trials are skipped as duplicates where the grid is subdivided)
-    const int tile_opts[][2] = {{128, cap0}, {256, 2 * cap0}, {128, cap0 / 2}, {256, cap0 / 2}, {64, cap0 / 2}};
-    for (const auto& t : tile_opts) trials.push_back({0.0, keep, t[0], t[1]});
-    trials.push_back({0.0, keep | KMC_FLAG_NO_TILE_SEARCH, 0, 0});
-    if (cfg->dim_pos == 3 && !(cfg->flags & KMC_FLAG_DSMC)) trials.push_back({0.0, keep | KMC_FLAG_STAGED_SEARCH, 0, 0});
+    const int tile_opts[][3] = {{128, cap0, 1}, {256, 2 * cap0, 1}, {128, cap0 / 2, 1}, {256, cap0 / 2, 1},
+                                {64, cap0 / 2, 1},   {256, cap0, 2},     {256, cap0, 3},      {128, cap0 / 2, 2}};
+    for (const auto& t : tile_opts) trials.push_back({0.0, keep, t[0], t[1], t[2]});
+    trials.push_back({0.0, keep | KMC_FLAG_NO_TILE_SEARCH, 0, 0, 0});
+    if (cfg->dim_pos == 3 && !(cfg->flags & KMC_FLAG_DSMC)) trials.push_back({0.0, keep | KMC_FLAG_STAGED_SEARCH, 0, 0, 0});
     double best_ms = -1.0;
     kmc_config pick = *cfg;
     int first_rc = KMC_OK;
@@ -898,6 +902,7 @@ int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, const void* 
         c.flags = t.flags;
         c.tile_threads = t.tile_threads;
         c.tile_cap = t.tile_cap;
+        c.tile_split = t.tile_split;
         kmc_handle* h = nullptr;
         const int rc = kmc_init(&c, n, pos, vel, where, &h);
         if (rc != KMC_OK) {
@@ -911,6 +916,7 @@ int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, const void* 
         for (const InstDev& I : h->inst_h) setup.insert(setup.end(), {I.s[0], I.s[1], I.s[2], I.tiled, I.staged});
         setup.push_back(h->any_tiled ? h->tile_threads : 0);
         setup.push_back(h->any_tiled ? h->tile_cap : 0);
+        setup.push_back(h->any_tiled ? h->tile_split : 0);
         if (std::find(tried.begin(), tried.end(), setup) != tried.end()) {
             kmc_free(h);
             continue;
@@ -988,6 +994,7 @@ int kmc_get_info(kmc_handle* h, kmc_info* info) {
     info->kernels_moments = 3;
     info->tile_threads = h->tile_threads;
     info->tile_cap = h->tile_cap;
+    info->tile_split = h->tile_split;
     info->graph_mode = (h->cfg.flags & KMC_FLAG_NO_GRAPH) || h->graph_failed
                            ? 0
                            : ((h->loop_graph[0] || h->loop_graph[1]) ? 2 : (h->loop_failed ? 1 : 0));

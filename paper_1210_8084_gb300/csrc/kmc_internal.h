@@ -144,6 +144,7 @@ struct Bufs {
     int radial;              // accumulate Sum v.r_hat (KMC_FLAG_RADIAL_MOMENT)
     int tile_threads;        // tile search: threads per c-bin block (64, 128 or 256)
     int tile_cap;            // tile search: candidates staged in shared memory at once (even)
+    int tile_split;          // tile search: blocks sharing one c-bin's window (binary32)
     // particle tag = (instance << id_bits) | instance-local id
     uint32_t id_bits;        // 32 when there is one instance
     uint32_t id_mask;

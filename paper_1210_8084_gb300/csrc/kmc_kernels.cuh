@@ -993,7 +993,17 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
     }
     __syncthreads();
     const int nr = nr_s, total = tot_s;
-    const bool once = total <= CAP;   // the whole window fits: stage it once for all home chunks
+    // The window may be split between tile_split blocks of the same c-bin
+    // (blockIdx.y = part), each taking every tile_split-th chunk of `per`
+    // candidates (binary32 only: the blocks combine their minima with the
+    // keys' atomicMin).  A block with a single chunk stages it once for all its
+    // home chunks.
+    const int split = kSym ? (int)gridDim.y : 1;
+    const int part = kSym ? (int)blockIdx.y : 0;
+    int per = CAP;
+    if (split > 1) per = min(CAP, ((total + split - 1) / split + 1) & ~1);
+    if (part * per >= total) return;   // nothing left for this block (block-uniform)
+    const bool once = part * per + split * per >= total;
     // Binary32 without per-candidate minimum image: candidates are staged in
     // pairs (staged entries 2k and 2k + 1 side by side, negated so that
     // x_i - x_j is one paired addition) and every home tests two candidates at
@@ -1007,7 +1017,7 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
     float4* pC = reinterpret_cast<float4*>(sv);          // (-vy, -vy', -vz, -vz')
     uint2* pT = reinterpret_cast<uint2*>(pC + CAP / 2);  // (tag, tag')
     auto stage = [&](int c0) {
-        const int cn = min(CAP, total - c0);
+        const int cn = min(per, total - c0);
         for (int e = tid; e < cn; e += blockDim.x) {
             const int ge = c0 + e;
             int r = 0;
@@ -1033,7 +1043,7 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
         }
     };
     if (once) {
-        stage(0);
+        stage(part * per);
         __syncthreads();
     }
     const T dt = step_dt(b.dyn[inst], T()), R2 = inst_R2(I, T());
@@ -1049,8 +1059,8 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
         const T vi[3] = {Q.x, Q.y, Q.z};
         const uint32_t tag = R<T>::bits(P.w);
         // sorted position by id, read by the move kernel to find a partner (every
-        // home is visited in exactly one chunk of homes)
-        if (home) b.slot_of[I.p_off + (int64_t)tag_id(b, tag)] = (uint32_t)p;
+        // home is visited in exactly one chunk of homes of part 0)
+        if (home && part == 0) b.slot_of[I.p_off + (int64_t)tag_id(b, tag)] = (uint32_t)p;
         T bd = R<T>::inf();
         uint32_t bid = 0xffffffffu;
         // binary32: a home tests only higher positions; binary64: the whole
@@ -1191,14 +1201,14 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
                 if (e < e1) one(e);
             }
         };
-        for (int c0 = 0; c0 < total; c0 += CAP) {
+        for (int c0 = part * per; c0 < total; c0 += split * per) {
             if (!once) {
                 __syncthreads();
                 stage(c0);
                 __syncthreads();
             }
             if (!home) continue;
-            const int c1 = min(total, c0 + CAP);
+            const int c1 = min(total, c0 + per);
             for (int r = 0; r < nr; ++r) {
                 const int e0 = max(rpre[r], c0), e1 = min(rpre[r] + rlen[r], c1);
                 if (e0 >= e1) continue;
@@ -1830,10 +1840,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 1) move_kernel(
 // the atomic order (the count is quadratic in the cell's size), and so do the
 // absorbed particles collected after the last cell.  The tags go to slot_of,
 // which is free between the move and the next search.
-// Both passes take kScatterItems particles per thread, a block's items apart
-// (coalesced), with every item's loads issued before any is used: each
-// particle costs two dependent round trips (its key, then its cell's range),
-// so a thread keeps several in flight.
+// The tag pass takes kScatterItems particles per thread, a block's items apart
+// (coalesced), with every item's loads issued before any is used: a particle
+// costs two dependent round trips (its key, then its cell's range), so a
+// thread keeps several in flight.  The moving pass (one particle per thread)
+// issues its state loads first.
 constexpr int kScatterItems = 4;
 
 template <typename T>
@@ -1882,37 +1893,24 @@ __device__ __forceinline__ uint32_t tags_below(const uint32_t* __restrict__ t, u
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads) scatter_kernel(Bufs<T> b) {
-    const int64_t p0 = (int64_t)blockIdx.x * blockDim.x * kScatterItems + threadIdx.x;
-    uint32_t k[kScatterItems], s0[kScatterItems], s1[kScatterItems];
-#pragma unroll
-    for (int i = 0; i < kScatterItems; ++i) {
-        const int64_t p = p0 + (int64_t)i * blockDim.x;
-        k[i] = p < b.n ? b.key[p] : 0xffffffffu;
+    using V = typename Vec4<T>::type;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= b.n) return;
+    // the particle's own words and state first (independent loads), then its cell's range
+    const uint32_t k = b.key[p], slot = b.slot[p], tag = b.tagB[p];
+    const V P = b.posB[p], Q = b.velB[p];
+    const uint32_t s0 = b.start[k];
+    const uint32_t s1 = k < b.n_keys ? b.start[k + 1] : s0;
+    uint32_t rank = slot;
+    if (s1 > s0 + 1u && s1 - s0 <= kCanonMax && s1 <= (uint32_t)b.n) rank = tags_below(b.slot_of, s0, s1, tag);
+    const uint32_t dst = s0 + rank;
+    if (dst >= (uint32_t)b.n) {  // only after a failed scan; reported as a device error
+        atomicOr(&b.st->error, kErrKeyRange);
+        return;
     }
-#pragma unroll
-    for (int i = 0; i < kScatterItems; ++i) {
-        s0[i] = s1[i] = 0u;
-        if (k[i] != 0xffffffffu) {
-            s0[i] = b.start[k[i]];
-            s1[i] = k[i] < b.n_keys ? b.start[k[i] + 1] : s0[i];
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < kScatterItems; ++i) {
-        const int64_t p = p0 + (int64_t)i * blockDim.x;
-        if (p >= b.n) break;
-        uint32_t rank = b.slot[p];
-        if (s1[i] > s0[i] + 1u && s1[i] - s0[i] <= kCanonMax && s1[i] <= (uint32_t)b.n)
-            rank = tags_below(b.slot_of, s0[i], s1[i], b.tagB[p]);
-        const uint32_t dst = s0[i] + rank;
-        if (dst >= (uint32_t)b.n) {  // only after a failed scan; reported as a device error
-            atomicOr(&b.st->error, kErrKeyRange);
-            continue;
-        }
-        b.posA[dst] = b.posB[p];
-        b.velA[dst] = b.velB[p];
-        b.bkey[dst] = kNoPartner;   // the next search starts from no partner
-    }
+    b.posA[dst] = P;
+    b.velA[dst] = Q;
+    b.bkey[dst] = kNoPartner;   // the next search starts from no partner
 }
 
 // Index (position in the input arrays, p_off + local id) of every particle of
@@ -2280,8 +2278,9 @@ template <typename T>
 cudaError_t launch_tile_search(const Bufs<T>& b, cudaStream_t s) {
     if (b.n == 0 || !b.any_tiled || b.n_keys == 0) return cudaSuccess;
     const size_t smem = tile_smem_bytes(b);
-    if (b.geo.dim == 3) tile_search_kernel<T, 3><<<b.n_keys, b.tile_threads, smem, s>>>(b);
-    else tile_search_kernel<T, 2><<<b.n_keys, b.tile_threads, smem, s>>>(b);
+    const dim3 grid(b.n_keys, sizeof(T) == 4 ? (unsigned)b.tile_split : 1u);   // split windows: binary32 only
+    if (b.geo.dim == 3) tile_search_kernel<T, 3><<<grid, b.tile_threads, smem, s>>>(b);
+    else tile_search_kernel<T, 2><<<grid, b.tile_threads, smem, s>>>(b);
     return cudaGetLastError();
 }
 
@@ -2317,7 +2316,7 @@ cudaError_t launch_scatter(const Bufs<T>& b, cudaStream_t s) {
     if (b.n == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((b.n + (int64_t)kThreads * kScatterItems - 1) / ((int64_t)kThreads * kScatterItems));
     scatter_tags_kernel<T><<<blocks, kThreads, 0, s>>>(b);
-    scatter_kernel<T><<<blocks, kThreads, 0, s>>>(b);
+    scatter_kernel<T><<<blocks_for(b.n), kThreads, 0, s>>>(b);
     return cudaGetLastError();
 }
 

@@ -644,13 +644,15 @@ def test_dsmc_variant_matches_oracle(prec, dim):
     sim.close()
 
 
-@pytest.mark.parametrize("prec,tt,cap", [(32, 64, 64), (32, 128, 768), (32, 256, 6144), (64, 128, 3072),
-                                         (64, 64, 100)])
-def test_tile_search_parameters_do_not_change_results(prec, tt, cap):
-    """Threads per c-bin block and staging capacity of the tile search (the
-    autotuner's choices) change speed only: the closest candidates and pairs
-    equal the oracle's, from a capacity far below one neighbourhood (many
-    staging chunks) to one above it."""
+@pytest.mark.parametrize("prec,tt,cap,split", [(32, 64, 64, 1), (32, 128, 768, 1), (32, 256, 6144, 1),
+                                               (64, 128, 3072, 1), (64, 64, 100, 1), (32, 256, 1536, 2),
+                                               (32, 128, 64, 3), (32, 256, 768, 8)])
+def test_tile_search_parameters_do_not_change_results(prec, tt, cap, split):
+    """Threads per c-bin block, staging capacity and the number of blocks that
+    share a c-bin's window (the autotuner's choices) change speed only: the
+    closest candidates and pairs equal the oracle's, from a capacity far below
+    one neighbourhood (many staging chunks) to one above it, and with up to 8
+    blocks per c-bin (some of them then without candidates)."""
     _setup()
     import paper_1210_8084_gb300 as k
     name, n, dim, n_cells, lo, hi, bc, lam, dt, _ = TILE_CASES[0]
@@ -658,10 +660,10 @@ def test_tile_search_parameters_do_not_change_results(prec, tt, cap):
     if prec == 32:
         pos, vel = f32_state(pos, vel, lo, hi, bc)
     cfg = k.make_config(dim_pos=dim, n_cells=n_cells, lo=lo, hi=hi, bc=bc, lam=lam, dt=dt, seed=5, precision=prec,
-                        flags=k.KMC_FLAG_RECORD, sub_cells=(1, 1, 1), tile_threads=tt, tile_cap=cap)
+                        flags=k.KMC_FLAG_RECORD, sub_cells=(1, 1, 1), tile_threads=tt, tile_cap=cap, tile_split=split)
     sim = k.Simulation(cfg, pos, vel)
     info = sim.info()
-    assert (info.tile_threads, info.tile_cap) == (tt, cap)
+    assert (info.tile_threads, info.tile_cap, info.tile_split) == (tt, cap, split)
     sim.step(1)
     best, partner = sim.partners()
     sim.close()
