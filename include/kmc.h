@@ -127,8 +127,8 @@ typedef struct kmc_config {
     double occupancy_target; /* automatic subdivision: particles per search cell aimed at (0 = 0.5) */
     int flags;          /* KMC_FLAG_* */
     double radial_center[3]; /* centre of the radial velocity moment (KMC_MOM_RADIAL), finite */
-    int tile_threads;   /* search of unsubdivided grids (one block per c-bin): threads per block, 64, 128
-                         * or 256 (0 = 256); speed only, never results */
+    int tile_threads;   /* search of unsubdivided grids (one block per c-bin): threads per block, a
+                         * multiple of 32 from 64 to 256 (0 = 256); speed only, never results */
     int tile_cap;       /* the same: candidates staged in shared memory at once, even, 64 ... 6144 in
                          * binary32, 64 ... 3072 in binary64 (0 = 1536 / 768, 48 KiB); speed only */
     int tile_split;     /* the same, binary32: blocks that share one c-bin's candidates, 1 ... 8 (0 = 1);

@@ -381,8 +381,8 @@ int validate_config(const kmc_config* c, int64_t n) {
         ~(KMC_FLAG_RECORD | KMC_FLAG_NO_GRAPH | KMC_FLAG_STAGED_SEARCH | KMC_FLAG_NO_TILE_SEARCH | KMC_FLAG_ADAPTIVE_DT |
           KMC_FLAG_VELOCITY_2D | KMC_FLAG_DSMC | KMC_FLAG_RADIAL_MOMENT))
         return fail(nullptr, KMC_EINVAL, "unknown flags");
-    if (c->tile_threads != 0 && c->tile_threads != 64 && c->tile_threads != 128 && c->tile_threads != 256)
-        return fail(nullptr, KMC_EINVAL, "tile_threads must be 0, 64, 128 or 256");
+    if (c->tile_threads != 0 && (c->tile_threads < 64 || c->tile_threads > 256 || (c->tile_threads & 31)))
+        return fail(nullptr, KMC_EINVAL, "tile_threads must be 0 or a multiple of 32 from 64 to 256");
     if (c->tile_split < 0 || c->tile_split > 8) return fail(nullptr, KMC_EINVAL, "tile_split must be 0 ... 8");
     if (c->tile_cap != 0 && (c->tile_cap < 64 || (c->tile_cap & 1) || c->tile_cap > (c->precision == 64 ? 3072 : 6144)))
         return fail(nullptr, KMC_EINVAL, "tile_cap must be 0 or even, 64 ... 6144 (binary32) / 3072 (binary64)");

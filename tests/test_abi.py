@@ -90,6 +90,10 @@ def test_invalid_config_is_rejected_without_device(built_lib):
         k.make_config(dt=0.0),
         k.make_config(lam=0.0, sigma=0.0),
         k.make_config(flags=1 << 8),
+        k.make_config(tile_threads=100),
+        k.make_config(tile_threads=288),
+        k.make_config(tile_cap=63),
+        k.make_config(tile_split=9),
     ]
     for cfg in bad:
         with pytest.raises(k.KmcError) as e:

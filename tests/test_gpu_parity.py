@@ -646,7 +646,8 @@ def test_dsmc_variant_matches_oracle(prec, dim):
 
 @pytest.mark.parametrize("prec,tt,cap,split", [(32, 64, 64, 1), (32, 128, 768, 1), (32, 256, 6144, 1),
                                                (64, 128, 3072, 1), (64, 64, 100, 1), (32, 256, 1536, 2),
-                                               (32, 128, 64, 3), (32, 256, 768, 8)])
+                                               (32, 128, 64, 3), (32, 256, 768, 8),
+                                               (32, 96, 1536, 1), (64, 224, 768, 1)])
 def test_tile_search_parameters_do_not_change_results(prec, tt, cap, split):
     """Threads per c-bin block, staging capacity and the number of blocks that
     share a c-bin's window (the autotuner's choices) change speed only: the
