@@ -247,6 +247,7 @@ def run_device(k, w, seed, steps, warmup, stream, occ=0.0, clocks=None, barrier=
     sim.step_profiled(warmup, want_moments=1)
     if barrier:
         barrier()
+    tests0 = sim.tile_tests()
     if clocks:
         clocks.start()
     if barrier:
@@ -255,9 +256,10 @@ def run_device(k, w, seed, steps, warmup, stream, occ=0.0, clocks=None, barrier=
     if barrier:
         barrier()
     clk = clocks.stop() if clocks else None
+    tests = (sim.tile_tests() - tests0) / (w["n"] * steps) if info.tile_prune and info.n_search_cells else None
     raw, der, glob = sim.moments()
     out = dict(prof=prof, info=info, clocks=clk, pairs=float(glob[0, 6]), e_start=float(e_start),
-               e_end=float(glob[0, 1]), cand=sim.window_size(), cfg=cfg, pos=pos, vel=vel)
+               e_end=float(glob[0, 1]), cand=sim.window_size(), cfg=cfg, pos=pos, vel=vel, tile_tests=tests)
     sim.close()
     torch.cuda.synchronize()
     return out
@@ -277,7 +279,10 @@ def roofline_of(w, r, steps, n_sm, peaks, peak_src, workload):
         # particle holds C_p candidates (itself included); binary32 tests every
         # unordered pair once, (C_p - 1) / 2 per particle, binary64 all C_p.
         cand = r["cand"]
-        tests = (cand - 1.0) / 2.0 if w["precision"] == 32 else cand
+        plain = (cand - 1.0) / 2.0 if w["precision"] == 32 else cand
+        # the pruned tile search counts the tests it makes (homes x staged slots of the clusters tested)
+        pruned = dom == "tile" and r.get("tile_tests") is not None
+        tests = r["tile_tests"] if pruned else plain
         flops = FLOPS_PER_TEST * tests * n
         if w["precision"] == 32:
             sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -291,6 +296,10 @@ def roofline_of(w, r, steps, n_sm, peaks, peak_src, workload):
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": src,
                 "ms_per_launch": round(phases[dom], 4), "algorithmic_flops_per_launch": int(flops),
                 "candidates_per_particle": round(cand, 3), "pair_tests_per_particle": round(tests, 3)}
+        if pruned:
+            roof["pair_tests_source"] = "counted by the pruned tile search (clusters of 8 out of reach skipped)"
+            roof["plain_pair_tests_per_particle"] = round(plain, 3)
+            roof["plain_equivalent_tflops"] = round(FLOPS_PER_TEST * plain * n / t_dom / 1e12, 3)
         if traffic is not None:
             roof["traffic_gbs"] = round(traffic / t_dom / 1e9, 1)
     else:
@@ -339,7 +348,8 @@ def ours(args):
 
     # ---------------- device-resident throughput (inputs already in HBM)
     r = run_device(k, w, seed, args.steps, args.warmup, stream, occ=args.occ, clocks=ClockSampler(local),
-                   barrier=barrier, tile=(args.tile_threads, args.tile_cap, args.tile_split))
+                   barrier=barrier, tile=(args.tile_threads, args.tile_cap, args.tile_split),
+                   flags=k.KMC_FLAG_NO_TILE_PRUNE if args.no_prune else 0)
     elapsed_ms = max_over_ranks([r["prof"]["total"]], world, "cuda")[0]
     pos, vel, cfg = r.pop("pos"), r.pop("vel"), r["cfg"]
 
@@ -389,6 +399,7 @@ def ours(args):
                    "precision": w["precision"], "search_cells": int(info.n_search_cells),
                    "sub_cells": list(info.sub_cells), "occupancy_target": args.occ,
                    "tile_threads": info.tile_threads, "tile_cap": info.tile_cap, "tile_split": info.tile_split,
+                   "tile_prune": info.tile_prune,
                    "l2": "no flush: state 2 x %.2f GB > 129 MB L2" % (n * 32 / 1e9),
                    "parallelism": f"replicas x{world}", "n_sm": n_sm},
         "phase_ms_per_step": {p: round(v, 4) for p, v in phases.items()},
@@ -701,6 +712,7 @@ def main():
     ap.add_argument("--tile-threads", type=int, default=0, help="tile search threads per c-bin block (0: default)")
     ap.add_argument("--tile-cap", type=int, default=0, help="tile search staging capacity (0: default)")
     ap.add_argument("--tile-split", type=int, default=0, help="tile search blocks per c-bin (0: default)")
+    ap.add_argument("--no-prune", action="store_true", help="binary32 tile search without cluster pruning")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

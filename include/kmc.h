@@ -82,6 +82,11 @@ extern "C" {
                             * must be 0 or 1).  Collided particles count as paired in the moments (zero virial);
                             * kmc_get_partners reports -1 */
 #define KMC_FLAG_RADIAL_MOMENT 128 /* also accumulate the radial velocity per c-bin (KMC_MOM_RADIAL, Eq. vel_r) */
+#define KMC_FLAG_NO_TILE_PRUNE 256 /* binary32 tile search: test every (home, candidate) pair of a c-bin block.  By
+                                    * default, where the contact distance R is at most half the narrowest c-bin
+                                    * width, the homes of a warp skip every cluster of 8 candidates whose swept box
+                                    * (positions over the step) stays farther than R, plus a rounding margin, from
+                                    * theirs; same results */
 #define KMC_FLAG_ADAPTIVE_DT 16  /* timestep dt(t) = dx_min / v_max(t) of each step's start state (Sect. "Simulation
                                   * setup"; dx_min the smallest c-bin width, v_max the largest speed of the instance,
                                   * |v|^2 = fma(vz, vz, fma(vy, vy, vx vx)) in the state precision, the quotient in
@@ -140,6 +145,14 @@ typedef struct kmc_config {
  * restricted to the search cells that can hold a candidate).  Synchronises. */
 KMC_API int kmc_window_size(kmc_handle* h, double* mean_candidates);
 
+/* Pair tests the binary32 tile search has evaluated since kmc_init with its
+ * pruning (KMC_FLAG_NO_TILE_PRUNE unset): for every cluster of 8 staged
+ * candidates that a warp tests, 8 x the homes of the warp (padding slots of a
+ * window row's last cluster included).  0 for handles without that search.
+ * The plain tile search tests (C_p - 1) / 2 pairs per particle, C_p from
+ * kmc_window_size.  Synchronises the handle's stream. */
+KMC_API int kmc_tile_tests(kmc_handle* h, double* tests);
+
 /* Read-only description of a handle (kmc_get_info). */
 typedef struct kmc_info {
     int64_t n_particles;     /* total over instances */
@@ -168,6 +181,8 @@ typedef struct kmc_info {
     int graph_mode;          /* how the last kmc_step ran: 2 = one CUDA graph for all its steps (a device-side
                               * loop counter drives a conditional while node), 1 = one graph per step,
                               * 0 = kernel by kernel (KMC_FLAG_NO_GRAPH, or before the first kmc_step) */
+    int tile_prune;          /* 1: the binary32 tile search skips candidate clusters out of reach (for some
+                              * instance) */
 } kmc_info;
 
 /* Create a simulation.  pos and vel are n x 3 row-major arrays of float
@@ -265,7 +280,7 @@ KMC_API int kmc_get_partners(kmc_handle* h, int32_t* best, int32_t* partner, int
  * kmc_init, warmed up for one step and timed over trial_steps >= 1 steps with
  * CUDA events on its stream, then freed; the caller's data are only read.
  * *best receives a copy of *cfg with occupancy_target, tile_threads, tile_cap,
- * tile_split and flags (the KMC_FLAG_NO_TILE_SEARCH / KMC_FLAG_STAGED_SEARCH bits) of the
+ * tile_split and flags (the KMC_FLAG_NO_TILE_SEARCH / KMC_FLAG_STAGED_SEARCH / KMC_FLAG_NO_TILE_PRUNE bits) of the
  * fastest setting and sub_cells = 0 (automatic); *ms_per_step (may be NULL)
  * its time.
  * Device memory: one handle at a time.  Synchronises cfg->stream.  Returns

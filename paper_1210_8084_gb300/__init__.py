@@ -39,6 +39,7 @@ KMC_FLAG_ADAPTIVE_DT = 16
 KMC_FLAG_VELOCITY_2D = 32
 KMC_FLAG_DSMC = 64
 KMC_FLAG_RADIAL_MOMENT = 128
+KMC_FLAG_NO_TILE_PRUNE = 256
 KMC_MOM_RAW = 1
 KMC_MOM_DERIVED = 2
 KMC_MOM_GLOBAL = 4
@@ -50,7 +51,7 @@ ABI_FUNCTIONS = (
     "kmc_init", "kmc_step", "kmc_moments", "kmc_moments_size", "kmc_free", "kmc_sync",
     "kmc_last_error", "kmc_get_info", "kmc_get_state", "kmc_set_state", "kmc_get_cell_keys",
     "kmc_get_partners", "kmc_step_profiled", "kmc_find_partners_noalloc", "kmc_window_size", "kmc_autotune",
-    "kmc_get_perm", "kmc_test_hold_scan",
+    "kmc_get_perm", "kmc_test_hold_scan", "kmc_tile_tests",
 )
 KMC_STATIC_MAX_PARTICLES = 262144
 
@@ -116,6 +117,7 @@ class KmcInfo(ctypes.Structure):
         ("tile_cap", ctypes.c_int),
         ("tile_split", ctypes.c_int),
         ("graph_mode", ctypes.c_int),
+        ("tile_prune", ctypes.c_int),
     ]
 
 
@@ -165,6 +167,8 @@ def _load():
     L.kmc_step_profiled.restype = ctypes.c_int
     L.kmc_window_size.argtypes = [H, ctypes.POINTER(ctypes.c_double)]
     L.kmc_window_size.restype = ctypes.c_int
+    L.kmc_tile_tests.argtypes = [H, ctypes.POINTER(ctypes.c_double)]
+    L.kmc_tile_tests.restype = ctypes.c_int
     L.kmc_find_partners_noalloc.argtypes = [ctypes.POINTER(KmcConfig), ctypes.c_int64, vp, vp, vp]
     L.kmc_find_partners_noalloc.restype = ctypes.c_int
     L.kmc_autotune.argtypes = [ctypes.POINTER(KmcConfig), ctypes.c_int64, vp, vp, ctypes.c_int, ctypes.c_int,
@@ -290,6 +294,13 @@ def kmc_window_size(h):
     return v.value
 
 
+def kmc_tile_tests(h):
+    """Pair tests made by the pruned binary32 tile search since kmc_init."""
+    v = ctypes.c_double()
+    _check(load().kmc_tile_tests(h, ctypes.byref(v)), h)
+    return v.value
+
+
 def kmc_find_partners_noalloc(cfg, n, pos, vel, best):
     """Closest candidate of every particle of a device-resident state, with no
     allocation (scratch in the library's fixed device array).  pos, vel, best
@@ -402,6 +413,9 @@ class Simulation:
 
     def window_size(self):
         return kmc_window_size(self.h)
+
+    def tile_tests(self):
+        return kmc_tile_tests(self.h)
 
     def state(self):
         pos = np.zeros((self.n, 3), dtype=self.dtype)

@@ -48,13 +48,14 @@ struct kmc_handle {
     DevState* st_d = nullptr;
     unsigned long long* acc = nullptr;
     unsigned long long* gacc = nullptr;   // per-instance integer totals (zero between reductions)
+    unsigned long long* tile_tests = nullptr;   // [kTestSlots] pair tests of the pruned tile search, cumulative
     double *mom = nullptr, *glob = nullptr;
     int32_t *rec_best = nullptr, *rec_partner = nullptr;
     uint32_t n_keys = 0, n_tiles = 0;
     uint32_t id_bits = 32;
     uint32_t n_stage_tiles = 0;
     int stage_cap = 0, stage_rows = 0, stage_stride = 0, stage_pair_cap = 0, any_direct = 1, any_tiled = 0;
-    int tile_threads = 256, tile_cap = 1536, tile_split = 1;
+    int tile_threads = 256, tile_cap = 1536, tile_split = 1, tile_prune = 1;
     int64_t n_bins = 0, bins_per_inst = 0;
     int64_t bytes = 0;
     int mom_state = 0;  // 1: acc/mom/glob describe the current state
@@ -142,6 +143,8 @@ Bufs<T> make_bufs(const kmc_handle* h) {
     b.tile_threads = h->tile_threads;
     b.tile_cap = h->tile_cap;
     b.tile_split = h->tile_split;
+    b.tile_prune = h->tile_prune;
+    b.tile_tests = h->tile_tests;
     b.id_bits = h->id_bits;
     b.id_mask = h->id_bits >= 32 ? 0xffffffffu : ((1u << h->id_bits) - 1u);
     return b;
@@ -379,7 +382,7 @@ int validate_config(const kmc_config* c, int64_t n) {
     if (c->n_instances > 1 && !c->instances) return fail(nullptr, KMC_EINVAL, "instances is NULL");
     if (c->flags &
         ~(KMC_FLAG_RECORD | KMC_FLAG_NO_GRAPH | KMC_FLAG_STAGED_SEARCH | KMC_FLAG_NO_TILE_SEARCH | KMC_FLAG_ADAPTIVE_DT |
-          KMC_FLAG_VELOCITY_2D | KMC_FLAG_DSMC | KMC_FLAG_RADIAL_MOMENT))
+          KMC_FLAG_VELOCITY_2D | KMC_FLAG_DSMC | KMC_FLAG_RADIAL_MOMENT | KMC_FLAG_NO_TILE_PRUNE))
         return fail(nullptr, KMC_EINVAL, "unknown flags");
     if (c->tile_threads != 0 && (c->tile_threads < 64 || c->tile_threads > 256 || (c->tile_threads & 31)))
         return fail(nullptr, KMC_EINVAL, "tile_threads must be 0 or a multiple of 32 from 64 to 256");
@@ -517,6 +520,7 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
     h->tile_threads = cfg->tile_threads > 0 ? cfg->tile_threads : 256;
     h->tile_cap = cfg->tile_cap > 0 ? cfg->tile_cap : (h->precision == 64 ? 768 : 1536);
     h->tile_split = h->precision == 64 ? 1 : (cfg->tile_split > 0 ? cfg->tile_split : 1);
+    h->tile_prune = h->precision == 32 && !(cfg->flags & KMC_FLAG_NO_TILE_PRUNE) ? 1 : 0;
 
     Geo& g = h->geo;
     g.dim = h->dim;
@@ -620,6 +624,9 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
     if ((rc = dev_alloc(h, (void**)&h->mom, sizeof(double) * kMomStride * (size_t)h->n_bins))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->glob, sizeof(double) * 8 * (size_t)h->n_inst))) return bail(rc);
     if ((rc = dev_alloc(h, (void**)&h->gacc, sizeof(unsigned long long) * 8 * (size_t)h->n_inst))) return bail(rc);
+    if ((rc = dev_alloc(h, (void**)&h->tile_tests, sizeof(unsigned long long) * kTestSlots))) return bail(rc);
+    if (cudaMemsetAsync(h->tile_tests, 0, sizeof(unsigned long long) * kTestSlots, h->stream) != cudaSuccess)
+        return bail(fail(h, KMC_ECUDA, "memset of the tile-search test counters failed"));
     if (cudaMemsetAsync(h->gacc, 0, sizeof(unsigned long long) * 8 * (size_t)h->n_inst, h->stream) != cudaSuccess)
         return bail(fail(h, KMC_ECUDA, "memset of the moment totals failed"));
     if (cfg->flags & KMC_FLAG_RECORD) {
@@ -684,6 +691,7 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
         // search cells that are the c-bins themselves: one block per cell
         h->any_tiled = 0;
         h->any_direct = 0;
+        int prune_any = 0;
         const bool dsmc = (h->cfg.flags & KMC_FLAG_DSMC) != 0;
         for (auto& I : h->inst_h) {
             if (dsmc) {   // no closest-approach search at all
@@ -694,7 +702,14 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
                       !(h->cfg.flags & KMC_FLAG_NO_TILE_SEARCH);
             h->any_tiled |= I.tiled;
             h->any_direct |= !I.tiled && !I.staged;   // searched one thread per particle
+            // pruning pays only where the contact distance is well inside a c-bin
+            // (a wider one puts every cluster of the window within reach)
+            double wmin = h->geo.L[0] / h->geo.n[0];
+            for (int d = 1; d < h->dim; ++d) wmin = std::min(wmin, h->geo.L[d] / h->geo.n[d]);
+            I.prune = I.tiled && h->tile_prune && sqrt(I.R2) <= 0.5 * wmin;
+            prune_any |= I.prune;
         }
+        h->tile_prune = prune_any;
         if (cudaMemcpyAsync(h->inst_d, h->inst_h.data(), sizeof(InstDev) * h->n_inst, cudaMemcpyHostToDevice,
                             h->stream) != cudaSuccess)
             return bail(fail(h, KMC_ECUDA, "upload of instance table failed"));
@@ -880,7 +895,7 @@ int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, const void* 
         int flags;
         int tile_threads, tile_cap, tile_split;
     };
-    const int keep = cfg->flags & ~(KMC_FLAG_NO_TILE_SEARCH | KMC_FLAG_STAGED_SEARCH);
+    const int keep = cfg->flags & ~(KMC_FLAG_NO_TILE_SEARCH | KMC_FLAG_STAGED_SEARCH | KMC_FLAG_NO_TILE_PRUNE);
     const int cap0 = cfg->precision == 64 ? 768 : 1536;
     std::vector<Trial> trials;
     for (double occ : {0.25, 0.35, 0.5, 0.7, 1.0, 1.5}) trials.push_back({occ, keep, 0, 0, 0});
@@ -889,6 +904,7 @@ int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, const void* 
     const int tile_opts[][3] = {{128, cap0, 1}, {256, 2 * cap0, 1}, {128, cap0 / 2, 1}, {256, cap0 / 2, 1},
                                 {64, cap0 / 2, 1},   {256, cap0, 2},     {256, cap0, 3},      {128, cap0 / 2, 2}};
     for (const auto& t : tile_opts) trials.push_back({0.0, keep, t[0], t[1], t[2]});
+    if (cfg->precision == 32) trials.push_back({0.0, keep | KMC_FLAG_NO_TILE_PRUNE, 0, 0, 0});
     trials.push_back({0.0, keep | KMC_FLAG_NO_TILE_SEARCH, 0, 0, 0});
     if (cfg->dim_pos == 3 && !(cfg->flags & KMC_FLAG_DSMC)) trials.push_back({0.0, keep | KMC_FLAG_STAGED_SEARCH, 0, 0, 0});
     double best_ms = -1.0;
@@ -917,6 +933,7 @@ int kmc_autotune(const kmc_config* cfg, int64_t n, const void* pos, const void* 
         setup.push_back(h->any_tiled ? h->tile_threads : 0);
         setup.push_back(h->any_tiled ? h->tile_cap : 0);
         setup.push_back(h->any_tiled ? h->tile_split : 0);
+        setup.push_back(h->any_tiled ? h->tile_prune : 0);
         if (std::find(tried.begin(), tried.end(), setup) != tried.end()) {
             kmc_free(h);
             continue;
@@ -995,6 +1012,7 @@ int kmc_get_info(kmc_handle* h, kmc_info* info) {
     info->tile_threads = h->tile_threads;
     info->tile_cap = h->tile_cap;
     info->tile_split = h->tile_split;
+    info->tile_prune = h->tile_prune;
     info->graph_mode = (h->cfg.flags & KMC_FLAG_NO_GRAPH) || h->graph_failed
                            ? 0
                            : ((h->loop_graph[0] || h->loop_graph[1]) ? 2 : (h->loop_failed ? 1 : 0));
@@ -1015,6 +1033,17 @@ int kmc_window_size(kmc_handle* h, double* mean_candidates) {
     KMC_CUDA(h, cudaMemcpyAsync(&t, total, sizeof(t), cudaMemcpyDeviceToHost, h->stream));
     KMC_CUDA(h, cudaStreamSynchronize(h->stream));
     *mean_candidates = (double)t / (double)h->n;
+    return KMC_OK;
+}
+
+int kmc_tile_tests(kmc_handle* h, double* tests) {
+    if (!h || !tests) return fail(h, KMC_EINVAL, "NULL argument");
+    unsigned long long t[kTestSlots];
+    KMC_CUDA(h, cudaMemcpyAsync(t, h->tile_tests, sizeof(t), cudaMemcpyDeviceToHost, h->stream));
+    KMC_CUDA(h, cudaStreamSynchronize(h->stream));
+    double sum = 0.0;
+    for (int i = 0; i < kTestSlots; ++i) sum += (double)t[i];
+    *tests = sum;
     return KMC_OK;
 }
 

@@ -19,6 +19,7 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 constexpr uint32_t kSpinCap = 1u << 22;  // bounded waits: iterations before giving up
 constexpr int kFoldCap = 64;           // wall folds per coordinate per step
 constexpr int kAccFields = 10;         // per c-bin accumulator: N, Sum v (3), Sum v^2 (3), Sum W, collided
+constexpr int kTestSlots = 256;        // counters of the pruned tile search's pair tests (blocks spread over them)
                                        // count, Sum v.r_hat
 constexpr int kMomStride = 18;         // per c-bin output: 8 raw, 8 derived, Sum v.r_hat, v_r
 constexpr uint32_t kCanonMax = 16384;  // search cells up to this many particles are put in id order
@@ -50,6 +51,7 @@ struct InstDev {
     // shared memory before the search
     int staged;
     int tiled;           // search cells are the c-bins: one block per cell (tile_search_kernel)
+    int prune;           // tiled, binary32: candidate clusters out of a warp's reach are skipped
     int adaptive;        // timestep dx_min / v_max(t) per step (Sect. "Simulation setup")
     double dx_min;       // smallest c-bin width over the position dimensions
     int tile_rows;
@@ -142,9 +144,11 @@ struct Bufs {
     int any_tiled;           // some instance uses the tile search (one block per c-bin)
     int dsmc;                // the random-partner comparison variant instead of the PoCA search
     int radial;              // accumulate Sum v.r_hat (KMC_FLAG_RADIAL_MOMENT)
-    int tile_threads;        // tile search: threads per c-bin block (64, 128 or 256)
+    int tile_threads;        // tile search: threads per c-bin block (a multiple of 32, 64 ... 256)
     int tile_cap;            // tile search: candidates staged in shared memory at once (even)
     int tile_split;          // tile search: blocks sharing one c-bin's window (binary32)
+    int tile_prune;          // tile search, binary32: skip candidate clusters out of a warp's reach
+    unsigned long long* tile_tests;  // [kTestSlots] pair tests made by the pruned tile search (cumulative; may be null)
     // particle tag = (instance << id_bits) | instance-local id
     uint32_t id_bits;        // 32 when there is one instance
     uint32_t id_mask;

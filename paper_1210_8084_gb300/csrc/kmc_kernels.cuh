@@ -891,6 +891,73 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) search_kerne
     }
 }
 
+// ------------------------------------------------------ paired binary32 test
+// A home particle of the paired test: its coordinates, the periodic image
+// shift of the candidates' range and the step's constants, each in both
+// halves of a float2.
+struct PairHome {
+    float2 x0, x1, x2, v0, v1, v2, s0, s1, s2, dt2, mR2;
+};
+
+__device__ __forceinline__ PairHome pair_home(const float xi[3], const float vi[3], const float sh[3], float dt,
+                                              float R2) {
+    PairHome h;
+    h.x0 = make_float2(xi[0], xi[0]);
+    h.x1 = make_float2(xi[1], xi[1]);
+    h.x2 = make_float2(xi[2], xi[2]);
+    h.v0 = make_float2(vi[0], vi[0]);
+    h.v1 = make_float2(vi[1], vi[1]);
+    h.v2 = make_float2(vi[2], vi[2]);
+    h.s0 = make_float2(sh[0], sh[0]);
+    h.s1 = make_float2(sh[1], sh[1]);
+    h.s2 = make_float2(sh[2], sh[2]);
+    h.dt2 = make_float2(dt, dt);
+    h.mR2 = make_float2(-R2, -R2);   // r2 - R^2 as r2 + (-R^2): the same rounding
+    return h;
+}
+
+// Criteria 1-2 of the acceptance test (Eqs. 5-6, 8-9) for one home against the
+// two candidates of a staged pair in the negated layout A = (-x, -x', -y, -y'),
+// B = (-z, -z', -vx, -vx'), C = (-vy, -vy', -vz, -vz').  Each component of
+// __fadd2_rn / __fmul2_rn / __ffma2_rn rounds exactly as the scalar operation,
+// and x - y is x + (-y) in IEEE arithmetic, so the decisions are bit for bit
+// those of poca_test_sh; the real-root test is evaluated for both candidates
+// so that no lane branches off for criterion 2, and b > 0 needs no test of its
+// own (a < 0 and fma(b, dt, a) > 0 give b dt > -a > 0 exactly).  Bit 0 / 1 of
+// the result: the first / second candidate passes; rr, a, bb give d^2 of a
+// passing candidate.
+template <int DIM, bool SH>
+__device__ __forceinline__ unsigned paired_test(const PairHome& h, const float4 A, const float4 B, const float4 C,
+                                                float2& rr, float2& a, float2& bb) {
+    float2 d0 = __fadd2_rn(h.x0, make_float2(A.x, A.y));
+    float2 d1 = __fadd2_rn(h.x1, make_float2(A.z, A.w));
+    float2 d2v = make_float2(0.f, 0.f);
+    if (DIM == 3) d2v = __fadd2_rn(h.x2, make_float2(B.x, B.y));
+    if (SH) {
+        d0 = __fadd2_rn(d0, h.s0);
+        d1 = __fadd2_rn(d1, h.s1);
+        if (DIM == 3) d2v = __fadd2_rn(d2v, h.s2);
+    }
+    const float2 u0 = __fadd2_rn(h.v0, make_float2(B.z, B.w));
+    const float2 u1 = __fadd2_rn(h.v1, make_float2(C.x, C.y));
+    a = __fmul2_rn(d0, u0);
+    a = __ffma2_rn(d1, u1, a);
+    bb = __fmul2_rn(u0, u0);
+    bb = __ffma2_rn(u1, u1, bb);
+    rr = __fmul2_rn(d0, d0);
+    rr = __ffma2_rn(d1, d1, rr);
+    if (DIM == 3) {
+        const float2 u2 = __fadd2_rn(h.v2, make_float2(C.z, C.w));
+        a = __ffma2_rn(d2v, u2, a);
+        bb = __ffma2_rn(u2, u2, bb);
+        rr = __ffma2_rn(d2v, d2v, rr);
+    }
+    const float2 f = __ffma2_rn(bb, h.dt2, a);
+    const float2 y = __fmul2_rn(bb, __fadd2_rn(rr, h.mR2));
+    const float2 disc = __ffma2_rn(a, a, make_float2(-y.x, -y.y));
+    return ((a.x < 0.f && f.x > 0.f && disc.x >= 0.f) ? 1u : 0u) | ((a.y < 0.f && f.y > 0.f && disc.y >= 0.f) ? 2u : 0u);
+}
+
 // ------------------------------------------------------ tile search
 // Instances whose search cells are the c-bins themselves (no subdivision):
 // every particle of a cell has the same window, the 3^D c-bin neighbourhood
@@ -914,14 +981,16 @@ struct TileCap<double> {
     static constexpr int value = 768;
 };
 
-template <typename T, int DIM, bool MINIMG>
-__device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>& G, const InstDev& I, int inst,
-                                                 uint32_t kc, int64_t h0, int64_t h1, typename Vec4<T>::type* sp,
-                                                 typename Vec4<T>::type* sv, int* rq0, int* rlen, int* rpre,
-                                                 T (*rsh)[3], int& nr_s, int& tot_s) {
-    using V = typename Vec4<T>::type;
+// The rows of c-bin kc's window as key ranges of sorted positions (one per
+// row and part of the fast dimension, with the row's periodic image shift):
+// range r is [rq0[r], rq0[r] + rlen[r]), at offset rpre[r] of the ranges'
+// concatenation; nr_s ranges, tot_s candidates.  Binary32 (symmetric) keeps
+// only positions from the cell's own first one h0 on.  Block-wide (syncs).
+template <typename T, int DIM>
+__device__ __forceinline__ void tile_window_ranges(const Bufs<T>& b, const GeoT<T>& G, const InstDev& I, int inst,
+                                                   uint32_t kc, int64_t h0, int* rq0, int* rlen, int* rpre,
+                                                   T (*rsh)[3], int& nr_s, int& tot_s) {
     constexpr bool kSym = sizeof(T) == 4;
-    const int CAP = b.tile_cap;   // even
     const int tid = threadIdx.x;
     // cell coordinates from the key (x slowest)
     uint32_t rel = kc - I.key_base;
@@ -992,6 +1061,18 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
         tot_s = acc;
     }
     __syncthreads();
+}
+
+template <typename T, int DIM, bool MINIMG>
+__device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>& G, const InstDev& I, int inst,
+                                                 uint32_t kc, int64_t h0, int64_t h1, typename Vec4<T>::type* sp,
+                                                 typename Vec4<T>::type* sv, int* rq0, int* rlen, int* rpre,
+                                                 T (*rsh)[3], int& nr_s, int& tot_s) {
+    using V = typename Vec4<T>::type;
+    constexpr bool kSym = sizeof(T) == 4;
+    const int CAP = b.tile_cap;   // even
+    const int tid = threadIdx.x;
+    tile_window_ranges<T, DIM>(b, G, I, inst, kc, h0, rq0, rlen, rpre, rsh, nr_s, tot_s);
     const int nr = nr_s, total = tot_s;
     // The window may be split between tile_split blocks of the same c-bin
     // (blockIdx.y = part), each taking every tile_split-th chunk of `per`
@@ -1123,55 +1204,17 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
                 auto close = [&](float rr, float a, float bb, uint32_t idj, int32_t q) {
                     take(R<float>::sub(rr, R<float>::div(R<float>::mul(a, a), bb)), idj, q);
                 };
-                const float2 xi0 = make_float2(xi[0], xi[0]), xi1 = make_float2(xi[1], xi[1]);
-                const float2 xi2 = make_float2(xi[2], xi[2]);
-                const float2 vi0 = make_float2(vi[0], vi[0]), vi1 = make_float2(vi[1], vi[1]);
-                const float2 vi2 = make_float2(vi[2], vi[2]);
-                const float2 sh0 = make_float2(sh[0], sh[0]), sh1 = make_float2(sh[1], sh[1]);
-                const float2 sh2 = make_float2(sh[2], sh[2]);
-                const float2 dt2 = make_float2(dt, dt);
-                const float2 mR2 = make_float2(-R2, -R2);   // r2 - R^2 as r2 + (-R^2): the same rounding
+                const PairHome ph = pair_home(xi, vi, sh, dt, R2);
                 int e = e0;
                 if ((e - c0) & 1) one(e++);
-                // Both candidates go through the whole test in paired form, the
-                // real-root test included, so that no lane branches off for
-                // criterion 2: only a candidate that passes all of criteria 1-2
-                // (about one test in a thousand) leaves the paired path, for d^2.
-                // b > 0 needs no test of its own: a < 0 and fma(b, dt, a) > 0
-                // give b dt > -a > 0 exactly (the rounding keeps the sign).
-                // the whole test of staged pair k (candidates 2k, 2k + 1 of the chunk);
-                // bit 0 / 1 of the result: candidate passes criteria 1-2
+                // Only a candidate that passes all of criteria 1-2 (about one test
+                // in a thousand) leaves the paired path, for d^2.  The whole test
+                // of staged pair k (candidates 2k, 2k + 1 of the chunk); bit 0 / 1
+                // of the result: candidate passes criteria 1-2
                 auto test2 = [&](int k, int32_t q, float2& rr, float2& a, float2& bb) -> unsigned {
-                    const float4 A = pA[k], B = pB[k], C = pC[k];
-                    float2 d0 = __fadd2_rn(xi0, make_float2(A.x, A.y));
-                    float2 d1 = __fadd2_rn(xi1, make_float2(A.z, A.w));
-                    float2 d2v = make_float2(0.f, 0.f);
-                    if (DIM == 3) d2v = __fadd2_rn(xi2, make_float2(B.x, B.y));
-                    if (SH) {
-                        d0 = __fadd2_rn(d0, sh0);
-                        d1 = __fadd2_rn(d1, sh1);
-                        if (DIM == 3) d2v = __fadd2_rn(d2v, sh2);
-                    }
-                    const float2 u0 = __fadd2_rn(vi0, make_float2(B.z, B.w));
-                    const float2 u1 = __fadd2_rn(vi1, make_float2(C.x, C.y));
-                    a = __fmul2_rn(d0, u0);
-                    a = __ffma2_rn(d1, u1, a);
-                    bb = __fmul2_rn(u0, u0);
-                    bb = __ffma2_rn(u1, u1, bb);
-                    rr = __fmul2_rn(d0, d0);
-                    rr = __ffma2_rn(d1, d1, rr);
-                    if (DIM == 3) {
-                        const float2 u2 = __fadd2_rn(vi2, make_float2(C.z, C.w));
-                        a = __ffma2_rn(d2v, u2, a);
-                        bb = __ffma2_rn(u2, u2, bb);
-                        rr = __ffma2_rn(d2v, d2v, rr);
-                    }
-                    const float2 f = __ffma2_rn(bb, dt2, a);
-                    const float2 y = __fmul2_rn(bb, __fadd2_rn(rr, mR2));
-                    const float2 disc = __ffma2_rn(a, a, make_float2(-y.x, -y.y));
-                    const bool ok0 = (!CHK || q > lim) && a.x < 0.f && f.x > 0.f && disc.x >= 0.f;
-                    const bool ok1 = (!CHK || q + 1 > lim) && a.y < 0.f && f.y > 0.f && disc.y >= 0.f;
-                    return (ok0 ? 1u : 0u) | (ok1 ? 2u : 0u);
+                    unsigned ok = paired_test<DIM, SH>(ph, pA[k], pB[k], pC[k], rr, a, bb);
+                    if (CHK) ok &= (q > lim ? 1u : 0u) | (q + 1 > lim ? 2u : 0u);
+                    return ok;
                 };
                 auto take2 = [&](unsigned ok, int k, int32_t q, float2 rr, float2 a, float2 bb) {
                     const uint2 tg = pT[k];
@@ -1245,6 +1288,367 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
     }
 }
 
+// ------------------------------------------------------ pruned tile search (binary32)
+// In a dense window almost every (home, candidate) pair of the tile search is
+// too far apart to meet within the step: a pair can pass criteria 1-2 only if,
+// at some time t in [0, dt], the two particles are within R of each other in
+// every coordinate.  So every particle is bounded by its swept box (the box of
+// the segment x .. x + v dt), the homes of a warp and each cluster of
+// kCluster staged candidates by the union of theirs, and a warp tests a
+// cluster only when its box, widened by R and a rounding margin, overlaps the
+// cluster's.  For small boxes the homes of a block (by quarter c-bin, in Morton
+// order) and the candidates of each window row (by half c-bin) are
+// counting-sorted in shared memory before they are grouped.  The order of the
+// tests changes nothing: each home keeps the minimum of its keys and every
+// partner key is an atomicMin.
+//
+// Rounding margin.  For a pair that the binary32 test accepts, exact arithmetic
+// on its rounded differences gives d^2 <= R^2 + 15 u |dr|^2 (u = 2^-24; the
+// error of disc is at most 14 u b |dr|^2), a crossing time within
+// 3 u |dr| / |dv| + 6 u dt of [0, dt], and differences within 6 u C of the
+// exact ones (C bounds every coordinate plus an image shift).  So at a time in
+// [0, dt] the two particles are within R + sqrt(15 u) |dr| + 3 u |dr| +
+// 7 u |dv| dt + 6 u C of each other in every coordinate.  With |dr| <=
+// 2 sqrt(3) w (w the widest c-bin: both lie in one 3^D neighbourhood) that is
+// below R (1 + 2^-10) + 2^-7 w + 2^-16 C, the warp's widening, plus 2^-12 of
+// each particle's |v dt|_1, the widening of every swept box.
+constexpr int kCluster = 4;      // staged candidates per cluster (two staged pairs: one step of the loop)
+constexpr int kHomeBuckets = 64; // home order inside a c-bin: quarter c-bins in Morton order
+constexpr int kRowBuckets = 24;  // buckets of a window row: 6 half c-bins along the fast dimension x 2 x 2
+
+// Index of the half c-bin of coordinate x along dimension d (any integer that
+// groups nearby particles serves: it orders, never decides).
+__device__ __forceinline__ int half_cbin(const GeoT<float>& G, float x, int d) {
+    const float t = (x - G.lo[d]) * G.inv[d] * 2.0f;
+    return t > 0.f ? (int)fminf(t, 1.0e9f) : 0;
+}
+
+// Quarter c-bin of coordinate x along dimension d, 0 ... 3 (ordering only).
+__device__ __forceinline__ int quarter_cbin(const GeoT<float>& G, float x, int d) {
+    const float t = (x - G.lo[d]) * G.inv[d] * 4.0f;
+    return (t > 0.f ? (int)fminf(t, 1.0e9f) : 0) & 3;
+}
+
+// Bucket of a home inside its c-bin: its quarter c-bin in every dimension, in
+// Morton order (the half c-bin in the high bits), so that a run of homes in
+// bucket order stays inside one half c-bin.
+template <int DIM>
+__device__ __forceinline__ int home_bucket(const GeoT<float>& G, const float4& P) {
+    const int qx = quarter_cbin(G, P.x, 0), qy = quarter_cbin(G, P.y, 1);
+    if (DIM == 3) {
+        const int qz = quarter_cbin(G, P.z, 2);
+        return ((((qz >> 1) * 2 + (qx >> 1)) * 2 + (qy >> 1)) << 3) | (((qz & 1) * 2 + (qx & 1)) * 2 + (qy & 1));
+    }
+    return (((qx >> 1) * 2 + (qy >> 1)) << 2) | ((qx & 1) * 2 + (qy & 1));
+}
+
+// Bucket of a candidate inside its window row (three c-bins along the fast
+// dimension): its half c-bin along the row (mod 6) and its half in the others.
+template <int DIM>
+__device__ __forceinline__ int row_bucket(const GeoT<float>& G, const float4& P) {
+    if (DIM == 3) return ((half_cbin(G, P.z, 2) % 6) * 2 + (half_cbin(G, P.x, 0) & 1)) * 2 + (half_cbin(G, P.y, 1) & 1);
+    return (half_cbin(G, P.y, 1) % 6) * 2 + (half_cbin(G, P.x, 0) & 1);
+}
+
+// Swept box of one particle over the step, widened by 2^-12 |v dt|_1.
+template <int DIM>
+__device__ __forceinline__ void swept_box(const float x[3], const float v[3], float dt, float lo[3], float hi[3]) {
+    float s[3], e = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        s[d] = v[d] * dt;
+        e += fabsf(s[d]);
+    }
+    e *= 0x1p-12f;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        lo[d] = x[d] + fminf(0.f, s[d]) - e;
+        hi[d] = x[d] + fmaxf(0.f, s[d]) + e;
+    }
+}
+
+// Dynamic shared memory of the pruned search for a capacity of `cap` staged
+// candidates (cap rounded down to a multiple of 16): six floats and one int per
+// staged candidate, three float2 per cluster (the staging ranks share them).
+__host__ __device__ constexpr size_t pruned_smem_bytes(int cap) {
+    return (size_t)(28 + 24 / kCluster) * (size_t)(cap & ~15);
+}
+
+template <int DIM>
+__device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const GeoT<float>& G, const InstDev& I,
+                                                   int inst, uint32_t kc, int64_t h0, int64_t h1, unsigned char* smem,
+                                                   int* rq0, int* rlen, int* rpre, float (*rsh)[3], int& nr_s,
+                                                   int& tot_s) {
+    const int CAP = b.tile_cap & ~15;   // staged slots per chunk (a multiple of kCluster)
+    const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
+    // staged pair k (slots 2k, 2k + 1): pA (-x, -x', -y, -y'), pB (-z, -z', -vx, -vx'),
+    // pC (-vy, -vy', -vz, -vz'), pQ (q, q') sorted positions (-1: pad)
+    float4* pA = reinterpret_cast<float4*>(smem);
+    float4* pB = pA + CAP / 2;
+    float4* pC = pB + CAP / 2;
+    int2* pQ = reinterpret_cast<int2*>(pC + CAP / 2);
+    // cluster c's box in the home frame: (lo, hi) per dimension
+    float2* cbx = reinterpret_cast<float2*>(pQ + CAP / 2);
+    float2* cby = cbx + CAP / kCluster;
+    float2* cbz = cby + CAP / kCluster;
+    unsigned short* srank = reinterpret_cast<unsigned short*>(cbx);   // staging only, before the boxes
+    __shared__ int bcnt[kTileRanges * kRowBuckets];
+    __shared__ int ppre[kTileRanges + 1];
+    __shared__ int pb0[kTileRanges], pb1[kTileRanges];
+    __shared__ int hcnt[kHomeBuckets];
+    __shared__ unsigned short hperm[kTileThreads];
+    __shared__ unsigned long long blk_tests;
+
+    tile_window_ranges<float, DIM>(b, G, I, inst, kc, h0, rq0, rlen, rpre, rsh, nr_s, tot_s);
+    const int nr = nr_s;
+    // every range padded to whole clusters: range r occupies [ppre[r], ppre[r + 1])
+    if (tid == 0) {
+        blk_tests = 0ull;
+        int acc = 0;
+        for (int r = 0; r < nr; ++r) {
+            ppre[r] = acc;
+            acc += (rlen[r] + kCluster - 1) / kCluster * kCluster;
+        }
+        ppre[nr] = acc;
+    }
+    __syncthreads();
+    const int ptot = ppre[nr];
+    // window split between gridDim.y blocks of the c-bin, as in the plain tile search
+    const int split = (int)gridDim.y, part = (int)blockIdx.y;
+    int per = CAP;
+    if (split > 1) per = min(CAP, ((ptot + split - 1) / split + kCluster - 1) / kCluster * kCluster);
+    if (part * per >= ptot) return;   // nothing left for this block (block-uniform)
+    const bool once = part * per + split * per >= ptot;
+    const float dt = step_dt(b.dyn[inst], 0.f), R2 = inst_R2(I, 0.f);
+    float wmax = 0.f, cmax = 0.f, lmax = 0.f;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        wmax = fmaxf(wmax, G.L[d] / (float)G.n[d]);
+        cmax = fmaxf(cmax, fmaxf(fabsf(G.lo[d]), fabsf(G.hi[d])));
+        lmax = fmaxf(lmax, G.L[d]);
+    }
+    const float margin = sqrtf(R2) * (1.f + 0x1p-10f) + 0x1p-7f * wmax + 0x1p-16f * (cmax + lmax);
+    const float qnan = __int_as_float(0x7fc00000);
+
+    // Stage chunk [c0, c0 + per) of the padded ranges, each range's part sorted
+    // by bucket, then the clusters' boxes.
+    auto stage = [&](int c0) {
+        const int cn = min(per, ptot - c0);
+        if (tid < nr) {
+            const int a = max(ppre[tid], c0);
+            const int e = max(a, min(ppre[tid + 1], c0 + cn));
+            pb0[tid] = a - c0;
+            pb1[tid] = e - c0;
+        }
+        for (int i = tid; i < nr * kRowBuckets; i += nthr) bcnt[i] = 0;
+        __syncthreads();
+        for (int e = tid; e < cn; e += nthr) {   // rank inside the bucket
+            const int ge = c0 + e;
+            int r = 0;
+            while (r + 1 < nr && ppre[r + 1] <= ge) ++r;
+            const int o = ge - ppre[r];
+            if (o < rlen[r]) {
+                const float4 P = ldg_vec(b.posA + rq0[r] + o);
+                srank[e] = (unsigned short)atomicAdd(&bcnt[r * kRowBuckets + row_bucket<DIM>(G, P)], 1);
+            }
+        }
+        __syncthreads();
+        if (tid < nr) {   // bucket starts: the range's part from its first slot, buckets in order
+            int acc = pb0[tid];
+            for (int k = 0; k < kRowBuckets; ++k) {
+                const int c = bcnt[tid * kRowBuckets + k];
+                bcnt[tid * kRowBuckets + k] = acc;
+                acc += c;
+            }
+        }
+        __syncthreads();
+        // every candidate to its sorted slot; the pads keep theirs (the end of
+        // the range's part) and fail every test (NaN)
+        for (int e = tid; e < cn; e += nthr) {
+            const int ge = c0 + e;
+            int r = 0;
+            while (r + 1 < nr && ppre[r + 1] <= ge) ++r;
+            const int o = ge - ppre[r];
+            int slot = e;
+            int32_t q = -1;
+            float4 P = make_float4(qnan, qnan, qnan, qnan), Q = P;
+            if (o < rlen[r]) {
+                q = rq0[r] + o;
+                P = ldg_vec(b.posA + q);
+                Q = ldg_vec(b.velA + q);
+                slot = bcnt[r * kRowBuckets + row_bucket<DIM>(G, P)] + srank[e];
+            }
+            const int k = slot >> 1, s = slot & 1;
+            float* a = reinterpret_cast<float*>(pA + k);
+            float* bz = reinterpret_cast<float*>(pB + k);
+            float* c = reinterpret_cast<float*>(pC + k);
+            a[s] = -P.x;
+            a[2 + s] = -P.y;
+            bz[s] = -P.z;
+            bz[2 + s] = -Q.x;
+            c[s] = -Q.y;
+            c[2 + s] = -Q.z;
+            reinterpret_cast<int32_t*>(pQ + k)[s] = q;
+        }
+        __syncthreads();
+        for (int c = tid; c < cn / kCluster; c += nthr) {   // cluster boxes
+            const int s0 = c * kCluster;
+            int r = 0;
+            while (r + 1 < nr && pb1[r] <= s0) ++r;
+            float lo[3] = {R<float>::inf(), R<float>::inf(), R<float>::inf()};
+            float hi[3] = {-R<float>::inf(), -R<float>::inf(), -R<float>::inf()};
+            for (int j = s0; j < s0 + kCluster; ++j) {
+                const int k = j >> 1, s = j & 1;
+                const float* a = reinterpret_cast<const float*>(pA + k);
+                const float* bz = reinterpret_cast<const float*>(pB + k);
+                const float* cc = reinterpret_cast<const float*>(pC + k);
+                const float x[3] = {-a[s], -a[2 + s], -bz[s]};
+                const float v[3] = {-bz[2 + s], -cc[s], -cc[2 + s]};
+                float l[3], h[3];
+                swept_box<DIM>(x, v, dt, l, h);
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {   // a pad's NaN drops out of fminf / fmaxf
+                    lo[d] = fminf(lo[d], l[d]);
+                    hi[d] = fmaxf(hi[d], h[d]);
+                }
+            }
+            // the test takes x_i - (x_j - shift): the cluster's box in the home frame
+            cbx[c] = make_float2(lo[0] - rsh[r][0], hi[0] - rsh[r][0]);
+            cby[c] = make_float2(lo[1] - rsh[r][1], hi[1] - rsh[r][1]);
+            if (DIM == 3) cbz[c] = make_float2(lo[2] - rsh[r][2], hi[2] - rsh[r][2]);
+        }
+    };
+
+    if (once) {
+        stage(part * per);
+        __syncthreads();
+    }
+    unsigned long long wtests = 0;   // this warp's (home, staged slot) tests
+    for (int64_t hc = h0; hc < h1; hc += nthr) {
+        // this chunk of homes, sorted by bucket: a warp takes 32 neighbours
+        const int nh = (int)min((int64_t)nthr, h1 - hc);
+        for (int i = tid; i < kHomeBuckets; i += nthr) hcnt[i] = 0;
+        __syncthreads();
+        int hb = 0, hr = 0;
+        if (tid < nh) {
+            hb = home_bucket<DIM>(G, b.posA[hc + tid]);
+            hr = atomicAdd(&hcnt[hb], 1);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int acc = 0;
+            for (int k = 0; k < kHomeBuckets; ++k) {
+                const int c = hcnt[k];
+                hcnt[k] = acc;
+                acc += c;
+            }
+        }
+        __syncthreads();
+        if (tid < nh) hperm[hcnt[hb] + hr] = (unsigned short)tid;
+        __syncthreads();
+        const bool home = tid < nh;
+        const int32_t p = home ? (int32_t)hc + (int32_t)hperm[tid] : -1;
+        float4 P = make_float4(qnan, qnan, qnan, qnan), Q = P;   // a lane without a home fails every test
+        if (home) {
+            P = b.posA[p];
+            Q = b.velA[p];
+        }
+        const uint32_t tag = __float_as_uint(P.w);
+        if (home && part == 0) b.slot_of[I.p_off + (int64_t)tag_id(b, tag)] = (uint32_t)p;
+        const float xi[3] = {P.x, P.y, P.z};
+        const float vi[3] = {Q.x, Q.y, Q.z};
+        float wlo[3] = {R<float>::inf(), R<float>::inf(), R<float>::inf()};
+        float whi[3] = {-R<float>::inf(), -R<float>::inf(), -R<float>::inf()};
+        if (home) swept_box<DIM>(xi, vi, dt, wlo, whi);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            for (int o = 16; o > 0; o >>= 1) {
+                wlo[d] = fminf(wlo[d], __shfl_xor_sync(kFull, wlo[d], o));
+                whi[d] = fmaxf(whi[d], __shfl_xor_sync(kFull, whi[d], o));
+            }
+            wlo[d] -= margin;
+            whi[d] += margin;
+        }
+        const unsigned whomes = (unsigned)__popc(__ballot_sync(kFull, home));
+        const bool warp_live = whomes != 0;
+        float bd = R<float>::inf();
+        uint32_t bid = 0xffffffffu;
+        // d^2 of a candidate that passed criteria 1-2; a home tests only
+        // candidates at higher sorted positions (each pair once)
+        auto close = [&](float rr, float a, float bb, int32_t q) {
+            if (q <= p) return;
+            const float d2 = R<float>::sub(rr, R<float>::div(R<float>::mul(a, a), bb));
+            const uint32_t idj = __float_as_uint(__ldg(&b.posA[q].w));
+            if (d2 < bd || (d2 == bd && idj < bid)) {
+                bd = d2;
+                bid = idj;
+            }
+            atomicMin(&b.bkey[q], partner_key<float>(d2, tag));
+        };
+        // the clusters [cb0, cb1) of one range part: 32 box tests per ballot,
+        // then the overlapping clusters, two staged pairs per step
+        auto scan_clusters = [&](auto has_shift, int cb0, int cb1, const float sh[3]) {
+            constexpr bool SH = decltype(has_shift)::value;
+            const PairHome ph = pair_home(xi, vi, sh, dt, R2);
+            for (int cb = cb0; cb < cb1; cb += 32) {
+                const int c = cb + lane;
+                bool ov = false;
+                if (c < cb1) {
+                    const float2 bx = cbx[c], by = cby[c];
+                    ov = bx.x <= whi[0] && wlo[0] <= bx.y && by.x <= whi[1] && wlo[1] <= by.y;
+                    if (DIM == 3) {
+                        const float2 bz = cbz[c];
+                        ov = ov && bz.x <= whi[2] && wlo[2] <= bz.y;
+                    }
+                }
+                unsigned m = __ballot_sync(kFull, ov);
+                wtests += (unsigned long long)(__popc(m) * kCluster) * whomes;
+                while (m) {
+                    const int j = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int k0 = (cb + j) * (kCluster / 2);
+#pragma unroll
+                    for (int k = k0; k < k0 + kCluster / 2; k += 2) {
+                        float2 rr0, a0, b0, rr1, a1, b1;
+                        const unsigned ok0 = paired_test<DIM, SH>(ph, pA[k], pB[k], pC[k], rr0, a0, b0);
+                        const unsigned ok1 = paired_test<DIM, SH>(ph, pA[k + 1], pB[k + 1], pC[k + 1], rr1, a1, b1);
+                        if (ok0 | ok1) {
+                            const int2 q0 = pQ[k], q1 = pQ[k + 1];
+                            if (ok0 & 1u) close(rr0.x, a0.x, b0.x, q0.x);
+                            if (ok0 & 2u) close(rr0.y, a0.y, b0.y, q0.y);
+                            if (ok1 & 1u) close(rr1.x, a1.x, b1.x, q1.x);
+                            if (ok1 & 2u) close(rr1.y, a1.y, b1.y, q1.y);
+                        }
+                    }
+                }
+            }
+        };
+        for (int c0 = part * per; c0 < ptot; c0 += split * per) {
+            if (!once) {
+                __syncthreads();
+                stage(c0);
+                __syncthreads();
+            }
+            if (!warp_live) continue;
+            for (int r = 0; r < nr; ++r) {
+                const int s0 = pb0[r], s1 = pb1[r];
+                if (s0 >= s1) continue;
+                const float sh[3] = {rsh[r][0], rsh[r][1], rsh[r][2]};
+                if (sh[0] != 0.f || sh[1] != 0.f || sh[2] != 0.f)
+                    scan_clusters(std::true_type{}, s0 / kCluster, s1 / kCluster, sh);
+                else
+                    scan_clusters(std::false_type{}, s0 / kCluster, s1 / kCluster, sh);
+            }
+        }
+        if (home && bid != 0xffffffffu) atomicMin(&b.bkey[p], partner_key<float>(bd, bid));
+    }
+    if (b.tile_tests) {   // one counter update per block, the blocks spread over kTestSlots counters
+        if (lane == 0 && wtests) atomicAdd(&blk_tests, wtests);
+        __syncthreads();
+        if (tid == 0 && blk_tests) atomicAdd(&b.tile_tests[(blockIdx.x + blockIdx.y) % kTestSlots], blk_tests);
+    }
+}
+
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kTileThreads) tile_search_kernel(Bufs<T> b) {
     using V = typename Vec4<T>::type;
@@ -1288,10 +1692,17 @@ __global__ void __launch_bounds__(kTileThreads) tile_search_kernel(Bufs<T> b) {
 #pragma unroll
         for (int d = 0; d < DIM; ++d) amb = amb || window_1d(g[d], g[d], 1, I.M[d], kk[d], G.wall[d]).amb;
     }
-    if (amb)
+    if (amb) {
         tile_search_cell<T, DIM, true>(b, G, I, inst_s, kc, h0_s, h1_s, sp, sv, rq0, rlen, rpre, rsh, nr_s, tot_s);
-    else
-        tile_search_cell<T, DIM, false>(b, G, I, inst_s, kc, h0_s, h1_s, sp, sv, rq0, rlen, rpre, rsh, nr_s, tot_s);
+        return;
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (I.prune) {
+            tile_search_pruned<DIM>(b, G, I, inst_s, kc, h0_s, h1_s, tile_smem, rq0, rlen, rpre, rsh, nr_s, tot_s);
+            return;
+        }
+    }
+    tile_search_cell<T, DIM, false>(b, G, I, inst_s, kc, h0_s, h1_s, sp, sv, rq0, rlen, rpre, rsh, nr_s, tot_s);
 }
 
 // Direct search of one particle (global loads), used by the staged kernel for
@@ -2286,7 +2697,9 @@ cudaError_t launch_tile_search(const Bufs<T>& b, cudaStream_t s) {
 
 template <typename T>
 size_t tile_smem_bytes(const Bufs<T>& b) {
-    return (size_t)b.tile_cap * 2 * sizeof(typename Vec4<T>::type);
+    const size_t plain = (size_t)b.tile_cap * 2 * sizeof(typename Vec4<T>::type);
+    if (sizeof(T) == 4 && b.tile_prune) return std::max(plain, pruned_smem_bytes(b.tile_cap));
+    return plain;
 }
 
 // Dynamic shared memory beyond 48 KiB must be allowed per kernel.

@@ -89,7 +89,7 @@ def test_invalid_config_is_rejected_without_device(built_lib):
         k.make_config(dim_pos=3, flags=k.KMC_FLAG_VELOCITY_2D),
         k.make_config(dt=0.0),
         k.make_config(lam=0.0, sigma=0.0),
-        k.make_config(flags=1 << 8),
+        k.make_config(flags=1 << 9),
         k.make_config(tile_threads=100),
         k.make_config(tile_threads=288),
         k.make_config(tile_cap=63),

@@ -369,6 +369,9 @@ TILE_CASES = [
     ("square2d_fp32_dense", 200_000, 2, (40, 40, 1), (0, 0, 0), (1, 1, 1), (WALL, WALL, PER), 5e-4, 0.005, 32),
     ("periodic3d_fp32_3cells", 20_000, 3, (3, 3, 4), (0, 0, 0), (1, 1, 1), (PER, PER, PER), 1e-3, 0.02, 32),
     ("tiny_cells_fp32", 7_777, 3, (30, 30, 4), (0, 0, 0), (1, 1, 0.2), (PER, PER, WALL), 1e-3, 0.003, 32),
+    # the 3-D Sod benchmark's geometry at small N: ~208 per dense c-bin, R = 0.11 and v_th dt = 0.2 c-bin widths
+    ("sod3d_fp32_narrow_contact", 120_000, 3, (16, 8, 8), (0, 0, 0), (1, 0.5, 0.5), (WALL, PER, PER), 0.0139,
+     0.0125, 32),
 ]
 
 
@@ -642,6 +645,73 @@ def test_dsmc_variant_matches_oracle(prec, dim):
         assert np.abs(pd[:, :dim] - p[:, :dim]).max() <= tol_x
         p, v = pd.astype(np.float64), vd.astype(np.float64)   # the next step from the device state
     sim.close()
+
+
+@pytest.mark.parametrize("case", [c for c in TILE_CASES if c[9] == 32], ids=[c[0] for c in TILE_CASES if c[9] == 32])
+def test_tile_pruning_changes_speed_only(case):
+    """The binary32 tile search skips candidate clusters whose swept boxes stay
+    out of the contact distance of a warp's homes: three steps with and without
+    the pruning give bit-identical closest candidates, pairs and states, and in
+    dense c-bins much wider than the contact distance the pruned search counts
+    fewer pair tests than the plain one's (C_p - 1) / 2 per particle."""
+    _setup()
+    import paper_1210_8084_gb300 as k
+    name, n, dim, n_cells, lo, hi, bc, lam, dt, prec = case
+    pos, vel = make_inputs(name, n, dim, lo, hi)
+    pos, vel = f32_state(pos, vel, lo, hi, bc)
+    out = []
+    for flags in (k.KMC_FLAG_RECORD, k.KMC_FLAG_RECORD | k.KMC_FLAG_NO_TILE_PRUNE):
+        cfg = k.make_config(dim_pos=dim, n_cells=n_cells, lo=lo, hi=hi, bc=bc, lam=lam, dt=dt, seed=9,
+                            precision=32, flags=flags, sub_cells=(1, 1, 1))
+        sim = k.Simulation(cfg, pos, vel)
+        info = sim.info()
+        if flags & k.KMC_FLAG_NO_TILE_PRUNE:
+            assert info.tile_prune == 0
+        else:   # pruned where the contact distance is at most half a c-bin
+            width = min((hi[d] - lo[d]) / n_cells[d] for d in range(dim))
+            assert info.tile_prune == int(np.sqrt(info.R2) <= 0.5 * width)
+            pruned = info.tile_prune
+        cand = sim.window_size()
+        sim.step(3)
+        best, partner = sim.partners()
+        p1, v1 = sim.state()
+        out.append((best, partner, p1, v1, sim.tile_tests(), cand))
+        sim.close()
+    (b0, q0, p0, w0, t0, c0), (b1, q1, p1, w1, t1, _) = out
+    assert (b0 >= 0).mean() > 0.05
+    assert np.array_equal(b0, b1) and np.array_equal(q0, q1)
+    assert np.array_equal(p0, p1) and np.array_equal(w0, w1)
+    assert t1 == 0.0
+    assert (t0 > 0) == bool(pruned)
+    if n / np.prod(n_cells[:dim]) >= 50 and np.sqrt(info.R2) < 0.25 * width:
+        # dense c-bins and a contact distance well inside one: fewer tests than
+        # the plain search's (C_p - 1) / 2 per particle-step (window of the first step)
+        assert t0 < 3 * n * (c0 - 1) / 2
+
+
+def test_tile_search_far_from_origin():
+    """Coordinates near 100 (the rounding margin of the pruned tile search grows
+    with the coordinates' magnitude): closest candidates and pairs equal the
+    oracle's binary32 decisions, with and without the pruning.  (The end-of-step
+    state is not compared with the binary64 oracle here: at |x| ~ 100 a binary32
+    position that ends within an ulp of a wall or face may fold or wrap
+    differently from the binary64 one.)"""
+    _setup()
+    import paper_1210_8084_gb300 as k
+    n, dim, n_cells, lo, hi, bc, lam, dt = 60_000, 3, (20, 6, 6), (100, -50, 7), (101, -49.7, 7.3), \
+        (WALL, PER, PER), 1e-3, 0.01
+    pos, vel = make_inputs("offset", n, dim, lo, hi)
+    pos, vel = f32_state(pos, vel, lo, hi, bc)
+    o = oracle_step(pos, vel, dim, n_cells, lo, hi, bc, oracle_R2(lam, n, dim, lo, hi), dt, 5, 0, True)
+    assert (o["best"] >= 0).mean() > 0.05
+    for flags in (k.KMC_FLAG_RECORD, k.KMC_FLAG_RECORD | k.KMC_FLAG_NO_TILE_PRUNE):
+        cfg = k.make_config(dim_pos=dim, n_cells=n_cells, lo=lo, hi=hi, bc=bc, lam=lam, dt=dt, seed=5,
+                            precision=32, flags=flags, sub_cells=(1, 1, 1))
+        sim = k.Simulation(cfg, pos, vel)
+        sim.step(1)
+        best, partner = sim.partners()
+        sim.close()
+        assert np.array_equal(best, o["best"]) and np.array_equal(partner, o["partner"])
 
 
 @pytest.mark.parametrize("prec,tt,cap,split", [(32, 64, 64, 1), (32, 128, 768, 1), (32, 256, 6144, 1),

@@ -101,7 +101,7 @@ def test_noalloc_checks_the_configuration_as_kmc_init_does():
     _setup()
     import paper_1210_8084_gb300 as k
     bad = [
-        k.make_config(dim_pos=3, n_cells=(10, 1, 1), lam=1e-3, dt=1e-3, flags=1 << 8),
+        k.make_config(dim_pos=3, n_cells=(10, 1, 1), lam=1e-3, dt=1e-3, flags=1 << 9),
         k.make_config(dim_pos=3, n_cells=(10, 1, 1), lam=1e-3, dt=1e-3, flags=k.KMC_FLAG_VELOCITY_2D),
         k.make_config(dim_pos=3, n_cells=(10, 1, 1), sigma=float("inf"), dt=1e-3),
         k.make_config(dim_pos=3, n_cells=(10, 1, 1), lam=1e-3, dt=0.0),
