@@ -297,7 +297,7 @@ def roofline_of(w, r, steps, n_sm, peaks, peak_src, workload):
                 "ms_per_launch": round(phases[dom], 4), "algorithmic_flops_per_launch": int(flops),
                 "candidates_per_particle": round(cand, 3), "pair_tests_per_particle": round(tests, 3)}
         if pruned:
-            roof["pair_tests_source"] = "counted by the pruned tile search (clusters of 8 out of reach skipped)"
+            roof["pair_tests_source"] = "counted by the pruned tile search (clusters of 4 candidates out of reach skipped)"
             roof["plain_pair_tests_per_particle"] = round(plain, 3)
             roof["plain_equivalent_tflops"] = round(FLOPS_PER_TEST * plain * n / t_dom / 1e12, 3)
         if traffic is not None:

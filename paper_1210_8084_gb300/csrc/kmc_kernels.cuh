@@ -892,15 +892,17 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) search_kerne
 }
 
 // ------------------------------------------------------ paired binary32 test
-// A home particle of the paired test: its coordinates, the periodic image
-// shift of the candidates' range and the step's constants, each in both
-// halves of a float2.
+// A home particle of the paired test (its coordinates and the step's
+// constants) and the periodic image shift of the candidates' range, each value
+// in both halves of a float2.
 struct PairHome {
-    float2 x0, x1, x2, v0, v1, v2, s0, s1, s2, dt2, mR2;
+    float2 x0, x1, x2, v0, v1, v2, dt2, mR2;
+};
+struct PairShift {
+    float2 s0, s1, s2;
 };
 
-__device__ __forceinline__ PairHome pair_home(const float xi[3], const float vi[3], const float sh[3], float dt,
-                                              float R2) {
+__device__ __forceinline__ PairHome pair_home(const float xi[3], const float vi[3], float dt, float R2) {
     PairHome h;
     h.x0 = make_float2(xi[0], xi[0]);
     h.x1 = make_float2(xi[1], xi[1]);
@@ -908,35 +910,34 @@ __device__ __forceinline__ PairHome pair_home(const float xi[3], const float vi[
     h.v0 = make_float2(vi[0], vi[0]);
     h.v1 = make_float2(vi[1], vi[1]);
     h.v2 = make_float2(vi[2], vi[2]);
-    h.s0 = make_float2(sh[0], sh[0]);
-    h.s1 = make_float2(sh[1], sh[1]);
-    h.s2 = make_float2(sh[2], sh[2]);
     h.dt2 = make_float2(dt, dt);
     h.mR2 = make_float2(-R2, -R2);   // r2 - R^2 as r2 + (-R^2): the same rounding
     return h;
 }
 
-// Criteria 1-2 of the acceptance test (Eqs. 5-6, 8-9) for one home against the
-// two candidates of a staged pair in the negated layout A = (-x, -x', -y, -y'),
-// B = (-z, -z', -vx, -vx'), C = (-vy, -vy', -vz, -vz').  Each component of
-// __fadd2_rn / __fmul2_rn / __ffma2_rn rounds exactly as the scalar operation,
-// and x - y is x + (-y) in IEEE arithmetic, so the decisions are bit for bit
-// those of poca_test_sh; the real-root test is evaluated for both candidates
-// so that no lane branches off for criterion 2, and b > 0 needs no test of its
-// own (a < 0 and fma(b, dt, a) > 0 give b dt > -a > 0 exactly).  Bit 0 / 1 of
-// the result: the first / second candidate passes; rr, a, bb give d^2 of a
-// passing candidate.
+__device__ __forceinline__ PairShift pair_shift(const float sh[3]) {
+    return PairShift{make_float2(sh[0], sh[0]), make_float2(sh[1], sh[1]), make_float2(sh[2], sh[2])};
+}
+
+// The arithmetic of criteria 1-2 (Eqs. 5-6, 8-9) for one home against the two
+// candidates of a staged pair in the negated layout A = (-x, -x', -y, -y'),
+// B = (-z, -z', -vx, -vx'), C = (-vy, -vy', -vz, -vz'): a = dr.dv, b = |dv|^2,
+// |dr|^2, f = fma(b, dt, a) and disc = a^2 - b (|dr|^2 - R^2).  Each component
+// of __fadd2_rn / __fmul2_rn / __ffma2_rn rounds exactly as the scalar
+// operation, and x - y is x + (-y) in IEEE arithmetic, so every quantity is bit
+// for bit that of poca_test_sh.
 template <int DIM, bool SH>
-__device__ __forceinline__ unsigned paired_test(const PairHome& h, const float4 A, const float4 B, const float4 C,
-                                                float2& rr, float2& a, float2& bb) {
+__device__ __forceinline__ void paired_core(const PairHome& h, const PairShift& sh, const float4 A, const float4 B,
+                                            const float4 C, float2& rr, float2& a, float2& bb, float2& f,
+                                            float2& disc) {
     float2 d0 = __fadd2_rn(h.x0, make_float2(A.x, A.y));
     float2 d1 = __fadd2_rn(h.x1, make_float2(A.z, A.w));
     float2 d2v = make_float2(0.f, 0.f);
     if (DIM == 3) d2v = __fadd2_rn(h.x2, make_float2(B.x, B.y));
     if (SH) {
-        d0 = __fadd2_rn(d0, h.s0);
-        d1 = __fadd2_rn(d1, h.s1);
-        if (DIM == 3) d2v = __fadd2_rn(d2v, h.s2);
+        d0 = __fadd2_rn(d0, sh.s0);
+        d1 = __fadd2_rn(d1, sh.s1);
+        if (DIM == 3) d2v = __fadd2_rn(d2v, sh.s2);
     }
     const float2 u0 = __fadd2_rn(h.v0, make_float2(B.z, B.w));
     const float2 u1 = __fadd2_rn(h.v1, make_float2(C.x, C.y));
@@ -952,10 +953,48 @@ __device__ __forceinline__ unsigned paired_test(const PairHome& h, const float4 
         bb = __ffma2_rn(u2, u2, bb);
         rr = __ffma2_rn(d2v, d2v, rr);
     }
-    const float2 f = __ffma2_rn(bb, h.dt2, a);
+    f = __ffma2_rn(bb, h.dt2, a);
     const float2 y = __fmul2_rn(bb, __fadd2_rn(rr, h.mR2));
-    const float2 disc = __ffma2_rn(a, a, make_float2(-y.x, -y.y));
+    disc = __ffma2_rn(a, a, make_float2(-y.x, -y.y));
+}
+
+// Criteria 1-2 for the two candidates: bit 0 / 1 of the result is set when the
+// first / second passes (the real-root test is evaluated for both, so that no
+// lane branches off for criterion 2; b > 0 needs no test of its own: a < 0 and
+// fma(b, dt, a) > 0 give b dt > -a > 0 exactly).  rr, a, bb give d^2 of a
+// passing candidate.
+template <int DIM, bool SH>
+__device__ __forceinline__ unsigned paired_test(const PairHome& h, const PairShift& sh, const float4 A,
+                                                const float4 B, const float4 C, float2& rr, float2& a, float2& bb) {
+    float2 f, disc;
+    paired_core<DIM, SH>(h, sh, A, B, C, rr, a, bb, f, disc);
     return ((a.x < 0.f && f.x > 0.f && disc.x >= 0.f) ? 1u : 0u) | ((a.y < 0.f && f.y > 0.f && disc.y >= 0.f) ? 2u : 0u);
+}
+
+// The same test with its decisions left in sign bits, for the pruned tile
+// search: bit 31 of w.x / w.y is set when a < 0, f > 0 and disc >= 0 may all
+// hold for the first / second candidate.  It is set for every candidate that
+// passes (a < 0 sets the sign of a; f > 0 and disc >= 0 leave theirs clear:
+// disc = fma(a, a, -y) is never -0, as an exact zero sum rounds to +0 and
+// a * a is never -0) and also for a = -0, f = +0 or a NaN, so the caller
+// re-tests a set bit exactly (pair_passes).  Four candidates' conditions then
+// cost four LOP3s and one compare.
+template <int DIM, bool SH>
+__device__ __forceinline__ uint2 paired_signs(const PairHome& h, const PairShift& sh, const float4 A, const float4 B,
+                                              const float4 C, float2& rr, float2& a, float2& bb) {
+    float2 f, disc;
+    paired_core<DIM, SH>(h, sh, A, B, C, rr, a, bb, f, disc);
+    return make_uint2(__float_as_uint(a.x) & ~__float_as_uint(f.x) & ~__float_as_uint(disc.x),
+                      __float_as_uint(a.y) & ~__float_as_uint(f.y) & ~__float_as_uint(disc.y));
+}
+
+// Criteria 1-2 for one candidate from its a, b, |dr|^2, rounded as in the
+// paired test (each paired component rounds as these scalar operations).
+__device__ __forceinline__ bool pair_passes(const PairHome& h, float rr, float a, float bb) {
+    const float f = __fmaf_rn(bb, h.dt2.x, a);
+    const float y = __fmul_rn(bb, __fadd_rn(rr, h.mR2.x));
+    const float disc = __fmaf_rn(a, a, -y);
+    return a < 0.f && f > 0.f && disc >= 0.f;
 }
 
 // ------------------------------------------------------ tile search
@@ -1204,7 +1243,8 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
                 auto close = [&](float rr, float a, float bb, uint32_t idj, int32_t q) {
                     take(R<float>::sub(rr, R<float>::div(R<float>::mul(a, a), bb)), idj, q);
                 };
-                const PairHome ph = pair_home(xi, vi, sh, dt, R2);
+                const PairHome ph = pair_home(xi, vi, dt, R2);
+                const PairShift ps = pair_shift(sh);
                 int e = e0;
                 if ((e - c0) & 1) one(e++);
                 // Only a candidate that passes all of criteria 1-2 (about one test
@@ -1212,7 +1252,7 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
                 // of staged pair k (candidates 2k, 2k + 1 of the chunk); bit 0 / 1
                 // of the result: candidate passes criteria 1-2
                 auto test2 = [&](int k, int32_t q, float2& rr, float2& a, float2& bb) -> unsigned {
-                    unsigned ok = paired_test<DIM, SH>(ph, pA[k], pB[k], pC[k], rr, a, bb);
+                    unsigned ok = paired_test<DIM, SH>(ph, ps, pA[k], pB[k], pC[k], rr, a, bb);
                     if (CHK) ok &= (q > lim ? 1u : 0u) | (q + 1 > lim ? 2u : 0u);
                     return ok;
                 };
@@ -1314,6 +1354,8 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
 // each particle's |v dt|_1, the widening of every swept box.
 constexpr int kCluster = 4;      // staged candidates per cluster (two staged pairs: one step of the loop)
 constexpr int kHomeBuckets = 64; // home order inside a c-bin: quarter c-bins in Morton order
+constexpr int kBatch = 64;       // clusters of one work item (a home group against them)
+constexpr int kMaxBatches = 64;  // batches of one staged chunk: 6144 / kCluster / kBatch + kTileRanges < 64
 constexpr int kRowBuckets = 24;  // buckets of a window row: 6 half c-bins along the fast dimension x 2 x 2
 
 // Index of the half c-bin of coordinate x along dimension d (any integer that
@@ -1391,12 +1433,16 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
     float2* cbx = reinterpret_cast<float2*>(pQ + CAP / 2);
     float2* cby = cbx + CAP / kCluster;
     float2* cbz = cby + CAP / kCluster;
-    unsigned short* srank = reinterpret_cast<unsigned short*>(cbx);   // staging only, before the boxes
+    uint32_t* srank = reinterpret_cast<uint32_t*>(cbx);   // staging only, before the boxes: bucket << 16 | rank
     __shared__ int bcnt[kTileRanges * kRowBuckets];
     __shared__ int ppre[kTileRanges + 1];
     __shared__ int pb0[kTileRanges], pb1[kTileRanges];
     __shared__ int hcnt[kHomeBuckets];
     __shared__ unsigned short hperm[kTileThreads];
+    __shared__ float gbox[kTileThreads / 32][6];          // home group boxes (lo, hi), widened
+    __shared__ int gnext[kTileThreads / 32];              // next batch of each home group
+    __shared__ int batch[kMaxBatches];                    // batch i: range << 16 | first cluster
+    __shared__ int nbatch_s;
     __shared__ unsigned long long blk_tests;
 
     tile_window_ranges<float, DIM>(b, G, I, inst, kc, h0, rq0, rlen, rpre, rsh, nr_s, tot_s);
@@ -1431,7 +1477,11 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
     const float qnan = __int_as_float(0x7fc00000);
 
     // Stage chunk [c0, c0 + per) of the padded ranges, each range's part sorted
-    // by bucket, then the clusters' boxes.
+    // by bucket, with the clusters' boxes: (1) every candidate's bucket and rank
+    // in it, (2) the bucket starts, (3) every candidate's sorted position q into
+    // its slot (a pad keeps its own slot, at the end of its range's part), (4)
+    // every slot gathers its candidate, and the four lanes of a cluster combine
+    // their swept boxes.
     auto stage = [&](int c0) {
         const int cn = min(per, ptot - c0);
         if (tid < nr) {
@@ -1442,14 +1492,14 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
         }
         for (int i = tid; i < nr * kRowBuckets; i += nthr) bcnt[i] = 0;
         __syncthreads();
-        for (int e = tid; e < cn; e += nthr) {   // rank inside the bucket
-            const int ge = c0 + e;
-            int r = 0;
-            while (r + 1 < nr && ppre[r + 1] <= ge) ++r;
-            const int o = ge - ppre[r];
-            if (o < rlen[r]) {
-                const float4 P = ldg_vec(b.posA + rq0[r] + o);
-                srank[e] = (unsigned short)atomicAdd(&bcnt[r * kRowBuckets + row_bucket<DIM>(G, P)], 1);
+        for (int r = 0; r < nr; ++r) {
+            const int ev = min(ppre[r] + rlen[r], c0 + cn);   // end of the range's real candidates
+            const int32_t qb = rq0[r] - ppre[r];
+#pragma unroll 2
+            for (int ge = max(ppre[r], c0) + tid; ge < ev; ge += nthr) {
+                const float4 P = ldg_vec(b.posA + qb + ge);
+                const int bk = row_bucket<DIM>(G, P);
+                srank[ge - c0] = ((uint32_t)bk << 16) | (uint32_t)atomicAdd(&bcnt[r * kRowBuckets + bk], 1);
             }
         }
         __syncthreads();
@@ -1462,60 +1512,59 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
             }
         }
         __syncthreads();
-        // every candidate to its sorted slot; the pads keep theirs (the end of
-        // the range's part) and fail every test (NaN)
-        for (int e = tid; e < cn; e += nthr) {
-            const int ge = c0 + e;
-            int r = 0;
-            while (r + 1 < nr && ppre[r + 1] <= ge) ++r;
-            const int o = ge - ppre[r];
-            int slot = e;
-            int32_t q = -1;
-            float4 P = make_float4(qnan, qnan, qnan, qnan), Q = P;
-            if (o < rlen[r]) {
-                q = rq0[r] + o;
-                P = ldg_vec(b.posA + q);
-                Q = ldg_vec(b.velA + q);
-                slot = bcnt[r * kRowBuckets + row_bucket<DIM>(G, P)] + srank[e];
+        int32_t* slot_q = reinterpret_cast<int32_t*>(pQ);
+        for (int r = 0; r < nr; ++r) {
+            const int ev = min(ppre[r] + rlen[r], c0 + cn);
+            const int e1 = min(ppre[r + 1], c0 + cn);
+            const int32_t qb = rq0[r] - ppre[r];
+            for (int ge = max(ppre[r], c0) + tid; ge < e1; ge += nthr) {
+                int slot = ge - c0;
+                int32_t q = -1;
+                if (ge < ev) {
+                    const uint32_t sr = srank[ge - c0];
+                    slot = bcnt[r * kRowBuckets + (int)(sr >> 16)] + (int)(sr & 0xffffu);
+                    q = qb + ge;
+                }
+                slot_q[slot] = q;
             }
-            const int k = slot >> 1, s = slot & 1;
-            float* a = reinterpret_cast<float*>(pA + k);
-            float* bz = reinterpret_cast<float*>(pB + k);
-            float* c = reinterpret_cast<float*>(pC + k);
-            a[s] = -P.x;
-            a[2 + s] = -P.y;
-            bz[s] = -P.z;
-            bz[2 + s] = -Q.x;
-            c[s] = -Q.y;
-            c[2 + s] = -Q.z;
-            reinterpret_cast<int32_t*>(pQ + k)[s] = q;
         }
         __syncthreads();
-        for (int c = tid; c < cn / kCluster; c += nthr) {   // cluster boxes
-            const int s0 = c * kCluster;
-            int r = 0;
-            while (r + 1 < nr && pb1[r] <= s0) ++r;
-            float lo[3] = {R<float>::inf(), R<float>::inf(), R<float>::inf()};
-            float hi[3] = {-R<float>::inf(), -R<float>::inf(), -R<float>::inf()};
-            for (int j = s0; j < s0 + kCluster; ++j) {
-                const int k = j >> 1, s = j & 1;
-                const float* a = reinterpret_cast<const float*>(pA + k);
-                const float* bz = reinterpret_cast<const float*>(pB + k);
-                const float* cc = reinterpret_cast<const float*>(pC + k);
-                const float x[3] = {-a[s], -a[2 + s], -bz[s]};
-                const float v[3] = {-bz[2 + s], -cc[s], -cc[2 + s]};
-                float l[3], h[3];
-                swept_box<DIM>(x, v, dt, l, h);
+        for (int s0 = 0; s0 < cn; s0 += nthr) {   // the same trip count on every lane (shuffles)
+            const int sl = s0 + tid;
+            float4 P = make_float4(qnan, qnan, qnan, qnan), Q = P;
+            if (sl < cn) {
+                const int32_t q = slot_q[sl];
+                if (q >= 0) {
+                    P = ldg_vec(b.posA + q);
+                    Q = ldg_vec(b.velA + q);
+                }
+                const int k = sl >> 1, h = sl & 1;
+                float* a = reinterpret_cast<float*>(pA + k);
+                float* bz = reinterpret_cast<float*>(pB + k);
+                float* c = reinterpret_cast<float*>(pC + k);
+                a[h] = -P.x;
+                a[2 + h] = -P.y;
+                bz[h] = -P.z;
+                bz[2 + h] = -Q.x;
+                c[h] = -Q.y;
+                c[2 + h] = -Q.z;
+            }
+            const float x[3] = {P.x, P.y, P.z}, v[3] = {Q.x, Q.y, Q.z};
+            float lo[3], hi[3];
+            swept_box<DIM>(x, v, dt, lo, hi);
 #pragma unroll
-                for (int d = 0; d < DIM; ++d) {   // a pad's NaN drops out of fminf / fmaxf
-                    lo[d] = fminf(lo[d], l[d]);
-                    hi[d] = fmaxf(hi[d], h[d]);
+            for (int d = 0; d < DIM; ++d) {   // a pad's NaN drops out of fminf / fmaxf
+                for (int o = 1; o < kCluster; o <<= 1) {
+                    lo[d] = fminf(lo[d], __shfl_xor_sync(kFull, lo[d], o));
+                    hi[d] = fmaxf(hi[d], __shfl_xor_sync(kFull, hi[d], o));
                 }
             }
-            // the test takes x_i - (x_j - shift): the cluster's box in the home frame
-            cbx[c] = make_float2(lo[0] - rsh[r][0], hi[0] - rsh[r][0]);
-            cby[c] = make_float2(lo[1] - rsh[r][1], hi[1] - rsh[r][1]);
-            if (DIM == 3) cbz[c] = make_float2(lo[2] - rsh[r][2], hi[2] - rsh[r][2]);
+            if ((tid & (kCluster - 1)) == 0 && sl < cn) {   // the cluster's box, without its range's image shift
+                const int c = sl / kCluster;
+                cbx[c] = make_float2(lo[0], hi[0]);
+                cby[c] = make_float2(lo[1], hi[1]);
+                if (DIM == 3) cbz[c] = make_float2(lo[2], hi[2]);
+            }
         }
     };
 
@@ -1523,9 +1572,15 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
         stage(part * per);
         __syncthreads();
     }
+    // Work of a chunk: every home group (32 sorted homes) against every batch of
+    // 32 clusters of the staged rows.  A warp starts on its own group and takes
+    // its batches from the group's counter; once that is exhausted it helps
+    // another group, so that no warp idles at the chunk's barrier while others
+    // work.  Results go straight to the keys (atomicMin on both sides of a
+    // passing pair), so a group's batches may run on any warp.
+    const int warp = tid >> 5, nwarps = nthr >> 5;
     unsigned long long wtests = 0;   // this warp's (home, staged slot) tests
     for (int64_t hc = h0; hc < h1; hc += nthr) {
-        // this chunk of homes, sorted by bucket: a warp takes 32 neighbours
         const int nh = (int)min((int64_t)nthr, h1 - hc);
         for (int i = tid; i < kHomeBuckets; i += nthr) hcnt[i] = 0;
         __syncthreads();
@@ -1546,101 +1601,150 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
         __syncthreads();
         if (tid < nh) hperm[hcnt[hb] + hr] = (unsigned short)tid;
         __syncthreads();
-        const bool home = tid < nh;
-        const int32_t p = home ? (int32_t)hc + (int32_t)hperm[tid] : -1;
-        float4 P = make_float4(qnan, qnan, qnan, qnan), Q = P;   // a lane without a home fails every test
-        if (home) {
-            P = b.posA[p];
-            Q = b.velA[p];
-        }
-        const uint32_t tag = __float_as_uint(P.w);
-        if (home && part == 0) b.slot_of[I.p_off + (int64_t)tag_id(b, tag)] = (uint32_t)p;
-        const float xi[3] = {P.x, P.y, P.z};
-        const float vi[3] = {Q.x, Q.y, Q.z};
-        float wlo[3] = {R<float>::inf(), R<float>::inf(), R<float>::inf()};
-        float whi[3] = {-R<float>::inf(), -R<float>::inf(), -R<float>::inf()};
-        if (home) swept_box<DIM>(xi, vi, dt, wlo, whi);
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-            for (int o = 16; o > 0; o >>= 1) {
-                wlo[d] = fminf(wlo[d], __shfl_xor_sync(kFull, wlo[d], o));
-                whi[d] = fmaxf(whi[d], __shfl_xor_sync(kFull, whi[d], o));
+        const int ngroups = (nh + 31) >> 5;
+        // group boxes: warp g bounds the swept boxes of group g, widened by the margin
+        if (warp < ngroups) {
+            const int hi = warp * 32 + lane;
+            float wlo[3] = {R<float>::inf(), R<float>::inf(), R<float>::inf()};
+            float whi[3] = {-R<float>::inf(), -R<float>::inf(), -R<float>::inf()};
+            if (hi < nh) {
+                const int32_t p = (int32_t)hc + (int32_t)hperm[hi];
+                const float4 P = b.posA[p], Q = b.velA[p];
+                // sorted position by id, read by the move kernel (part 0 visits every home once)
+                if (part == 0) b.slot_of[I.p_off + (int64_t)tag_id(b, __float_as_uint(P.w))] = (uint32_t)p;
+                const float x[3] = {P.x, P.y, P.z}, v[3] = {Q.x, Q.y, Q.z};
+                swept_box<DIM>(x, v, dt, wlo, whi);
             }
-            wlo[d] -= margin;
-            whi[d] += margin;
-        }
-        const unsigned whomes = (unsigned)__popc(__ballot_sync(kFull, home));
-        const bool warp_live = whomes != 0;
-        float bd = R<float>::inf();
-        uint32_t bid = 0xffffffffu;
-        // d^2 of a candidate that passed criteria 1-2; a home tests only
-        // candidates at higher sorted positions (each pair once)
-        auto close = [&](float rr, float a, float bb, int32_t q) {
-            if (q <= p) return;
-            const float d2 = R<float>::sub(rr, R<float>::div(R<float>::mul(a, a), bb));
-            const uint32_t idj = __float_as_uint(__ldg(&b.posA[q].w));
-            if (d2 < bd || (d2 == bd && idj < bid)) {
-                bd = d2;
-                bid = idj;
-            }
-            atomicMin(&b.bkey[q], partner_key<float>(d2, tag));
-        };
-        // the clusters [cb0, cb1) of one range part: 32 box tests per ballot,
-        // then the overlapping clusters, two staged pairs per step
-        auto scan_clusters = [&](auto has_shift, int cb0, int cb1, const float sh[3]) {
-            constexpr bool SH = decltype(has_shift)::value;
-            const PairHome ph = pair_home(xi, vi, sh, dt, R2);
-            for (int cb = cb0; cb < cb1; cb += 32) {
-                const int c = cb + lane;
-                bool ov = false;
-                if (c < cb1) {
-                    const float2 bx = cbx[c], by = cby[c];
-                    ov = bx.x <= whi[0] && wlo[0] <= bx.y && by.x <= whi[1] && wlo[1] <= by.y;
-                    if (DIM == 3) {
-                        const float2 bz = cbz[c];
-                        ov = ov && bz.x <= whi[2] && wlo[2] <= bz.y;
-                    }
-                }
-                unsigned m = __ballot_sync(kFull, ov);
-                wtests += (unsigned long long)(__popc(m) * kCluster) * whomes;
-                while (m) {
-                    const int j = __ffs(m) - 1;
-                    m &= m - 1;
-                    const int k0 = (cb + j) * (kCluster / 2);
 #pragma unroll
-                    for (int k = k0; k < k0 + kCluster / 2; k += 2) {
-                        float2 rr0, a0, b0, rr1, a1, b1;
-                        const unsigned ok0 = paired_test<DIM, SH>(ph, pA[k], pB[k], pC[k], rr0, a0, b0);
-                        const unsigned ok1 = paired_test<DIM, SH>(ph, pA[k + 1], pB[k + 1], pC[k + 1], rr1, a1, b1);
-                        if (ok0 | ok1) {
-                            const int2 q0 = pQ[k], q1 = pQ[k + 1];
-                            if (ok0 & 1u) close(rr0.x, a0.x, b0.x, q0.x);
-                            if (ok0 & 2u) close(rr0.y, a0.y, b0.y, q0.y);
-                            if (ok1 & 1u) close(rr1.x, a1.x, b1.x, q1.x);
-                            if (ok1 & 2u) close(rr1.y, a1.y, b1.y, q1.y);
-                        }
-                    }
+            for (int d = 0; d < DIM; ++d) {
+                for (int o = 16; o > 0; o >>= 1) {
+                    wlo[d] = fminf(wlo[d], __shfl_xor_sync(kFull, wlo[d], o));
+                    whi[d] = fmaxf(whi[d], __shfl_xor_sync(kFull, whi[d], o));
                 }
             }
-        };
+            if (lane == 0) {
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    gbox[warp][d] = d < DIM ? wlo[d] - margin : 0.f;
+                    gbox[warp][3 + d] = d < DIM ? whi[d] + margin : 0.f;
+                }
+            }
+        }
         for (int c0 = part * per; c0 < ptot; c0 += split * per) {
             if (!once) {
                 __syncthreads();
                 stage(c0);
-                __syncthreads();
             }
-            if (!warp_live) continue;
-            for (int r = 0; r < nr; ++r) {
-                const int s0 = pb0[r], s1 = pb1[r];
-                if (s0 >= s1) continue;
+            // batches of kBatch clusters of each range's part; fresh group counters
+            if (tid == 0) {
+                int nb = 0;
+                for (int r = 0; r < nr; ++r)
+                    for (int c = pb0[r] / kCluster; c < pb1[r] / kCluster; c += kBatch) batch[nb++] = (r << 16) | c;
+                nbatch_s = nb;
+            }
+            if (tid < ngroups) gnext[tid] = 0;
+            __syncthreads();
+            const int nbatch = nbatch_s;
+            int g = warp % ngroups, loaded = -1;
+            PairHome ph;
+            float wlo[3], whi[3];
+            int32_t p = -1;
+            uint32_t tag = 0;
+            unsigned ghomes = 0;
+            // d^2 of a candidate that passed criteria 1-2; a home tests only
+            // candidates at higher sorted positions (each pair once)
+            auto close = [&](float rr, float a, float bb, int32_t q) {
+                if (q <= p) return;
+                const float d2 = R<float>::sub(rr, R<float>::div(R<float>::mul(a, a), bb));
+                atomicMin(&b.bkey[p], partner_key<float>(d2, __float_as_uint(__ldg(&b.posA[q].w))));
+                atomicMin(&b.bkey[q], partner_key<float>(d2, tag));
+            };
+            // clusters [cb0, cb1) of one range part: 32 box tests per ballot, then
+            // the overlapping clusters, two staged pairs each
+            auto scan_batch = [&](auto has_shift, int cb0, int cb1, const float sh[3]) {
+                constexpr bool SH = decltype(has_shift)::value;
+                const PairShift ps = pair_shift(sh);
+                for (int cb = cb0; cb < cb1; cb += 32) {
+                    // the warp's box moved by the image shift meets the cluster's box
+                    // (x_i - (x_j - shift) = (x_i + shift) - x_j)
+                    const int c = cb + lane;
+                    bool ov = false;
+                    if (c < cb1) {
+                        const float2 bx = cbx[c], by = cby[c];
+                        ov = bx.x <= whi[0] + sh[0] && wlo[0] + sh[0] <= bx.y && by.x <= whi[1] + sh[1] &&
+                             wlo[1] + sh[1] <= by.y;
+                        if (DIM == 3) {
+                            const float2 bz = cbz[c];
+                            ov = ov && bz.x <= whi[2] + sh[2] && wlo[2] + sh[2] <= bz.y;
+                        }
+                    }
+                    unsigned m = __ballot_sync(kFull, ov);
+                    wtests += (unsigned long long)(__popc(m) * kCluster) * ghomes;
+                    while (m) {
+                        const int j = __ffs(m) - 1;
+                        m &= m - 1;
+                        const int k = (cb + j) * (kCluster / 2);
+                        float2 rr0, a0, b0, rr1, a1, b1;
+                        const uint2 w0 = paired_signs<DIM, SH>(ph, ps, pA[k], pB[k], pC[k], rr0, a0, b0);
+                        const uint2 w1 = paired_signs<DIM, SH>(ph, ps, pA[k + 1], pB[k + 1], pC[k + 1], rr1, a1, b1);
+                        if ((int)(w0.x | w0.y | w1.x | w1.y) < 0) {   // some candidate may pass: exact tests
+                            const int2 q0 = pQ[k], q1 = pQ[k + 1];
+                            if ((int)w0.x < 0 && pair_passes(ph, rr0.x, a0.x, b0.x)) close(rr0.x, a0.x, b0.x, q0.x);
+                            if ((int)w0.y < 0 && pair_passes(ph, rr0.y, a0.y, b0.y)) close(rr0.y, a0.y, b0.y, q0.y);
+                            if ((int)w1.x < 0 && pair_passes(ph, rr1.x, a1.x, b1.x)) close(rr1.x, a1.x, b1.x, q1.x);
+                            if ((int)w1.y < 0 && pair_passes(ph, rr1.y, a1.y, b1.y)) close(rr1.y, a1.y, b1.y, q1.y);
+                        }
+                    }
+                }
+            };
+            while (true) {
+                int bi = 0;
+                if (lane == 0) {
+                    bi = atomicAdd(&gnext[g], 1);
+                    if (bi >= nbatch) {   // this group is done: the next one with batches left
+                        volatile int* gv = gnext;
+                        int ng = -1;
+                        for (int j = 1; j < ngroups && ng < 0; ++j) {
+                            const int gg = (g + j) % ngroups;
+                            if (gv[gg] < nbatch) ng = gg;
+                        }
+                        bi = ng < 0 ? -1 : -2 - ng;
+                    }
+                }
+                bi = __shfl_sync(kFull, bi, 0);
+                if (bi == -1) break;
+                if (bi < 0) {
+                    g = -2 - bi;
+                    continue;
+                }
+                if (g != loaded) {   // this group's homes (a lane without one fails every test)
+                    loaded = g;
+                    const int hi = g * 32 + lane;
+                    float4 P = make_float4(qnan, qnan, qnan, qnan), Q = P;
+                    p = -1;
+                    if (hi < nh) {
+                        p = (int32_t)hc + (int32_t)hperm[hi];
+                        P = b.posA[p];
+                        Q = b.velA[p];
+                    }
+                    const float xi[3] = {P.x, P.y, P.z}, vi[3] = {Q.x, Q.y, Q.z};
+                    ph = pair_home(xi, vi, dt, R2);
+                    tag = __float_as_uint(P.w);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        wlo[d] = gbox[g][d];
+                        whi[d] = gbox[g][3 + d];
+                    }
+                    ghomes = (unsigned)min(32, nh - g * 32);
+                }
+                const int r = batch[bi] >> 16, cb0 = batch[bi] & 0xffff;
+                const int cb1 = min(cb0 + kBatch, pb1[r] / kCluster);
                 const float sh[3] = {rsh[r][0], rsh[r][1], rsh[r][2]};
-                if (sh[0] != 0.f || sh[1] != 0.f || sh[2] != 0.f)
-                    scan_clusters(std::true_type{}, s0 / kCluster, s1 / kCluster, sh);
-                else
-                    scan_clusters(std::false_type{}, s0 / kCluster, s1 / kCluster, sh);
+                if (sh[0] != 0.f || sh[1] != 0.f || sh[2] != 0.f) scan_batch(std::true_type{}, cb0, cb1, sh);
+                else scan_batch(std::false_type{}, cb0, cb1, sh);
             }
         }
-        if (home && bid != 0xffffffffu) atomicMin(&b.bkey[p], partner_key<float>(bd, bid));
+        __syncthreads();   // the next home chunk rewrites hperm, the group boxes and counters
     }
     if (b.tile_tests) {   // one counter update per block, the blocks spread over kTestSlots counters
         if (lane == 0 && wtests) atomicAdd(&blk_tests, wtests);
@@ -1650,7 +1754,7 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
 }
 
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kTileThreads) tile_search_kernel(Bufs<T> b) {
+__global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 1) tile_search_kernel(Bufs<T> b) {
     using V = typename Vec4<T>::type;
     extern __shared__ __align__(32) unsigned char tile_smem[];   // 2 x tile_cap vectors
     V* sp = reinterpret_cast<V*>(tile_smem);
