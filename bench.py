@@ -151,6 +151,8 @@ def fp32_peak_tflops(n_sm, sm_mhz):
 KERNEL_SEGMENTS = {
     "tile_search": ("// ------------------------------------------------------ tile search",
                     "// Direct search of one particle (global loads)"),
+    "tile_pruned": ("// ------------------------------------------------------ pruned tile search (binary32)",
+                    "// The plain tile search: one block per c-bin"),
     "search": ("// The PoCA acceptance test of the ordered pair (i, j)",
                "// ------------------------------------------------------ tile search"),
     "move": ("// Unambiguous pairs, CM-frame scattering", "// Counting-sort scatter B -> A in canonical order"),
@@ -272,7 +274,7 @@ def roofline_of(w, r, steps, n_sm, peaks, peak_src, workload):
     dom = max(("search", "tile", "move", "scan", "scatter", "moments"), key=lambda p: phases[p])
     t_dom = phases[dom] * 1e-3
     frac_paired = 2 * r["pairs"] / n
-    kernel = {"search": "search", "tile": "tile_search"}.get(dom, dom)
+    kernel = {"search": "search", "tile": "tile_pruned" if r.get("tile_tests") is not None else "tile_search"}.get(dom, dom)
     traffic = profiled_traffic(kernel, workload, n)
     if dom in ("search", "tile"):
         # arithmetic-bound: 25 binary32 operations per pair test.  The window of a

@@ -82,11 +82,13 @@ extern "C" {
                             * must be 0 or 1).  Collided particles count as paired in the moments (zero virial);
                             * kmc_get_partners reports -1 */
 #define KMC_FLAG_RADIAL_MOMENT 128 /* also accumulate the radial velocity per c-bin (KMC_MOM_RADIAL, Eq. vel_r) */
-#define KMC_FLAG_NO_TILE_PRUNE 256 /* binary32 tile search: test every (home, candidate) pair of a c-bin block.  By
-                                    * default, where the contact distance R is at most half the narrowest c-bin
-                                    * width, the homes of a warp skip every cluster of 8 candidates whose swept box
-                                    * (positions over the step) stays farther than R, plus a rounding margin, from
-                                    * theirs; same results */
+#define KMC_FLAG_NO_TILE_PRUNE 256 /* binary32: no pruned tile search.  By default an instance whose automatic
+                                    * search cells would be its c-bins (the reach exceeds half a c-bin), whose contact
+                                    * distance R is at most half the narrowest c-bin and whose periodic dimensions
+                                    * have 6 c-bins or more searches on half c-bins (sub_cells 2 per position
+                                    * dimension) with one block per c-bin, where each group of 32 homes skips every
+                                    * cluster of 4 candidates whose swept box (positions over the step) stays farther
+                                    * than R, plus a rounding margin, from the group's; same results */
 #define KMC_FLAG_ADAPTIVE_DT 16  /* timestep dt(t) = dx_min / v_max(t) of each step's start state (Sect. "Simulation
                                   * setup"; dx_min the smallest c-bin width, v_max the largest speed of the instance,
                                   * |v|^2 = fma(vz, vz, fma(vy, vy, vx vx)) in the state precision, the quotient in
@@ -146,9 +148,10 @@ typedef struct kmc_config {
 KMC_API int kmc_window_size(kmc_handle* h, double* mean_candidates);
 
 /* Pair tests the binary32 tile search has evaluated since kmc_init with its
- * pruning (KMC_FLAG_NO_TILE_PRUNE unset): for every cluster of 8 staged
- * candidates that a warp tests, 8 x the homes of the warp (padding slots of a
- * window row's last cluster included).  0 for handles without that search.
+ * pruning (KMC_FLAG_NO_TILE_PRUNE unset): for every cluster of 4 staged
+ * candidates that a group of homes tests, 4 x the homes of the group (padding
+ * slots of a window row's last cluster included).  0 for handles without that
+ * search.
  * The plain tile search tests (C_p - 1) / 2 pairs per particle, C_p from
  * kmc_window_size.  Synchronises the handle's stream. */
 KMC_API int kmc_tile_tests(kmc_handle* h, double* tests);

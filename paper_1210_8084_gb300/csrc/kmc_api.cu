@@ -55,6 +55,7 @@ struct kmc_handle {
     uint32_t id_bits = 32;
     uint32_t n_stage_tiles = 0;
     int stage_cap = 0, stage_rows = 0, stage_stride = 0, stage_pair_cap = 0, any_direct = 1, any_tiled = 0;
+    int any_plain_tiled = 0;
     int tile_threads = 256, tile_cap = 1536, tile_split = 1, tile_prune = 1;
     int64_t n_bins = 0, bins_per_inst = 0;
     int64_t bytes = 0;
@@ -138,6 +139,7 @@ Bufs<T> make_bufs(const kmc_handle* h) {
     b.stage_pair_cap = h->stage_pair_cap;
     b.any_direct = h->any_direct;
     b.any_tiled = h->any_tiled;
+    b.any_plain_tiled = h->any_plain_tiled;
     b.dsmc = (h->cfg.flags & KMC_FLAG_DSMC) ? 1 : 0;
     b.radial = (h->cfg.flags & KMC_FLAG_RADIAL_MOMENT) ? 1 : 0;
     b.tile_threads = h->tile_threads;
@@ -295,9 +297,38 @@ void choose_subdivision(const kmc_handle* h, InstDev& I, double vmax, uint32_t m
             s[dmax] = std::max(1, (int)(s[dmax] * 0.9));
         }
     }
+    bool forced = false;
     for (int d = 0; d < 3; ++d) {
-        if (d < h->dim && h->cfg.sub_cells[d] > 0) s[d] = h->cfg.sub_cells[d];
+        if (d < h->dim && h->cfg.sub_cells[d] > 0) {
+            s[d] = h->cfg.sub_cells[d];
+            forced = true;
+        }
         if (d >= h->dim || (h->cfg.flags & KMC_FLAG_DSMC)) s[d] = 1;   // DSMC: collision cells are the c-bins
+    }
+    // Pruned tile search (binary32): where the search cells would be the c-bins
+    // (the reach exceeds half a c-bin) but the contact distance is at most half
+    // the narrowest c-bin, search on half c-bins with one block per c-bin that
+    // skips the candidate clusters out of reach.  Periodic dimensions need 6
+    // c-bins or more (a window of 6 half c-bins that never meets its own image)
+    // and the key count stays within the cap above.
+    I.prune = 0;
+    if (!forced && h->tile_prune && s[0] == 1 && s[1] == 1 && s[2] == 1 &&
+        !(h->cfg.flags & (KMC_FLAG_DSMC | KMC_FLAG_NO_TILE_SEARCH | KMC_FLAG_STAGED_SEARCH))) {
+        double wmin = h->geo.L[0] / h->geo.n[0];
+        bool ok = true;
+        double keys = (double)h->bins_per_inst;
+        for (int d = 0; d < h->dim; ++d) {
+            wmin = std::min(wmin, h->geo.L[d] / h->geo.n[d]);
+            if (h->geo.bc[d] == KMC_BC_PERIODIC && h->geo.n[d] < 6) ok = false;
+            keys *= 2.0;
+        }
+        ok = ok && sqrt(I.R2) <= 0.5 * wmin && keys <= 8.0 * (double)I.n + 4.0 * (double)h->bins_per_inst;
+        if (ok) {
+            for (int d = 0; d < h->dim; ++d) s[d] = 2;
+            I.prune = 1;
+        }
+    }
+    for (int d = 0; d < 3; ++d) {
         I.s[d] = s[d];
         I.M[d] = h->geo.n[d] * s[d];
         I.w[d] = h->geo.L[d] / (double)I.M[d];
@@ -690,6 +721,7 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
         plan_staged_search(h, max_occ);
         // search cells that are the c-bins themselves: one block per cell
         h->any_tiled = 0;
+        h->any_plain_tiled = 0;
         h->any_direct = 0;
         int prune_any = 0;
         const bool dsmc = (h->cfg.flags & KMC_FLAG_DSMC) != 0;
@@ -698,15 +730,12 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
                 I.staged = I.tiled = 0;
                 continue;
             }
-            I.tiled = !I.staged && I.n > 0 && I.s[0] == 1 && I.s[1] == 1 && I.s[2] == 1 &&
+            I.tiled = !I.staged && I.n > 0 && ((I.s[0] == 1 && I.s[1] == 1 && I.s[2] == 1) || I.prune) &&
                       !(h->cfg.flags & KMC_FLAG_NO_TILE_SEARCH);
+            I.prune = I.prune && I.tiled;
             h->any_tiled |= I.tiled;
+            h->any_plain_tiled |= I.tiled && !I.prune;
             h->any_direct |= !I.tiled && !I.staged;   // searched one thread per particle
-            // pruning pays only where the contact distance is well inside a c-bin
-            // (a wider one puts every cluster of the window within reach)
-            double wmin = h->geo.L[0] / h->geo.n[0];
-            for (int d = 1; d < h->dim; ++d) wmin = std::min(wmin, h->geo.L[d] / h->geo.n[d]);
-            I.prune = I.tiled && h->tile_prune && sqrt(I.R2) <= 0.5 * wmin;
             prune_any |= I.prune;
         }
         h->tile_prune = prune_any;
@@ -1006,7 +1035,8 @@ int kmc_get_info(kmc_handle* h, kmc_info* info) {
     // per-particle search (also records slot_of outside tiled instances), tile
     // search, staged search, move, scan, two scatter passes,
     // then moments and two finalize kernels when moments are wanted
-    info->kernels_per_step = ((h->any_direct || h->n_stage_tiles > 0) ? 1 : 0) + (h->any_tiled ? 1 : 0) +
+    info->kernels_per_step = ((h->any_direct || h->n_stage_tiles > 0) ? 1 : 0) + (h->any_plain_tiled ? 1 : 0) +
+                             (h->tile_prune ? 1 : 0) +
                              (h->n_stage_tiles > 0 ? 1 : 0) + ((h->cfg.flags & KMC_FLAG_DSMC) ? 1 : 0) + 4;
     info->kernels_moments = 3;
     info->tile_threads = h->tile_threads;

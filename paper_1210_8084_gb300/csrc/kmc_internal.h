@@ -142,12 +142,13 @@ struct Bufs {
     int stage_pair_cap;      // entries of the binary32 pair list
     int any_direct;          // some instance uses the direct (per-thread) search
     int any_tiled;           // some instance uses the tile search (one block per c-bin)
+    int any_plain_tiled;     // some tiled instance searches on its c-bins (not pruned)
     int dsmc;                // the random-partner comparison variant instead of the PoCA search
     int radial;              // accumulate Sum v.r_hat (KMC_FLAG_RADIAL_MOMENT)
     int tile_threads;        // tile search: threads per c-bin block (a multiple of 32, 64 ... 256)
     int tile_cap;            // tile search: candidates staged in shared memory at once (even)
     int tile_split;          // tile search: blocks sharing one c-bin's window (binary32)
-    int tile_prune;          // tile search, binary32: skip candidate clusters out of a warp's reach
+    int tile_prune;          // some instance uses the pruned tile search (binary32, half c-bins)
     unsigned long long* tile_tests;  // [kTestSlots] pair tests made by the pruned tile search (cumulative; may be null)
     // particle tag = (instance << id_bits) | instance-local id
     uint32_t id_bits;        // 32 when there is one instance

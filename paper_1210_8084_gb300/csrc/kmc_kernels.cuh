@@ -1333,14 +1333,16 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
 // too far apart to meet within the step: a pair can pass criteria 1-2 only if,
 // at some time t in [0, dt], the two particles are within R of each other in
 // every coordinate.  So every particle is bounded by its swept box (the box of
-// the segment x .. x + v dt), the homes of a warp and each cluster of
-// kCluster staged candidates by the union of theirs, and a warp tests a
-// cluster only when its box, widened by R and a rounding margin, overlaps the
-// cluster's.  For small boxes the homes of a block (by quarter c-bin, in Morton
-// order) and the candidates of each window row (by half c-bin) are
-// counting-sorted in shared memory before they are grouped.  The order of the
-// tests changes nothing: each home keeps the minimum of its keys and every
-// partner key is an atomicMin.
+// the segment x .. x + v dt), a group of 32 homes and each cluster of kCluster
+// staged candidates by the union of theirs, and a warp tests a cluster only
+// when the group's box, widened by R and a rounding margin, overlaps the
+// cluster's.  For small boxes these instances search on half c-bins (2 search
+// cells per c-bin and dimension): the canonical (search cell, id) order then
+// groups every c-bin's particles by half c-bin, so consecutive homes and
+// consecutive candidates are close in space without any sort in the block.
+// The window is still the 3^D c-bin neighbourhood (criterion 3), as rows of
+// half c-bins.  The order of the tests changes nothing: every home's key and
+// every candidate's key take the minimum of theirs by atomicMin.
 //
 // Rounding margin.  For a pair that the binary32 test accepts, exact arithmetic
 // on its rounded differences gives d^2 <= R^2 + 15 u |dr|^2 (u = 2^-24; the
@@ -1350,47 +1352,13 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
 // [0, dt] the two particles are within R + sqrt(15 u) |dr| + 3 u |dr| +
 // 7 u |dv| dt + 6 u C of each other in every coordinate.  With |dr| <=
 // 2 sqrt(3) w (w the widest c-bin: both lie in one 3^D neighbourhood) that is
-// below R (1 + 2^-10) + 2^-7 w + 2^-16 C, the warp's widening, plus 2^-12 of
+// below R (1 + 2^-10) + 2^-7 w + 2^-16 C, the group's widening, plus 2^-12 of
 // each particle's |v dt|_1, the widening of every swept box.
+constexpr int kSub = 2;          // search cells per c-bin and position dimension of a pruned instance
+constexpr int kSubRanges = 72;   // window rows (6 x 6 in 3-D) x 2 parts of the fast dimension
 constexpr int kCluster = 4;      // staged candidates per cluster (two staged pairs: one step of the loop)
-constexpr int kHomeBuckets = 64; // home order inside a c-bin: quarter c-bins in Morton order
 constexpr int kBatch = 64;       // clusters of one work item (a home group against them)
-constexpr int kMaxBatches = 64;  // batches of one staged chunk: 6144 / kCluster / kBatch + kTileRanges < 64
-constexpr int kRowBuckets = 24;  // buckets of a window row: 6 half c-bins along the fast dimension x 2 x 2
-
-// Index of the half c-bin of coordinate x along dimension d (any integer that
-// groups nearby particles serves: it orders, never decides).
-__device__ __forceinline__ int half_cbin(const GeoT<float>& G, float x, int d) {
-    const float t = (x - G.lo[d]) * G.inv[d] * 2.0f;
-    return t > 0.f ? (int)fminf(t, 1.0e9f) : 0;
-}
-
-// Quarter c-bin of coordinate x along dimension d, 0 ... 3 (ordering only).
-__device__ __forceinline__ int quarter_cbin(const GeoT<float>& G, float x, int d) {
-    const float t = (x - G.lo[d]) * G.inv[d] * 4.0f;
-    return (t > 0.f ? (int)fminf(t, 1.0e9f) : 0) & 3;
-}
-
-// Bucket of a home inside its c-bin: its quarter c-bin in every dimension, in
-// Morton order (the half c-bin in the high bits), so that a run of homes in
-// bucket order stays inside one half c-bin.
-template <int DIM>
-__device__ __forceinline__ int home_bucket(const GeoT<float>& G, const float4& P) {
-    const int qx = quarter_cbin(G, P.x, 0), qy = quarter_cbin(G, P.y, 1);
-    if (DIM == 3) {
-        const int qz = quarter_cbin(G, P.z, 2);
-        return ((((qz >> 1) * 2 + (qx >> 1)) * 2 + (qy >> 1)) << 3) | (((qz & 1) * 2 + (qx & 1)) * 2 + (qy & 1));
-    }
-    return (((qx >> 1) * 2 + (qy >> 1)) << 2) | ((qx & 1) * 2 + (qy & 1));
-}
-
-// Bucket of a candidate inside its window row (three c-bins along the fast
-// dimension): its half c-bin along the row (mod 6) and its half in the others.
-template <int DIM>
-__device__ __forceinline__ int row_bucket(const GeoT<float>& G, const float4& P) {
-    if (DIM == 3) return ((half_cbin(G, P.z, 2) % 6) * 2 + (half_cbin(G, P.x, 0) & 1)) * 2 + (half_cbin(G, P.y, 1) & 1);
-    return (half_cbin(G, P.y, 1) % 6) * 2 + (half_cbin(G, P.x, 0) & 1);
-}
+constexpr int kMaxBatches = 128; // batches of one staged chunk: 6144 / kCluster / kBatch + kSubRanges < 128
 
 // Swept box of one particle over the step, widened by 2^-12 |v dt|_1.
 template <int DIM>
@@ -1411,41 +1379,121 @@ __device__ __forceinline__ void swept_box(const float x[3], const float v[3], fl
 
 // Dynamic shared memory of the pruned search for a capacity of `cap` staged
 // candidates (cap rounded down to a multiple of 16): six floats and one int per
-// staged candidate, three float2 per cluster (the staging ranks share them).
+// staged candidate, three float2 and one int per cluster.
 __host__ __device__ constexpr size_t pruned_smem_bytes(int cap) {
-    return (size_t)(28 + 24 / kCluster) * (size_t)(cap & ~15);
+    return (size_t)(28 + 28 / kCluster) * (size_t)(cap & ~15);
 }
 
+// Search key of search cell (gx, gy, gz) of instance I.
+template <int DIM>
+__device__ __forceinline__ uint32_t cell_key(const InstDev& I, int gx, int gy, int gz) {
+    if (DIM == 3) return I.key_base + ((uint32_t)gx * (uint32_t)I.M[1] + (uint32_t)gy) * (uint32_t)I.M[2] + (uint32_t)gz;
+    return I.key_base + (uint32_t)gx * (uint32_t)I.M[1] + (uint32_t)gy;
+}
+
+// One block per c-bin c of a pruned instance.
 template <int DIM>
 __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const GeoT<float>& G, const InstDev& I,
-                                                   int inst, uint32_t kc, int64_t h0, int64_t h1, unsigned char* smem,
-                                                   int* rq0, int* rlen, int* rpre, float (*rsh)[3], int& nr_s,
-                                                   int& tot_s) {
+                                                   int inst, const int c[3], unsigned char* smem) {
+    constexpr int F = DIM - 1;   // fastest key dimension
     const int CAP = b.tile_cap & ~15;   // staged slots per chunk (a multiple of kCluster)
-    const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x;
+    const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x, warp = tid >> 5;
     // staged pair k (slots 2k, 2k + 1): pA (-x, -x', -y, -y'), pB (-z, -z', -vx, -vx'),
     // pC (-vy, -vy', -vz, -vz'), pQ (q, q') sorted positions (-1: pad)
     float4* pA = reinterpret_cast<float4*>(smem);
     float4* pB = pA + CAP / 2;
     float4* pC = pB + CAP / 2;
     int2* pQ = reinterpret_cast<int2*>(pC + CAP / 2);
-    // cluster c's box in the home frame: (lo, hi) per dimension
+    // cluster c: its box (lo, hi) per dimension without its range's image shift,
+    // and the largest sorted position in it
     float2* cbx = reinterpret_cast<float2*>(pQ + CAP / 2);
     float2* cby = cbx + CAP / kCluster;
     float2* cbz = cby + CAP / kCluster;
-    uint32_t* srank = reinterpret_cast<uint32_t*>(cbx);   // staging only, before the boxes: bucket << 16 | rank
-    __shared__ int bcnt[kTileRanges * kRowBuckets];
-    __shared__ int ppre[kTileRanges + 1];
-    __shared__ int pb0[kTileRanges], pb1[kTileRanges];
-    __shared__ int hcnt[kHomeBuckets];
-    __shared__ unsigned short hperm[kTileThreads];
+    int* cqmax = reinterpret_cast<int*>(cbz + CAP / kCluster);
+    __shared__ int rq0[kSubRanges], rlen[kSubRanges], ppre[kSubRanges + 1], pb0[kSubRanges], pb1[kSubRanges];
+    __shared__ float rsh[kSubRanges][3];
+    __shared__ int hq0[4], hpre[5];                       // the c-bin's own rows (homes)
     __shared__ float gbox[kTileThreads / 32][6];          // home group boxes (lo, hi), widened
+    __shared__ int gminp[kTileThreads / 32];              // lowest sorted position of each home group
     __shared__ int gnext[kTileThreads / 32];              // next batch of each home group
     __shared__ int batch[kMaxBatches];                    // batch i: range << 16 | first cluster
-    __shared__ int nbatch_s;
+    __shared__ int nr_s, nbatch_s;
     __shared__ unsigned long long blk_tests;
 
-    tile_window_ranges<float, DIM>(b, G, I, inst, kc, h0, rq0, rlen, rpre, rsh, nr_s, tot_s);
+    // the homes: rows (2 c_x + i, 2 c_y + j) of the c-bin, each with its two
+    // search cells along the fast dimension (consecutive keys)
+    constexpr int kHomeRows = DIM == 3 ? 4 : 2;
+    if (tid < kHomeRows) {
+        const int gx = kSub * c[0] + (DIM == 3 ? tid >> 1 : tid);
+        const int gy = DIM == 3 ? kSub * c[1] + (tid & 1) : kSub * c[1];
+        const uint32_t k0 = DIM == 3 ? cell_key<3>(I, gx, gy, kSub * c[2]) : cell_key<2>(I, gx, gy, 0);
+        const uint32_t nmax = (uint32_t)b.n;
+        const int32_t q0 = (int32_t)min(b.start[k0], nmax), q1 = (int32_t)min(b.start[k0 + kSub], nmax);
+        hq0[tid] = q0;
+        hpre[tid + 1] = max(q1 - q0, 0);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        hpre[0] = 0;
+        for (int i = 1; i <= kHomeRows; ++i) hpre[i] += hpre[i - 1];
+    }
+    __syncthreads();
+    const int nh_all = hpre[kHomeRows];
+    if (nh_all == 0) return;   // block-uniform
+    const int32_t h0 = hq0[0];   // the c-bin's lowest sorted position (its first row comes first)
+
+    // the window: rows of the c-bin neighbourhood in search cells, each cut to
+    // positions from h0 on (binary32 symmetric search: the lower sorted position
+    // of a pair tests it)
+    {
+        int wlo[3], whi[3], nw[3] = {1, 1, 1};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            wlo[d] = kSub * c[d] - kSub;
+            whi[d] = kSub * c[d] + 2 * kSub - 1;
+            if (G.wall[d]) {
+                wlo[d] = max(wlo[d], 0);
+                whi[d] = min(whi[d], I.M[d] - 1);
+            }
+            nw[d] = whi[d] - wlo[d] + 1;
+        }
+        // fast-dimension parts (a periodic window may wrap)
+        const int MF = I.M[F];
+        int fa[2], fb[2];
+        float fs[2] = {0.f, 0.f};
+        int nf = 1;
+        if (wlo[F] < 0) {
+            fa[0] = wlo[F] + MF; fb[0] = MF - 1; fs[0] = G.L[F];
+            fa[1] = 0; fb[1] = whi[F];
+            nf = 2;
+        } else if (whi[F] >= MF) {
+            fa[0] = wlo[F]; fb[0] = MF - 1;
+            fa[1] = 0; fb[1] = whi[F] - MF; fs[1] = -G.L[F];
+            nf = 2;
+        } else {
+            fa[0] = wlo[F]; fb[0] = whi[F];
+        }
+        const int ny = DIM == 3 ? nw[1] : 1;
+        const int nrange = nw[0] * ny * nf;
+        for (int t = tid; t < nrange; t += nthr) {
+            const int part = t % nf, row = t / nf;
+            const int ix = DIM == 3 ? row / ny : row, iy = DIM == 3 ? row % ny : 0;
+            float sx, sy = 0.f;
+            const int gx = unwrap<float>(wlo[0] + ix, I.M[0], G.L[0], sx);
+            const int gy = DIM == 3 ? unwrap<float>(wlo[1] + iy, I.M[1], G.L[1], sy) : 0;
+            const uint32_t rk = DIM == 3 ? cell_key<3>(I, gx, gy, 0) : cell_key<2>(I, gx, 0, 0);
+            const uint32_t nmax = (uint32_t)b.n;
+            const int32_t q0 = max((int32_t)min(b.start[rk + (uint32_t)fa[part]], nmax), h0);
+            const int32_t q1 = (int32_t)min(b.start[rk + (uint32_t)fb[part] + 1u], nmax);
+            rq0[t] = q0;
+            rlen[t] = max(q1 - q0, 0);
+            rsh[t][0] = sx;
+            rsh[t][1] = DIM == 3 ? sy : fs[part];
+            rsh[t][2] = DIM == 3 ? fs[part] : 0.f;
+        }
+        if (tid == 0) nr_s = nrange;
+    }
+    __syncthreads();
     const int nr = nr_s;
     // every range padded to whole clusters: range r occupies [ppre[r], ppre[r + 1])
     if (tid == 0) {
@@ -1476,151 +1524,111 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
     const float margin = sqrtf(R2) * (1.f + 0x1p-10f) + 0x1p-7f * wmax + 0x1p-16f * (cmax + lmax);
     const float qnan = __int_as_float(0x7fc00000);
 
-    // Stage chunk [c0, c0 + per) of the padded ranges, each range's part sorted
-    // by bucket, with the clusters' boxes: (1) every candidate's bucket and rank
-    // in it, (2) the bucket starts, (3) every candidate's sorted position q into
-    // its slot (a pad keeps its own slot, at the end of its range's part), (4)
-    // every slot gathers its candidate, and the four lanes of a cluster combine
-    // their swept boxes.
+    // Stage chunk [c0, c0 + per) of the padded ranges: every slot gathers its
+    // candidate (a pad: NaN, position -1), and the kCluster lanes of a cluster
+    // combine their swept boxes and positions.
     auto stage = [&](int c0) {
         const int cn = min(per, ptot - c0);
-        if (tid < nr) {
-            const int a = max(ppre[tid], c0);
-            const int e = max(a, min(ppre[tid + 1], c0 + cn));
-            pb0[tid] = a - c0;
-            pb1[tid] = e - c0;
+        for (int r = tid; r < nr; r += nthr) {   // up to kSubRanges ranges, blocks from 64 threads
+            const int a = max(ppre[r], c0);
+            const int e = max(a, min(ppre[r + 1], c0 + cn));
+            pb0[r] = a - c0;
+            pb1[r] = e - c0;
         }
-        for (int i = tid; i < nr * kRowBuckets; i += nthr) bcnt[i] = 0;
-        __syncthreads();
-        for (int r = 0; r < nr; ++r) {
-            const int ev = min(ppre[r] + rlen[r], c0 + cn);   // end of the range's real candidates
-            const int32_t qb = rq0[r] - ppre[r];
-#pragma unroll 2
-            for (int ge = max(ppre[r], c0) + tid; ge < ev; ge += nthr) {
-                const float4 P = ldg_vec(b.posA + qb + ge);
-                const int bk = row_bucket<DIM>(G, P);
-                srank[ge - c0] = ((uint32_t)bk << 16) | (uint32_t)atomicAdd(&bcnt[r * kRowBuckets + bk], 1);
-            }
-        }
-        __syncthreads();
-        if (tid < nr) {   // bucket starts: the range's part from its first slot, buckets in order
-            int acc = pb0[tid];
-            for (int k = 0; k < kRowBuckets; ++k) {
-                const int c = bcnt[tid * kRowBuckets + k];
-                bcnt[tid * kRowBuckets + k] = acc;
-                acc += c;
-            }
-        }
-        __syncthreads();
-        int32_t* slot_q = reinterpret_cast<int32_t*>(pQ);
-        for (int r = 0; r < nr; ++r) {
-            const int ev = min(ppre[r] + rlen[r], c0 + cn);
-            const int e1 = min(ppre[r + 1], c0 + cn);
-            const int32_t qb = rq0[r] - ppre[r];
-            for (int ge = max(ppre[r], c0) + tid; ge < e1; ge += nthr) {
-                int slot = ge - c0;
-                int32_t q = -1;
-                if (ge < ev) {
-                    const uint32_t sr = srank[ge - c0];
-                    slot = bcnt[r * kRowBuckets + (int)(sr >> 16)] + (int)(sr & 0xffffu);
-                    q = qb + ge;
-                }
-                slot_q[slot] = q;
-            }
-        }
-        __syncthreads();
         for (int s0 = 0; s0 < cn; s0 += nthr) {   // the same trip count on every lane (shuffles)
             const int sl = s0 + tid;
             float4 P = make_float4(qnan, qnan, qnan, qnan), Q = P;
+            int32_t q = -1;
             if (sl < cn) {
-                const int32_t q = slot_q[sl];
-                if (q >= 0) {
+                const int ge = c0 + sl;
+                int lo = 0, hi = nr - 1;   // the range holding padded offset ge
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (ppre[mid] <= ge) lo = mid;
+                    else hi = mid - 1;
+                }
+                const int o = ge - ppre[lo];
+                if (o < rlen[lo]) {
+                    q = rq0[lo] + o;
                     P = ldg_vec(b.posA + q);
                     Q = ldg_vec(b.velA + q);
                 }
                 const int k = sl >> 1, h = sl & 1;
                 float* a = reinterpret_cast<float*>(pA + k);
                 float* bz = reinterpret_cast<float*>(pB + k);
-                float* c = reinterpret_cast<float*>(pC + k);
+                float* cc = reinterpret_cast<float*>(pC + k);
                 a[h] = -P.x;
                 a[2 + h] = -P.y;
                 bz[h] = -P.z;
                 bz[2 + h] = -Q.x;
-                c[h] = -Q.y;
-                c[2 + h] = -Q.z;
+                cc[h] = -Q.y;
+                cc[2 + h] = -Q.z;
+                reinterpret_cast<int32_t*>(pQ + k)[h] = q;
             }
             const float x[3] = {P.x, P.y, P.z}, v[3] = {Q.x, Q.y, Q.z};
             float lo[3], hi[3];
             swept_box<DIM>(x, v, dt, lo, hi);
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) {   // a pad's NaN drops out of fminf / fmaxf
-                for (int o = 1; o < kCluster; o <<= 1) {
+            for (int o = 1; o < kCluster; o <<= 1) {   // a pad's NaN drops out of fminf / fmaxf
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
                     lo[d] = fminf(lo[d], __shfl_xor_sync(kFull, lo[d], o));
                     hi[d] = fmaxf(hi[d], __shfl_xor_sync(kFull, hi[d], o));
                 }
+                q = max(q, __shfl_xor_sync(kFull, q, o));
             }
-            if ((tid & (kCluster - 1)) == 0 && sl < cn) {   // the cluster's box, without its range's image shift
-                const int c = sl / kCluster;
-                cbx[c] = make_float2(lo[0], hi[0]);
-                cby[c] = make_float2(lo[1], hi[1]);
-                if (DIM == 3) cbz[c] = make_float2(lo[2], hi[2]);
+            if ((tid & (kCluster - 1)) == 0 && sl < cn) {
+                const int cl = sl / kCluster;
+                cbx[cl] = make_float2(lo[0], hi[0]);
+                cby[cl] = make_float2(lo[1], hi[1]);
+                if (DIM == 3) cbz[cl] = make_float2(lo[2], hi[2]);
+                cqmax[cl] = q;
             }
         }
     };
 
+    // Work of a chunk: every home group (32 homes) against every batch of
+    // kBatch clusters of the staged rows.  A warp starts on its own group and
+    // takes its batches from the group's counter; once that is exhausted it
+    // helps another group, so that no warp idles at the chunk's barrier while
+    // others work.  Results go straight to the keys (atomicMin on both sides of
+    // a passing pair), so a group's batches may run on any warp.
     if (once) {
         stage(part * per);
         __syncthreads();
     }
-    // Work of a chunk: every home group (32 sorted homes) against every batch of
-    // 32 clusters of the staged rows.  A warp starts on its own group and takes
-    // its batches from the group's counter; once that is exhausted it helps
-    // another group, so that no warp idles at the chunk's barrier while others
-    // work.  Results go straight to the keys (atomicMin on both sides of a
-    // passing pair), so a group's batches may run on any warp.
-    const int warp = tid >> 5, nwarps = nthr >> 5;
-    unsigned long long wtests = 0;   // this warp's (home, staged slot) tests
-    for (int64_t hc = h0; hc < h1; hc += nthr) {
-        const int nh = (int)min((int64_t)nthr, h1 - hc);
-        for (int i = tid; i < kHomeBuckets; i += nthr) hcnt[i] = 0;
-        __syncthreads();
-        int hb = 0, hr = 0;
-        if (tid < nh) {
-            hb = home_bucket<DIM>(G, b.posA[hc + tid]);
-            hr = atomicAdd(&hcnt[hb], 1);
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int acc = 0;
-            for (int k = 0; k < kHomeBuckets; ++k) {
-                const int c = hcnt[k];
-                hcnt[k] = acc;
-                acc += c;
-            }
-        }
-        __syncthreads();
-        if (tid < nh) hperm[hcnt[hb] + hr] = (unsigned short)tid;
-        __syncthreads();
+    unsigned wtests = 0;   // this warp's (home, staged slot) tests
+    // position of home i (0 ... nh_all - 1) of the c-bin's rows
+    auto home_pos = [&](int i) -> int32_t {
+        int k = 0;
+        while (k + 1 < kHomeRows && hpre[k + 1] <= i) ++k;
+        return hq0[k] + (i - hpre[k]);
+    };
+    for (int hc = 0; hc < nh_all; hc += nthr) {
+        const int nh = min(nthr, nh_all - hc);
         const int ngroups = (nh + 31) >> 5;
         // group boxes: warp g bounds the swept boxes of group g, widened by the margin
         if (warp < ngroups) {
             const int hi = warp * 32 + lane;
             float wlo[3] = {R<float>::inf(), R<float>::inf(), R<float>::inf()};
             float whi[3] = {-R<float>::inf(), -R<float>::inf(), -R<float>::inf()};
+            int32_t pmin = 0x7fffffff;
             if (hi < nh) {
-                const int32_t p = (int32_t)hc + (int32_t)hperm[hi];
+                const int32_t p = home_pos(hc + hi);
                 const float4 P = b.posA[p], Q = b.velA[p];
                 // sorted position by id, read by the move kernel (part 0 visits every home once)
                 if (part == 0) b.slot_of[I.p_off + (int64_t)tag_id(b, __float_as_uint(P.w))] = (uint32_t)p;
                 const float x[3] = {P.x, P.y, P.z}, v[3] = {Q.x, Q.y, Q.z};
                 swept_box<DIM>(x, v, dt, wlo, whi);
+                pmin = p;
             }
+            for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) {
-                for (int o = 16; o > 0; o >>= 1) {
+                for (int d = 0; d < DIM; ++d) {
                     wlo[d] = fminf(wlo[d], __shfl_xor_sync(kFull, wlo[d], o));
                     whi[d] = fmaxf(whi[d], __shfl_xor_sync(kFull, whi[d], o));
                 }
+                pmin = min(pmin, __shfl_xor_sync(kFull, pmin, o));
             }
             if (lane == 0) {
 #pragma unroll
@@ -1628,6 +1636,7 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
                     gbox[warp][d] = d < DIM ? wlo[d] - margin : 0.f;
                     gbox[warp][3 + d] = d < DIM ? whi[d] + margin : 0.f;
                 }
+                gminp[warp] = pmin;
             }
         }
         for (int c0 = part * per; c0 < ptot; c0 += split * per) {
@@ -1639,7 +1648,7 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
             if (tid == 0) {
                 int nb = 0;
                 for (int r = 0; r < nr; ++r)
-                    for (int c = pb0[r] / kCluster; c < pb1[r] / kCluster; c += kBatch) batch[nb++] = (r << 16) | c;
+                    for (int cl = pb0[r] / kCluster; cl < pb1[r] / kCluster; cl += kBatch) batch[nb++] = (r << 16) | cl;
                 nbatch_s = nb;
             }
             if (tid < ngroups) gnext[tid] = 0;
@@ -1648,7 +1657,7 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
             int g = warp % ngroups, loaded = -1;
             PairHome ph;
             float wlo[3], whi[3];
-            int32_t p = -1;
+            int32_t p = -1, pmin = 0;
             uint32_t tag = 0;
             unsigned ghomes = 0;
             // d^2 of a candidate that passed criteria 1-2; a home tests only
@@ -1659,42 +1668,43 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
                 atomicMin(&b.bkey[p], partner_key<float>(d2, __float_as_uint(__ldg(&b.posA[q].w))));
                 atomicMin(&b.bkey[q], partner_key<float>(d2, tag));
             };
-            // clusters [cb0, cb1) of one range part: 32 box tests per ballot, then
-            // the overlapping clusters, two staged pairs each
-            auto scan_batch = [&](auto has_shift, int cb0, int cb1, const float sh[3]) {
+            // the candidates of cluster cl (two staged pairs) against this lane's home
+            auto test_cluster = [&](auto has_shift, int cl, const PairShift& ps) {
                 constexpr bool SH = decltype(has_shift)::value;
+                const int k = cl * (kCluster / 2);
+                float2 rr0, a0, b0, rr1, a1, b1;
+                const uint2 w0 = paired_signs<DIM, SH>(ph, ps, pA[k], pB[k], pC[k], rr0, a0, b0);
+                const uint2 w1 = paired_signs<DIM, SH>(ph, ps, pA[k + 1], pB[k + 1], pC[k + 1], rr1, a1, b1);
+                if ((int)(w0.x | w0.y | w1.x | w1.y) < 0) {   // some candidate may pass: exact tests
+                    const int2 q0 = pQ[k], q1 = pQ[k + 1];
+                    if ((int)w0.x < 0 && pair_passes(ph, rr0.x, a0.x, b0.x)) close(rr0.x, a0.x, b0.x, q0.x);
+                    if ((int)w0.y < 0 && pair_passes(ph, rr0.y, a0.y, b0.y)) close(rr0.y, a0.y, b0.y, q0.y);
+                    if ((int)w1.x < 0 && pair_passes(ph, rr1.x, a1.x, b1.x)) close(rr1.x, a1.x, b1.x, q1.x);
+                    if ((int)w1.y < 0 && pair_passes(ph, rr1.y, a1.y, b1.y)) close(rr1.y, a1.y, b1.y, q1.y);
+                }
+            };
+            // clusters [cb0, cb1) of one range part: 32 box tests per ballot, then
+            // the overlapping clusters.  A cluster whose positions all lie at or
+            // below the group's lowest home holds no pair the group tests.
+            auto scan_batch = [&](auto has_shift, int cb0, int cb1, const float sh[3]) {
                 const PairShift ps = pair_shift(sh);
                 for (int cb = cb0; cb < cb1; cb += 32) {
-                    // the warp's box moved by the image shift meets the cluster's box
+                    // the group's box moved by the image shift meets the cluster's box
                     // (x_i - (x_j - shift) = (x_i + shift) - x_j)
-                    const int c = cb + lane;
+                    const int cl = cb + lane;
                     bool ov = false;
-                    if (c < cb1) {
-                        const float2 bx = cbx[c], by = cby[c];
-                        ov = bx.x <= whi[0] + sh[0] && wlo[0] + sh[0] <= bx.y && by.x <= whi[1] + sh[1] &&
-                             wlo[1] + sh[1] <= by.y;
+                    if (cl < cb1) {
+                        const float2 bx = cbx[cl], by = cby[cl];
+                        ov = cqmax[cl] > pmin && bx.x <= whi[0] + sh[0] && wlo[0] + sh[0] <= bx.y &&
+                             by.x <= whi[1] + sh[1] && wlo[1] + sh[1] <= by.y;
                         if (DIM == 3) {
-                            const float2 bz = cbz[c];
+                            const float2 bz = cbz[cl];
                             ov = ov && bz.x <= whi[2] + sh[2] && wlo[2] + sh[2] <= bz.y;
                         }
                     }
-                    unsigned m = __ballot_sync(kFull, ov);
-                    wtests += (unsigned long long)(__popc(m) * kCluster) * ghomes;
-                    while (m) {
-                        const int j = __ffs(m) - 1;
-                        m &= m - 1;
-                        const int k = (cb + j) * (kCluster / 2);
-                        float2 rr0, a0, b0, rr1, a1, b1;
-                        const uint2 w0 = paired_signs<DIM, SH>(ph, ps, pA[k], pB[k], pC[k], rr0, a0, b0);
-                        const uint2 w1 = paired_signs<DIM, SH>(ph, ps, pA[k + 1], pB[k + 1], pC[k + 1], rr1, a1, b1);
-                        if ((int)(w0.x | w0.y | w1.x | w1.y) < 0) {   // some candidate may pass: exact tests
-                            const int2 q0 = pQ[k], q1 = pQ[k + 1];
-                            if ((int)w0.x < 0 && pair_passes(ph, rr0.x, a0.x, b0.x)) close(rr0.x, a0.x, b0.x, q0.x);
-                            if ((int)w0.y < 0 && pair_passes(ph, rr0.y, a0.y, b0.y)) close(rr0.y, a0.y, b0.y, q0.y);
-                            if ((int)w1.x < 0 && pair_passes(ph, rr1.x, a1.x, b1.x)) close(rr1.x, a1.x, b1.x, q1.x);
-                            if ((int)w1.y < 0 && pair_passes(ph, rr1.y, a1.y, b1.y)) close(rr1.y, a1.y, b1.y, q1.y);
-                        }
-                    }
+                    const unsigned m = __ballot_sync(kFull, ov);
+                    wtests += (unsigned)(__popc(m) * kCluster) * ghomes;
+                    for (unsigned mm = m; mm; mm &= mm - 1) test_cluster(has_shift, cb + __ffs(mm) - 1, ps);
                 }
             };
             while (true) {
@@ -1723,7 +1733,7 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
                     float4 P = make_float4(qnan, qnan, qnan, qnan), Q = P;
                     p = -1;
                     if (hi < nh) {
-                        p = (int32_t)hc + (int32_t)hperm[hi];
+                        p = home_pos(hc + hi);
                         P = b.posA[p];
                         Q = b.velA[p];
                     }
@@ -1735,6 +1745,7 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
                         wlo[d] = gbox[g][d];
                         whi[d] = gbox[g][3 + d];
                     }
+                    pmin = gminp[g];
                     ghomes = (unsigned)min(32, nh - g * 32);
                 }
                 const int r = batch[bi] >> 16, cb0 = batch[bi] & 0xffff;
@@ -1744,15 +1755,62 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
                 else scan_batch(std::false_type{}, cb0, cb1, sh);
             }
         }
-        __syncthreads();   // the next home chunk rewrites hperm, the group boxes and counters
+        __syncthreads();   // the next home chunk rewrites the group boxes and counters
     }
     if (b.tile_tests) {   // one counter update per block, the blocks spread over kTestSlots counters
-        if (lane == 0 && wtests) atomicAdd(&blk_tests, wtests);
+        if (lane == 0 && wtests) atomicAdd(&blk_tests, (unsigned long long)wtests);
         __syncthreads();
         if (tid == 0 && blk_tests) atomicAdd(&b.tile_tests[(blockIdx.x + blockIdx.y) % kTestSlots], blk_tests);
     }
 }
 
+// Instance of c-bin bc (instances own consecutive c-bin ranges) and the
+// c-bin's coordinates in key order (x slowest).
+template <int DIM>
+__device__ __forceinline__ int cbin_of_block(const Bufs<float>& b, const Geo& geo, uint32_t bc, int c[3]) {
+    int lo = 0, hi = b.n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.inst[mid].bin_base <= bc) lo = mid;
+        else hi = mid - 1;
+    }
+    uint32_t rel = bc - b.inst[lo].bin_base;
+    c[2] = 0;
+    if (DIM == 3) {
+        c[2] = (int)(rel % (uint32_t)geo.n[2]);
+        rel /= (uint32_t)geo.n[2];
+    }
+    c[1] = (int)(rel % (uint32_t)geo.n[1]);
+    c[0] = (int)(rel / (uint32_t)geo.n[1]);
+    return lo;
+}
+
+// The pruned tile search: one block per c-bin of the pruned instances (grid:
+// every c-bin; the others' blocks return at once).  A kernel of its own, so
+// that its registers are allocated apart from the plain tile search's.
+template <int DIM>
+__global__ void __launch_bounds__(kTileThreads, 4) tile_pruned_kernel(Bufs<float> b) {
+    extern __shared__ __align__(32) unsigned char tile_smem[];
+    __shared__ GeoT<float> G;
+    __shared__ int inst_s, c_s[3];
+    if (threadIdx.x == 0) {
+        G.load(b.geo);
+        int c[3];
+        inst_s = cbin_of_block<DIM>(b, b.geo, blockIdx.x, c);
+        c_s[0] = c[0];
+        c_s[1] = c[1];
+        c_s[2] = c[2];
+    }
+    __syncthreads();
+    const InstDev& I = b.inst[inst_s];
+    if (!I.prune) return;   // block-uniform
+    const int c[3] = {c_s[0], c_s[1], c_s[2]};
+    tile_search_pruned<DIM>(b, G, I, inst_s, c, tile_smem);
+}
+
+// The plain tile search: one block per c-bin of the tiled instances whose
+// search cells are the c-bins (grid: every c-bin, in key order inside each
+// instance; other blocks return at once).
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 1) tile_search_kernel(Bufs<T> b) {
     using V = typename Vec4<T>::type;
@@ -1764,23 +1822,29 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 1) tile_sea
     __shared__ T rsh[kTileRanges][3];
     __shared__ int nr_s, tot_s, inst_s;
     __shared__ int64_t h0_s, h1_s;
-    const uint32_t kc = blockIdx.x;
+    const uint32_t bc = blockIdx.x;
     if (threadIdx.x == 0) {
         G.load(b.geo);
-        // instance of the key (instances own consecutive key ranges)
+        // instance of the c-bin (instances own consecutive c-bin ranges)
         int lo = 0, hi = b.n_inst - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (b.inst[mid].key_base <= kc) lo = mid;
+            if (b.inst[mid].bin_base <= bc) lo = mid;
             else hi = mid - 1;
         }
         inst_s = lo;
+    }
+    __syncthreads();
+    const InstDev& I = b.inst[inst_s];
+    if (!I.tiled || I.prune) return;   // block-uniform
+    // search cells are the c-bins: the c-bin's key (x slowest, as the c-bin order here)
+    const uint32_t kc = I.key_base + (bc - I.bin_base);
+    if (threadIdx.x == 0) {
         h0_s = min(b.start[kc], (uint32_t)b.n);
         h1_s = min(b.start[kc + 1], (uint32_t)b.n);
     }
     __syncthreads();
-    const InstDev& I = b.inst[inst_s];
-    if (!I.tiled || h0_s >= h1_s) return;   // block-uniform
+    if (h0_s >= h1_s) return;   // block-uniform
     bool amb = false;
     {
         // ambiguity of the periodic images is a property of the cell's window
@@ -1796,17 +1860,10 @@ __global__ void __launch_bounds__(kTileThreads, sizeof(T) == 4 ? 4 : 1) tile_sea
 #pragma unroll
         for (int d = 0; d < DIM; ++d) amb = amb || window_1d(g[d], g[d], 1, I.M[d], kk[d], G.wall[d]).amb;
     }
-    if (amb) {
+    if (amb)
         tile_search_cell<T, DIM, true>(b, G, I, inst_s, kc, h0_s, h1_s, sp, sv, rq0, rlen, rpre, rsh, nr_s, tot_s);
-        return;
-    }
-    if constexpr (sizeof(T) == 4) {
-        if (I.prune) {
-            tile_search_pruned<DIM>(b, G, I, inst_s, kc, h0_s, h1_s, tile_smem, rq0, rlen, rpre, rsh, nr_s, tot_s);
-            return;
-        }
-    }
-    tile_search_cell<T, DIM, false>(b, G, I, inst_s, kc, h0_s, h1_s, sp, sv, rq0, rlen, rpre, rsh, nr_s, tot_s);
+    else
+        tile_search_cell<T, DIM, false>(b, G, I, inst_s, kc, h0_s, h1_s, sp, sv, rq0, rlen, rpre, rsh, nr_s, tot_s);
 }
 
 // Direct search of one particle (global loads), used by the staged kernel for
@@ -2792,18 +2849,25 @@ cudaError_t launch_search(const Bufs<T>& b, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_tile_search(const Bufs<T>& b, cudaStream_t s) {
     if (b.n == 0 || !b.any_tiled || b.n_keys == 0) return cudaSuccess;
-    const size_t smem = tile_smem_bytes(b);
-    const dim3 grid(b.n_keys, sizeof(T) == 4 ? (unsigned)b.tile_split : 1u);   // split windows: binary32 only
-    if (b.geo.dim == 3) tile_search_kernel<T, 3><<<grid, b.tile_threads, smem, s>>>(b);
-    else tile_search_kernel<T, 2><<<grid, b.tile_threads, smem, s>>>(b);
+    const dim3 grid((unsigned)b.n_bins, sizeof(T) == 4 ? (unsigned)b.tile_split : 1u);   // split: binary32 only
+    if (b.any_plain_tiled) {
+        const size_t smem = tile_smem_bytes(b);
+        if (b.geo.dim == 3) tile_search_kernel<T, 3><<<grid, b.tile_threads, smem, s>>>(b);
+        else tile_search_kernel<T, 2><<<grid, b.tile_threads, smem, s>>>(b);
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (b.tile_prune) {
+            const size_t smem = pruned_smem_bytes(b.tile_cap);
+            if (b.geo.dim == 3) tile_pruned_kernel<3><<<grid, b.tile_threads, smem, s>>>(b);
+            else tile_pruned_kernel<2><<<grid, b.tile_threads, smem, s>>>(b);
+        }
+    }
     return cudaGetLastError();
 }
 
 template <typename T>
 size_t tile_smem_bytes(const Bufs<T>& b) {
-    const size_t plain = (size_t)b.tile_cap * 2 * sizeof(typename Vec4<T>::type);
-    if (sizeof(T) == 4 && b.tile_prune) return std::max(plain, pruned_smem_bytes(b.tile_cap));
-    return plain;
+    return (size_t)b.tile_cap * 2 * sizeof(typename Vec4<T>::type);
 }
 
 // Dynamic shared memory beyond 48 KiB must be allowed per kernel.
@@ -2811,8 +2875,14 @@ template <typename T>
 cudaError_t prepare_tile(const Bufs<T>& b) {
     const int bytes = (int)tile_smem_bytes(b);
     cudaError_t e = cudaFuncSetAttribute(tile_search_kernel<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(tile_search_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tile_search_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if constexpr (sizeof(T) == 4) {
+        const int pb = (int)pruned_smem_bytes(b.tile_cap);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(tile_pruned_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(tile_pruned_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
+    }
+    return e;
 }
 
 template <typename T>

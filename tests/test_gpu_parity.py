@@ -660,16 +660,20 @@ def test_tile_pruning_changes_speed_only(case):
     pos, vel = make_inputs(name, n, dim, lo, hi)
     pos, vel = f32_state(pos, vel, lo, hi, bc)
     out = []
+    # pruned (half c-bin search cells) where the contact distance is at most half a
+    # c-bin and every periodic dimension has 6 c-bins or more
+    expect = name in ("cubic3d_fp32_walls", "sod3d_fp32_narrow_contact")
     for flags in (k.KMC_FLAG_RECORD, k.KMC_FLAG_RECORD | k.KMC_FLAG_NO_TILE_PRUNE):
         cfg = k.make_config(dim_pos=dim, n_cells=n_cells, lo=lo, hi=hi, bc=bc, lam=lam, dt=dt, seed=9,
-                            precision=32, flags=flags, sub_cells=(1, 1, 1))
+                            precision=32, flags=flags)
         sim = k.Simulation(cfg, pos, vel)
         info = sim.info()
         if flags & k.KMC_FLAG_NO_TILE_PRUNE:
             assert info.tile_prune == 0
-        else:   # pruned where the contact distance is at most half a c-bin
-            width = min((hi[d] - lo[d]) / n_cells[d] for d in range(dim))
-            assert info.tile_prune == int(np.sqrt(info.R2) <= 0.5 * width)
+        else:
+            assert info.tile_prune == int(expect)
+            if expect:
+                assert list(info.sub_cells) == [2, 2, 2]
             pruned = info.tile_prune
         cand = sim.window_size()
         sim.step(3)
@@ -683,6 +687,7 @@ def test_tile_pruning_changes_speed_only(case):
     assert np.array_equal(p0, p1) and np.array_equal(w0, w1)
     assert t1 == 0.0
     assert (t0 > 0) == bool(pruned)
+    width = min((hi[d] - lo[d]) / n_cells[d] for d in range(dim))
     if n / np.prod(n_cells[:dim]) >= 50 and np.sqrt(info.R2) < 0.25 * width:
         # dense c-bins and a contact distance well inside one: fewer tests than
         # the plain search's (C_p - 1) / 2 per particle-step (window of the first step)
@@ -706,8 +711,9 @@ def test_tile_search_far_from_origin():
     assert (o["best"] >= 0).mean() > 0.05
     for flags in (k.KMC_FLAG_RECORD, k.KMC_FLAG_RECORD | k.KMC_FLAG_NO_TILE_PRUNE):
         cfg = k.make_config(dim_pos=dim, n_cells=n_cells, lo=lo, hi=hi, bc=bc, lam=lam, dt=dt, seed=5,
-                            precision=32, flags=flags, sub_cells=(1, 1, 1))
+                            precision=32, flags=flags)
         sim = k.Simulation(cfg, pos, vel)
+        assert sim.info().tile_prune == (0 if flags & k.KMC_FLAG_NO_TILE_PRUNE else 1)
         sim.step(1)
         best, partner = sim.partners()
         sim.close()
@@ -720,7 +726,8 @@ def test_tile_search_far_from_origin():
                                                (32, 96, 1536, 1), (64, 224, 768, 1)])
 def test_tile_search_parameters_do_not_change_results(prec, tt, cap, split):
     """Threads per c-bin block, staging capacity and the number of blocks that
-    share a c-bin's window (the autotuner's choices) change speed only: the
+    share a c-bin's window (the autotuner's choices; binary32: the pruned
+    search, binary64: the plain tile search) change speed only: the
     closest candidates and pairs equal the oracle's, from a capacity far below
     one neighbourhood (many staging chunks) to one above it, and with up to 8
     blocks per c-bin (some of them then without candidates)."""
@@ -731,10 +738,11 @@ def test_tile_search_parameters_do_not_change_results(prec, tt, cap, split):
     if prec == 32:
         pos, vel = f32_state(pos, vel, lo, hi, bc)
     cfg = k.make_config(dim_pos=dim, n_cells=n_cells, lo=lo, hi=hi, bc=bc, lam=lam, dt=dt, seed=5, precision=prec,
-                        flags=k.KMC_FLAG_RECORD, sub_cells=(1, 1, 1), tile_threads=tt, tile_cap=cap, tile_split=split)
+                        flags=k.KMC_FLAG_RECORD, tile_threads=tt, tile_cap=cap, tile_split=split)
     sim = k.Simulation(cfg, pos, vel)
     info = sim.info()
     assert (info.tile_threads, info.tile_cap, info.tile_split) == (tt, cap, split)
+    assert info.tile_prune == (prec == 32)   # binary32: the pruned search on half c-bins
     sim.step(1)
     best, partner = sim.partners()
     sim.close()
