@@ -1384,6 +1384,34 @@ __host__ __device__ constexpr size_t pruned_smem_bytes(int cap) {
     return (size_t)(28 + 28 / kCluster) * (size_t)(cap & ~15);
 }
 
+// Exclusive prefix sums of v(0) ... v(n - 1), n <= 96, by one whole warp: lane
+// l sums entries 3l ... 3l + 2, the lanes scan their sums; out[i] = v(0) + ... +
+// v(i - 1) for i <= n.
+template <typename Fn>
+__device__ __forceinline__ void warp_exclusive_scan96(int n, Fn v, int* out) {
+    const int lane = threadIdx.x & 31;
+    int x[3], own = 0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int i = 3 * lane + j;
+        x[j] = i < n ? v(i) : 0;
+        own += x[j];
+    }
+    int inc = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+    }
+    int acc = inc - own;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int i = 3 * lane + j;
+        if (i <= n) out[i] = acc;
+        acc += x[j];
+    }
+}
+
 // Search key of search cell (gx, gy, gz) of instance I.
 template <int DIM>
 __device__ __forceinline__ uint32_t cell_key(const InstDev& I, int gx, int gy, int gz) {
@@ -1397,7 +1425,7 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
                                                    int inst, const int c[3], unsigned char* smem) {
     constexpr int F = DIM - 1;   // fastest key dimension
     const int CAP = b.tile_cap & ~15;   // staged slots per chunk (a multiple of kCluster)
-    const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x, warp = tid >> 5, nwarps = nthr >> 5;
     // staged pair k (slots 2k, 2k + 1): pA (-x, -x', -y, -y'), pB (-z, -z', -vx, -vx'),
     // pC (-vy, -vy', -vz, -vz'), pQ (q, q') sorted positions (-1: pad)
     float4* pA = reinterpret_cast<float4*>(smem);
@@ -1417,7 +1445,8 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
     __shared__ int gminp[kTileThreads / 32];              // lowest sorted position of each home group
     __shared__ int gnext[kTileThreads / 32];              // next batch of each home group
     __shared__ int batch[kMaxBatches];                    // batch i: range << 16 | first cluster
-    __shared__ int nr_s, nbatch_s;
+    __shared__ int bpre[kSubRanges + 1];                  // first batch of each range's part
+    __shared__ int nr_s;
     __shared__ unsigned long long blk_tests;
 
     // the homes: rows (2 c_x + i, 2 c_y + j) of the c-bin, each with its two
@@ -1496,15 +1525,8 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
     __syncthreads();
     const int nr = nr_s;
     // every range padded to whole clusters: range r occupies [ppre[r], ppre[r + 1])
-    if (tid == 0) {
-        blk_tests = 0ull;
-        int acc = 0;
-        for (int r = 0; r < nr; ++r) {
-            ppre[r] = acc;
-            acc += (rlen[r] + kCluster - 1) / kCluster * kCluster;
-        }
-        ppre[nr] = acc;
-    }
+    if (warp == 0) warp_exclusive_scan96(nr, [&](int r) { return (rlen[r] + kCluster - 1) / kCluster * kCluster; }, ppre);
+    if (tid == 0) blk_tests = 0ull;
     __syncthreads();
     const int ptot = ppre[nr];
     // window split between gridDim.y blocks of the c-bin, as in the plain tile search
@@ -1524,9 +1546,11 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
     const float margin = sqrtf(R2) * (1.f + 0x1p-10f) + 0x1p-7f * wmax + 0x1p-16f * (cmax + lmax);
     const float qnan = __int_as_float(0x7fc00000);
 
-    // Stage chunk [c0, c0 + per) of the padded ranges: every slot gathers its
-    // candidate (a pad: NaN, position -1), and the kCluster lanes of a cluster
-    // combine their swept boxes and positions.
+    // Stage chunk [c0, c0 + per) of the padded ranges: a warp per range part,
+    // each slot gathers its candidate (a pad: NaN, position -1) with the next
+    // slot's loads already in flight, and the kCluster lanes of a cluster
+    // combine their swept boxes and positions.  Then the batches of kBatch
+    // clusters of every part.
     auto stage = [&](int c0) {
         const int cn = min(per, ptot - c0);
         for (int r = tid; r < nr; r += nthr) {   // up to kSubRanges ranges, blocks from 64 threads
@@ -1535,55 +1559,69 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
             pb0[r] = a - c0;
             pb1[r] = e - c0;
         }
-        for (int s0 = 0; s0 < cn; s0 += nthr) {   // the same trip count on every lane (shuffles)
-            const int sl = s0 + tid;
-            float4 P = make_float4(qnan, qnan, qnan, qnan), Q = P;
-            int32_t q = -1;
-            if (sl < cn) {
-                const int ge = c0 + sl;
-                int lo = 0, hi = nr - 1;   // the range holding padded offset ge
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (ppre[mid] <= ge) lo = mid;
-                    else hi = mid - 1;
+        __syncthreads();
+        for (int r = warp; r < nr; r += nwarps) {
+            const int s0 = pb0[r], s1 = pb1[r];
+            if (s0 >= s1) continue;   // warp-uniform
+            const int32_t qb = rq0[r] + c0 - ppre[r];   // sorted position of slot s: qb + s
+            const int sv = min(s1, ppre[r] + rlen[r] - c0);   // slots below sv hold candidates
+            auto fetch = [&](int sl, float4& P, float4& Q) {
+                P = make_float4(qnan, qnan, qnan, qnan);
+                Q = P;
+                if (sl < sv) {
+                    P = ldg_vec(b.posA + qb + sl);
+                    Q = ldg_vec(b.velA + qb + sl);
                 }
-                const int o = ge - ppre[lo];
-                if (o < rlen[lo]) {
-                    q = rq0[lo] + o;
-                    P = ldg_vec(b.posA + q);
-                    Q = ldg_vec(b.velA + q);
+            };
+            float4 P, Q;
+            fetch(s0 + lane, P, Q);
+            for (int e0 = s0; e0 < s1; e0 += 32) {   // the same trip count on the warp's lanes (shuffles)
+                const int sl = e0 + lane;
+                float4 Pn, Qn;
+                fetch(sl + 32, Pn, Qn);
+                if (sl < s1) {
+                    const int k = sl >> 1, h = sl & 1;
+                    float* pa = reinterpret_cast<float*>(pA + k);
+                    float* pbz = reinterpret_cast<float*>(pB + k);
+                    float* pc = reinterpret_cast<float*>(pC + k);
+                    pa[h] = -P.x;
+                    pa[2 + h] = -P.y;
+                    pbz[h] = -P.z;
+                    pbz[2 + h] = -Q.x;
+                    pc[h] = -Q.y;
+                    pc[2 + h] = -Q.z;
+                    reinterpret_cast<int32_t*>(pQ + k)[h] = sl < sv ? qb + sl : -1;
                 }
-                const int k = sl >> 1, h = sl & 1;
-                float* a = reinterpret_cast<float*>(pA + k);
-                float* bz = reinterpret_cast<float*>(pB + k);
-                float* cc = reinterpret_cast<float*>(pC + k);
-                a[h] = -P.x;
-                a[2 + h] = -P.y;
-                bz[h] = -P.z;
-                bz[2 + h] = -Q.x;
-                cc[h] = -Q.y;
-                cc[2 + h] = -Q.z;
-                reinterpret_cast<int32_t*>(pQ + k)[h] = q;
-            }
-            const float x[3] = {P.x, P.y, P.z}, v[3] = {Q.x, Q.y, Q.z};
-            float lo[3], hi[3];
-            swept_box<DIM>(x, v, dt, lo, hi);
+                const float x[3] = {P.x, P.y, P.z}, v[3] = {Q.x, Q.y, Q.z};
+                float lo[3], hi[3];
+                swept_box<DIM>(x, v, dt, lo, hi);
+                int32_t q = sl < sv ? qb + sl : -1;
 #pragma unroll
-            for (int o = 1; o < kCluster; o <<= 1) {   // a pad's NaN drops out of fminf / fmaxf
+                for (int o = 1; o < kCluster; o <<= 1) {   // a pad's NaN drops out of fminf / fmaxf
 #pragma unroll
-                for (int d = 0; d < DIM; ++d) {
-                    lo[d] = fminf(lo[d], __shfl_xor_sync(kFull, lo[d], o));
-                    hi[d] = fmaxf(hi[d], __shfl_xor_sync(kFull, hi[d], o));
+                    for (int d = 0; d < DIM; ++d) {
+                        lo[d] = fminf(lo[d], __shfl_xor_sync(kFull, lo[d], o));
+                        hi[d] = fmaxf(hi[d], __shfl_xor_sync(kFull, hi[d], o));
+                    }
+                    q = max(q, __shfl_xor_sync(kFull, q, o));
                 }
-                q = max(q, __shfl_xor_sync(kFull, q, o));
+                if ((lane & (kCluster - 1)) == 0 && sl < s1) {
+                    const int cl = sl / kCluster;
+                    cbx[cl] = make_float2(lo[0], hi[0]);
+                    cby[cl] = make_float2(lo[1], hi[1]);
+                    if (DIM == 3) cbz[cl] = make_float2(lo[2], hi[2]);
+                    cqmax[cl] = q;
+                }
+                P = Pn;
+                Q = Qn;
             }
-            if ((tid & (kCluster - 1)) == 0 && sl < cn) {
-                const int cl = sl / kCluster;
-                cbx[cl] = make_float2(lo[0], hi[0]);
-                cby[cl] = make_float2(lo[1], hi[1]);
-                if (DIM == 3) cbz[cl] = make_float2(lo[2], hi[2]);
-                cqmax[cl] = q;
-            }
+        }
+        if (warp == 0) {   // batch i: range << 16 | first cluster, ranges in order
+            warp_exclusive_scan96(nr, [&](int r) { return ((pb1[r] - pb0[r]) / kCluster + kBatch - 1) / kBatch; }, bpre);
+            __syncwarp();
+            for (int r = lane; r < nr; r += 32)
+                for (int j = 0, cl = pb0[r] / kCluster; cl < pb1[r] / kCluster; ++j, cl += kBatch)
+                    batch[bpre[r] + j] = (r << 16) | cl;
         }
     };
 
@@ -1644,16 +1682,9 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
                 __syncthreads();
                 stage(c0);
             }
-            // batches of kBatch clusters of each range's part; fresh group counters
-            if (tid == 0) {
-                int nb = 0;
-                for (int r = 0; r < nr; ++r)
-                    for (int cl = pb0[r] / kCluster; cl < pb1[r] / kCluster; cl += kBatch) batch[nb++] = (r << 16) | cl;
-                nbatch_s = nb;
-            }
-            if (tid < ngroups) gnext[tid] = 0;
+            if (tid < ngroups) gnext[tid] = 0;   // fresh group counters
             __syncthreads();
-            const int nbatch = nbatch_s;
+            const int nbatch = bpre[nr];
             int g = warp % ngroups, loaded = -1;
             PairHome ph;
             float wlo[3], whi[3];
