@@ -56,6 +56,7 @@ struct kmc_handle {
     uint32_t n_stage_tiles = 0;
     int stage_cap = 0, stage_rows = 0, stage_stride = 0, stage_pair_cap = 0, any_direct = 1, any_tiled = 0;
     int any_plain_tiled = 0;
+    int cbin_moments = 0;   // moments one warp per c-bin (every c-bin: at most kCbinRows runs of search cells)
     int tile_threads = 256, tile_cap = 1536, tile_split = 1, tile_prune = 1;
     int64_t n_bins = 0, bins_per_inst = 0;
     int64_t bytes = 0;
@@ -146,6 +147,7 @@ Bufs<T> make_bufs(const kmc_handle* h) {
     b.tile_cap = h->tile_cap;
     b.tile_split = h->tile_split;
     b.tile_prune = h->tile_prune;
+    b.cbin_moments = h->cbin_moments;
     b.tile_tests = h->tile_tests;
     b.id_bits = h->id_bits;
     b.id_mask = h->id_bits >= 32 ? 0xffffffffu : ((1u << h->id_bits) - 1u);
@@ -716,6 +718,9 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
                 return bail(fail(h, KMC_ERANGE, "search grid exceeds 2^32 keys; set sub_cells"));
         }
         h->n_keys = (uint32_t)keys;
+        h->cbin_moments = 1;
+        for (const InstDev& I : h->inst_h)
+            if ((h->dim == 3 ? I.s[0] * I.s[1] : I.s[0]) > kCbinRows) h->cbin_moments = 0;
         // keys of the cells, one key after them for absorbed particles, and the end offset
         h->n_tiles = (uint32_t)((keys + 2 + kScanTile - 1) / kScanTile);
         plan_staged_search(h, max_occ);

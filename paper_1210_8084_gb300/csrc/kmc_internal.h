@@ -20,6 +20,7 @@ constexpr uint32_t kSpinCap = 1u << 22;  // bounded waits: iterations before giv
 constexpr int kFoldCap = 64;           // wall folds per coordinate per step
 constexpr int kAccFields = 10;         // per c-bin accumulator: N, Sum v (3), Sum v^2 (3), Sum W, collided
 constexpr int kTestSlots = 256;        // counters of the pruned tile search's pair tests (blocks spread over them)
+constexpr int kCbinRows = 4;           // rows of search cells per c-bin up to which moments go one warp per c-bin
                                        // count, Sum v.r_hat
 constexpr int kMomStride = 18;         // per c-bin output: 8 raw, 8 derived, Sum v.r_hat, v_r
 constexpr uint32_t kCanonMax = 16384;  // search cells up to this many particles are put in id order
@@ -145,6 +146,7 @@ struct Bufs {
     int any_plain_tiled;     // some tiled instance searches on its c-bins (not pruned)
     int dsmc;                // the random-partner comparison variant instead of the PoCA search
     int radial;              // accumulate Sum v.r_hat (KMC_FLAG_RADIAL_MOMENT)
+    int cbin_moments;        // every c-bin is at most kCbinRows runs of search cells: moments per c-bin
     int tile_threads;        // tile search: threads per c-bin block (a multiple of 32, 64 ... 256)
     int tile_cap;            // tile search: candidates staged in shared memory at once (even)
     int tile_split;          // tile search: blocks sharing one c-bin's window (binary32)

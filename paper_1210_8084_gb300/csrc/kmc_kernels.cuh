@@ -300,34 +300,41 @@ __device__ __forceinline__ long long fixed_of(double x, double scale) { return _
 __device__ __forceinline__ void block_moment_partials(MomentSlots& S, unsigned long long* acc, bool valid,
                                                       uint32_t bin, const long long fl[kMomSums], int cnt_l,
                                                       int coll_l) {
-    unsigned todo = __ballot_sync(kFull, valid);
-    while (todo) {
-        const int leader = __ffs(todo) - 1;
-        const uint32_t gb = __shfl_sync(kFull, bin, leader);
-        const bool mine = valid && bin == gb;
-        const unsigned grp = __ballot_sync(kFull, mine);
-        long long f[kMomSums];
+    // runs of lanes with the same bin (a lane without particles is a run of its
+    // own): a segmented sum over the warp in five shuffle steps, whatever the
+    // number of runs; the last lane of each run adds a slot
+    const unsigned lane = lane_id();
+    const uint32_t key = valid ? bin : 0xffffffffu;
+    const uint32_t prev = __shfl_up_sync(kFull, key, 1);
+    const unsigned heads = __ballot_sync(kFull, lane == 0 || !valid || key != prev);
+    const int seg = __popc(heads & (0xffffffffu >> (31 - lane)));   // run index of this lane
+    long long f[kMomSums];
 #pragma unroll
-        for (int k = 0; k < kMomSums; ++k) f[k] = mine ? fl[k] : 0ll;
-        int c = mine ? cnt_l : 0, cc = mine ? coll_l : 0;
-        if (grp != (1u << leader)) {
+    for (int k = 0; k < kMomSums; ++k) f[k] = valid ? fl[k] : 0ll;
+    int c = valid ? cnt_l : 0, cc = valid ? coll_l : 0;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
+    for (int o = 1; o < 32; o <<= 1) {
+        const int so = __shfl_up_sync(kFull, seg, o);
+        const bool add = lane >= (unsigned)o && so == seg;
 #pragma unroll
-                for (int k = 0; k < kMomSums; ++k) f[k] += __shfl_xor_sync(kFull, f[k], o);
-            }
-            c = __reduce_add_sync(kFull, (unsigned)c);
-            cc = __reduce_add_sync(kFull, (unsigned)cc);
+        for (int k = 0; k < kMomSums; ++k) {
+            const long long y = __shfl_up_sync(kFull, f[k], o);
+            if (add) f[k] += y;
         }
-        if ((int)lane_id() == leader) {
-            const int slot = atomicAdd(&S.n, 1);
-            S.bin[slot] = gb;
-#pragma unroll
-            for (int k = 0; k < kMomSums; ++k) S.f[k][slot] = f[k];
-            S.cnt[slot] = c;
-            S.coll[slot] = cc;
+        const int yc = __shfl_up_sync(kFull, c, o), ycc = __shfl_up_sync(kFull, cc, o);
+        if (add) {
+            c += yc;
+            cc += ycc;
         }
-        todo &= ~grp;
+    }
+    const int seg_next = __shfl_down_sync(kFull, seg, 1);
+    if (valid && (lane == 31 || seg_next != seg)) {
+        const int slot = atomicAdd(&S.n, 1);
+        S.bin[slot] = bin;
+#pragma unroll
+        for (int k = 0; k < kMomSums; ++k) S.f[k][slot] = f[k];
+        S.cnt[slot] = c;
+        S.coll[slot] = cc;
     }
     __syncthreads();
     const int ns = S.n;
@@ -2746,6 +2753,91 @@ __global__ void __launch_bounds__(kThreads) moments_kernel(Bufs<T> b, int use_vi
     block_moment_partials(S, b.acc, cnt > 0, cur, f, cnt, coll);
 }
 
+// The same sums where every c-bin of every instance is at most kCbinRows runs
+// of consecutive search cells (the search cells are the c-bins or their
+// halves): one warp per c-bin reads its runs of the sorted state A and stores
+// its sums, with no atomics (fixed-point sums do not depend on their order).
+template <typename T, int DIM, bool RADIAL>
+__global__ void __launch_bounds__(kThreads) moments_cbin_kernel(Bufs<T> b, int use_virial) {
+    using V = typename Vec4<T>::type;
+    __shared__ GeoT<T> G;
+    if (threadIdx.x == 0) G.load(b.geo);
+    __syncthreads();
+    const int64_t bc = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    if (bc >= b.n_bins) return;   // warp-uniform
+    const int lane = (int)lane_id();
+    int inst = 0;
+    {
+        int hi = b.n_inst - 1;
+        while (inst < hi) {
+            const int mid = (inst + hi + 1) >> 1;
+            if ((int64_t)b.inst[mid].bin_base <= bc) inst = mid;
+            else hi = mid - 1;
+        }
+    }
+    const InstDev& I = b.inst[inst];
+    // c-bin coordinates in moment order (x fastest)
+    uint32_t rel = (uint32_t)(bc - I.bin_base);
+    const int cx = (int)(rel % (uint32_t)G.n[0]);
+    rel /= (uint32_t)G.n[0];
+    const int cy = DIM == 3 ? (int)(rel % (uint32_t)G.n[1]) : (int)rel;
+    const int cz = DIM == 3 ? (int)(rel / (uint32_t)G.n[1]) : 0;
+    const T sv = pow2_of(b.dyn[inst].mom_e[0], T()), s2 = pow2_of(b.dyn[inst].mom_e[1], T());
+    const T sw = pow2_of(b.dyn[inst].mom_e[2], T());
+    long long f[kMomSums] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int cnt = 0, coll = 0;
+    // rows of search cells inside the c-bin: (x, y) in 3-D, x in 2-D; each row's
+    // cells along the fast dimension are consecutive keys
+    const int rows = DIM == 3 ? I.s[0] * I.s[1] : I.s[0];
+    const int sf = DIM == 3 ? I.s[2] : I.s[1];
+    for (int row = 0; row < rows; ++row) {
+        const int gx = cx * I.s[0] + (DIM == 3 ? row / I.s[1] : row);
+        uint32_t key;
+        if (DIM == 3)
+            key = I.key_base + ((uint32_t)gx * (uint32_t)I.M[1] + (uint32_t)(cy * I.s[1] + row % I.s[1])) *
+                                   (uint32_t)I.M[2] + (uint32_t)(cz * sf);
+        else
+            key = I.key_base + (uint32_t)gx * (uint32_t)I.M[1] + (uint32_t)(cy * sf);
+        const int64_t q0 = min(b.start[key], (uint32_t)b.n), q1 = min(b.start[key + (uint32_t)sf], (uint32_t)b.n);
+        for (int64_t p = q0 + lane; p < q1; p += 32) {
+            const V P = b.posA[p];
+            const V Q = b.velA[p];
+            const bool collided = use_virial && Q.w != R<T>::inf();
+            f[0] += fixed_of(Q.x, sv); f[1] += fixed_of(Q.y, sv); f[2] += fixed_of(Q.z, sv);
+            f[3] += fixed_of(Q.x * Q.x, s2); f[4] += fixed_of(Q.y * Q.y, s2); f[5] += fixed_of(Q.z * Q.z, s2);
+            if (collided) f[6] += fixed_of(Q.w, sw);
+            if (RADIAL) {   // Eq. vel_r, as in moments_kernel
+                const T x[3] = {P.x, P.y, P.z};
+                const T v3[3] = {Q.x, Q.y, Q.z};
+                T r2 = (T)0, vd = (T)0;
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                    const T dx = x[d] - G.rc[d];
+                    r2 += dx * dx;
+                    vd += v3[d] * dx;
+                }
+                if (r2 > (T)0) f[7] += fixed_of(vd / R<T>::sqrt_(r2), sv);
+            }
+            cnt += 1;
+            coll += collided ? 1 : 0;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < kMomSums; ++k) f[k] += __shfl_xor_sync(kFull, f[k], o);
+    }
+    cnt = (int)__reduce_add_sync(kFull, (unsigned)cnt);
+    coll = (int)__reduce_add_sync(kFull, (unsigned)coll);
+    if (lane == 0) {
+        unsigned long long* a = b.acc + (size_t)bc * kAccFields;
+        a[0] = (unsigned long long)cnt;
+#pragma unroll
+        for (int k = 0; k < kMomSums; ++k) a[acc_field(k)] = (unsigned long long)f[k];
+        a[8] = (unsigned long long)coll;
+    }
+}
+
 // Candidates each particle of A examines (the sizes of its search window), summed
 // over the particles: a diagnostic for the arithmetic roofline of the search.
 template <typename T, int DIM>
@@ -2969,6 +3061,17 @@ cudaError_t launch_cell_keys(const Bufs<T>& b, int32_t* keys, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_moments(const Bufs<T>& b, int use_virial, cudaStream_t s) {
     if (b.n == 0) return cudaSuccess;
+    if (b.cbin_moments) {   // one warp per c-bin
+        const unsigned blocks = (unsigned)((b.n_bins + kThreads / 32 - 1) / (kThreads / 32));
+        if (b.radial) {
+            if (b.geo.dim == 3) moments_cbin_kernel<T, 3, true><<<blocks, kThreads, 0, s>>>(b, use_virial);
+            else moments_cbin_kernel<T, 2, true><<<blocks, kThreads, 0, s>>>(b, use_virial);
+        } else {
+            if (b.geo.dim == 3) moments_cbin_kernel<T, 3, false><<<blocks, kThreads, 0, s>>>(b, use_virial);
+            else moments_cbin_kernel<T, 2, false><<<blocks, kThreads, 0, s>>>(b, use_virial);
+        }
+        return cudaGetLastError();
+    }
     const int64_t threads = (b.n + kMomItems - 1) / kMomItems;
     const unsigned blocks = (unsigned)((threads + kThreads - 1) / kThreads);
     if (b.radial) {
