@@ -2787,40 +2787,70 @@ __global__ void __launch_bounds__(kThreads) moments_cbin_kernel(Bufs<T> b, int u
     long long f[kMomSums] = {0, 0, 0, 0, 0, 0, 0, 0};
     int cnt = 0, coll = 0;
     // rows of search cells inside the c-bin: (x, y) in 3-D, x in 2-D; each row's
-    // cells along the fast dimension are consecutive keys
+    // cells along the fast dimension are consecutive keys.  Lane r < rows reads
+    // row r's range, then the lanes stride over the rows' particles together.
     const int rows = DIM == 3 ? I.s[0] * I.s[1] : I.s[0];
     const int sf = DIM == 3 ? I.s[2] : I.s[1];
-    for (int row = 0; row < rows; ++row) {
-        const int gx = cx * I.s[0] + (DIM == 3 ? row / I.s[1] : row);
+    uint32_t r0 = 0, rl = 0;
+    if (lane < rows) {
+        const int gx = cx * I.s[0] + (DIM == 3 ? lane / I.s[1] : lane);
         uint32_t key;
         if (DIM == 3)
-            key = I.key_base + ((uint32_t)gx * (uint32_t)I.M[1] + (uint32_t)(cy * I.s[1] + row % I.s[1])) *
+            key = I.key_base + ((uint32_t)gx * (uint32_t)I.M[1] + (uint32_t)(cy * I.s[1] + lane % I.s[1])) *
                                    (uint32_t)I.M[2] + (uint32_t)(cz * sf);
         else
             key = I.key_base + (uint32_t)gx * (uint32_t)I.M[1] + (uint32_t)(cy * sf);
-        const int64_t q0 = min(b.start[key], (uint32_t)b.n), q1 = min(b.start[key + (uint32_t)sf], (uint32_t)b.n);
-        for (int64_t p = q0 + lane; p < q1; p += 32) {
-            const V P = b.posA[p];
-            const V Q = b.velA[p];
-            const bool collided = use_virial && Q.w != R<T>::inf();
-            f[0] += fixed_of(Q.x, sv); f[1] += fixed_of(Q.y, sv); f[2] += fixed_of(Q.z, sv);
-            f[3] += fixed_of(Q.x * Q.x, s2); f[4] += fixed_of(Q.y * Q.y, s2); f[5] += fixed_of(Q.z * Q.z, s2);
-            if (collided) f[6] += fixed_of(Q.w, sw);
-            if (RADIAL) {   // Eq. vel_r, as in moments_kernel
-                const T x[3] = {P.x, P.y, P.z};
-                const T v3[3] = {Q.x, Q.y, Q.z};
-                T r2 = (T)0, vd = (T)0;
+        r0 = min(b.start[key], (uint32_t)b.n);
+        rl = min(b.start[key + (uint32_t)sf], (uint32_t)b.n) - r0;
+    }
+    uint32_t rs[kCbinRows], re[kCbinRows];   // row r: particles [rs, re) of the c-bin's concatenation
+    uint32_t base[kCbinRows];
+    uint32_t total = 0;
 #pragma unroll
-                for (int d = 0; d < DIM; ++d) {
-                    const T dx = x[d] - G.rc[d];
-                    r2 += dx * dx;
-                    vd += v3[d] * dx;
-                }
-                if (r2 > (T)0) f[7] += fixed_of(vd / R<T>::sqrt_(r2), sv);
+    for (int r = 0; r < kCbinRows; ++r) {
+        base[r] = __shfl_sync(kFull, r0, r);
+        rs[r] = total;
+        total += r < rows ? __shfl_sync(kFull, rl, r) : 0u;
+        re[r] = total;
+    }
+    auto pos_of = [&](uint32_t i) -> int64_t {   // sorted position of the c-bin's particle i
+        int64_t p = 0;
+#pragma unroll
+        for (int r = 0; r < kCbinRows; ++r)
+            if (i >= rs[r] && i < re[r]) p = (int64_t)base[r] + (i - rs[r]);
+        return p;
+    };
+    auto add = [&](const V& P, const V& Q) {
+        const bool collided = use_virial && Q.w != R<T>::inf();
+        f[0] += fixed_of(Q.x, sv); f[1] += fixed_of(Q.y, sv); f[2] += fixed_of(Q.z, sv);
+        f[3] += fixed_of(Q.x * Q.x, s2); f[4] += fixed_of(Q.y * Q.y, s2); f[5] += fixed_of(Q.z * Q.z, s2);
+        if (collided) f[6] += fixed_of(Q.w, sw);
+        if (RADIAL) {   // Eq. vel_r, as in moments_kernel
+            const T x[3] = {P.x, P.y, P.z};
+            const T v3[3] = {Q.x, Q.y, Q.z};
+            T r2 = (T)0, vd = (T)0;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                const T dx = x[d] - G.rc[d];
+                r2 += dx * dx;
+                vd += v3[d] * dx;
             }
-            cnt += 1;
-            coll += collided ? 1 : 0;
+            if (r2 > (T)0) f[7] += fixed_of(vd / R<T>::sqrt_(r2), sv);
         }
+        cnt += 1;
+        coll += collided ? 1 : 0;
+    };
+    for (uint32_t i = lane; i < total; i += 64) {   // two particles per lane with their loads in flight
+        const bool two = i + 32 < total;
+        const int64_t p0 = pos_of(i), p1 = two ? pos_of(i + 32) : p0;
+        const V P0 = b.posA[p0], Q0 = b.velA[p0];
+        V P1 = P0, Q1 = Q0;
+        if (two) {
+            P1 = b.posA[p1];
+            Q1 = b.velA[p1];
+        }
+        add(P0, Q0);
+        if (two) add(P1, Q1);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
