@@ -266,6 +266,44 @@ def test_batched_equals_plain_instances():
     batch.close()
 
 
+def test_batched_pruned_and_plain_tile_instances():
+    """A batch whose instances take different tile searches (the pruned search on
+    half c-bins where the contact distance is small, the plain tile search on
+    c-bins where it is not) evolves each instance exactly as a separate run, and
+    launches both tile kernels."""
+    _setup()
+    import paper_1210_8084_gb300 as k
+    from paper_1210_8084_gb300 import inputs
+    lo, hi, bc, cells = (0, 0, 0), (1, 0.5, 0.5), (WALL, PER, PER), (12, 6, 6)
+    ns, lams = [40_000, 30_000, 20_000], [5e-3, 1e-4, 5e-2]
+    insts, P, V = [], [], []
+    for i, (n, lam) in enumerate(zip(ns, lams)):
+        p, v = f32_state(*inputs.sod_tube(n, seed=200 + i, lo=lo, hi=hi), lo, hi, bc)
+        P.append(p)
+        V.append(v)
+        insts.append(dict(n=n, lam=lam, dt=1e-2, seed=300 + i))
+    base = dict(dim_pos=3, n_cells=cells, lo=lo, hi=hi, bc=bc, precision=32)
+    batch = k.Simulation(k.make_config(**base, instances=insts), np.concatenate(P), np.concatenate(V))
+    info = batch.info()
+    assert info.tile_prune == 1
+    assert info.kernels_per_step == 6   # plain tile search, pruned tile search, move, scan, two scatter passes
+    batch.step(3)
+    pb, vb = batch.state()
+    raw_b = batch.moments()[0]
+    off, nb = 0, int(np.prod(cells))
+    for i, inst in enumerate(insts):
+        plain = k.Simulation(k.make_config(**base, lam=inst["lam"], dt=inst["dt"], seed=inst["seed"]), P[i], V[i])
+        assert plain.info().tile_prune == (0 if i == 1 else 1)
+        plain.step(3)
+        pp, vp = plain.state()
+        assert np.array_equal(pp, pb[off:off + ns[i]]), i
+        assert np.array_equal(vp, vb[off:off + ns[i]]), i
+        assert np.array_equal(plain.moments()[0], raw_b[nb * i:nb * (i + 1)]), i
+        off += ns[i]
+        plain.close()
+    batch.close()
+
+
 @pytest.mark.parametrize("n", [0, 1, 2, 255, 257])
 def test_tiny_and_ragged_sizes(n):
     _setup()
@@ -372,6 +410,11 @@ TILE_CASES = [
     # the 3-D Sod benchmark's geometry at small N: ~208 per dense c-bin, R = 0.11 and v_th dt = 0.2 c-bin widths
     ("sod3d_fp32_narrow_contact", 120_000, 3, (16, 8, 8), (0, 0, 0), (1, 0.5, 0.5), (WALL, PER, PER), 0.0139,
      0.0125, 32),
+    # 2-D with a contact distance of a third of a c-bin (the pruned search in 2-D), walls on all sides
+    ("square2d_fp32_narrow", 200_000, 2, (40, 40, 1), (0, 0, 0), (1, 1, 1), (WALL, WALL, PER), 0.02, 0.005, 32),
+    # 2-D periodic in y (images in the pruned search's rows)
+    ("slab2d_fp32_periodic_narrow", 100_000, 2, (20, 12, 1), (0, 0, 0), (1, 0.6, 1), (WALL, PER, PER), 0.02, 0.01,
+     32),
 ]
 
 
@@ -662,7 +705,8 @@ def test_tile_pruning_changes_speed_only(case):
     out = []
     # pruned (half c-bin search cells) where the contact distance is at most half a
     # c-bin and every periodic dimension has 6 c-bins or more
-    expect = name in ("cubic3d_fp32_walls", "sod3d_fp32_narrow_contact")
+    expect = name in ("cubic3d_fp32_walls", "sod3d_fp32_narrow_contact", "square2d_fp32_narrow",
+                      "slab2d_fp32_periodic_narrow")
     for flags in (k.KMC_FLAG_RECORD, k.KMC_FLAG_RECORD | k.KMC_FLAG_NO_TILE_PRUNE):
         cfg = k.make_config(dim_pos=dim, n_cells=n_cells, lo=lo, hi=hi, bc=bc, lam=lam, dt=dt, seed=9,
                             precision=32, flags=flags)
@@ -673,7 +717,7 @@ def test_tile_pruning_changes_speed_only(case):
         else:
             assert info.tile_prune == int(expect)
             if expect:
-                assert list(info.sub_cells) == [2, 2, 2]
+                assert list(info.sub_cells)[:dim] == [2] * dim
             pruned = info.tile_prune
         cand = sim.window_size()
         sim.step(3)
