@@ -744,6 +744,8 @@ int kmc_init(const kmc_config* cfg, int64_t n, const void* pos, const void* vel,
             prune_any |= I.prune;
         }
         h->tile_prune = prune_any;
+        // the pruned search's default staging capacity fills 4 blocks per SM
+        if (prune_any && h->cfg.tile_cap == 0 && !h->any_plain_tiled) h->tile_cap = kPrunedCap;
         if (cudaMemcpyAsync(h->inst_d, h->inst_h.data(), sizeof(InstDev) * h->n_inst, cudaMemcpyHostToDevice,
                             h->stream) != cudaSuccess)
             return bail(fail(h, KMC_ECUDA, "upload of instance table failed"));

@@ -18,6 +18,7 @@
 // search cell (a c-bin subdivided s_d times per dimension, x slowest).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <math.h>
 #include <stdint.h>
 
@@ -1385,10 +1386,17 @@ __device__ __forceinline__ void swept_box(const float x[3], const float v[3], fl
 }
 
 // Dynamic shared memory of the pruned search for a capacity of `cap` staged
-// candidates (cap rounded down to a multiple of 16): six floats and one int per
-// staged candidate, three float2 and one int per cluster.
+// candidates (cap rounded down to a multiple of 16): six floats per staged
+// candidate, three half2 and one int per cluster.
 __host__ __device__ constexpr size_t pruned_smem_bytes(int cap) {
-    return (size_t)(28 + 28 / kCluster) * (size_t)(cap & ~15);
+    return (size_t)(24 + 16 / kCluster) * (size_t)(cap & ~15);
+}
+
+// Conservative half-precision bounds of a box coordinate in c-bin units of the
+// block's frame: lo rounded down, hi up, both widened by eps (the rounding of
+// the float map into those units).
+__device__ __forceinline__ __half2 unit_bounds(float lo, float hi, float eps) {
+    return __halves2half2(__float2half_rd(lo - eps), __float2half_ru(hi + eps));
 }
 
 // Exclusive prefix sums of v(0) ... v(n - 1), n <= 96, by one whole warp: lane
@@ -1434,16 +1442,16 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
     const int CAP = b.tile_cap & ~15;   // staged slots per chunk (a multiple of kCluster)
     const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x, warp = tid >> 5, nwarps = nthr >> 5;
     // staged pair k (slots 2k, 2k + 1): pA (-x, -x', -y, -y'), pB (-z, -z', -vx, -vx'),
-    // pC (-vy, -vy', -vz, -vz'), pQ (q, q') sorted positions (-1: pad)
+    // pC (-vy, -vy', -vz, -vz')
     float4* pA = reinterpret_cast<float4*>(smem);
     float4* pB = pA + CAP / 2;
     float4* pC = pB + CAP / 2;
-    int2* pQ = reinterpret_cast<int2*>(pC + CAP / 2);
-    // cluster c: its box (lo, hi) per dimension without its range's image shift,
-    // and the largest sorted position in it
-    float2* cbx = reinterpret_cast<float2*>(pQ + CAP / 2);
-    float2* cby = cbx + CAP / kCluster;
-    float2* cbz = cby + CAP / kCluster;
+    // cluster c: its box (lo, hi) per dimension in the block's frame (c-bin units
+    // from the c-bin's low corner, its range's image shift applied), and the
+    // largest sorted position in it
+    __half2* cbx = reinterpret_cast<__half2*>(pC + CAP / 2);
+    __half2* cby = cbx + CAP / kCluster;
+    __half2* cbz = cby + CAP / kCluster;
     int* cqmax = reinterpret_cast<int*>(cbz + CAP / kCluster);
     __shared__ int rq0[kSubRanges], rlen[kSubRanges], ppre[kSubRanges + 1], pb0[kSubRanges], pb1[kSubRanges];
     __shared__ float rsh[kSubRanges][3];
@@ -1551,6 +1559,11 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
         lmax = fmaxf(lmax, G.L[d]);
     }
     const float margin = sqrtf(R2) * (1.f + 0x1p-10f) + 0x1p-7f * wmax + 0x1p-16f * (cmax + lmax);
+    // Boxes go to c-bin units of this block's frame, u = (x - lo) n / L - c: three
+    // binary32 roundings of terms up to (cmax + lmax) n / L, covered by eps
+    float ueps[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) ueps[d] = 0x1p-10f + 0x1p-21f * (cmax + lmax) * G.inv[d];
     const float qnan = __int_as_float(0x7fc00000);
 
     // Stage chunk [c0, c0 + per) of the padded ranges: a warp per range part,
@@ -1597,7 +1610,6 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
                     pbz[2 + h] = -Q.x;
                     pc[h] = -Q.y;
                     pc[2 + h] = -Q.z;
-                    reinterpret_cast<int32_t*>(pQ + k)[h] = sl < sv ? qb + sl : -1;
                 }
                 const float x[3] = {P.x, P.y, P.z}, v[3] = {Q.x, Q.y, Q.z};
                 float lo[3], hi[3];
@@ -1613,10 +1625,18 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
                     q = max(q, __shfl_xor_sync(kFull, q, o));
                 }
                 if ((lane & (kCluster - 1)) == 0 && sl < s1) {
+                    // the test takes x_i - (x_j - shift): the box of x_j - shift, in c-bin
+                    // units from the block's c-bin corner
                     const int cl = sl / kCluster;
-                    cbx[cl] = make_float2(lo[0], hi[0]);
-                    cby[cl] = make_float2(lo[1], hi[1]);
-                    if (DIM == 3) cbz[cl] = make_float2(lo[2], hi[2]);
+                    float ul[3], uh[3];
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) {
+                        ul[d] = (lo[d] - rsh[r][d] - G.lo[d]) * G.inv[d] - (float)c[d];
+                        uh[d] = (hi[d] - rsh[r][d] - G.lo[d]) * G.inv[d] - (float)c[d];
+                    }
+                    cbx[cl] = unit_bounds(ul[0], uh[0], ueps[0]);
+                    cby[cl] = unit_bounds(ul[1], uh[1], ueps[1]);
+                    if (DIM == 3) cbz[cl] = unit_bounds(ul[2], uh[2], ueps[2]);
                     cqmax[cl] = q;
                 }
                 P = Pn;
@@ -1675,11 +1695,11 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
                 }
                 pmin = min(pmin, __shfl_xor_sync(kFull, pmin, o));
             }
-            if (lane == 0) {
+            if (lane == 0) {   // widened by the margin, in c-bin units of the block's frame
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    gbox[warp][d] = d < DIM ? wlo[d] - margin : 0.f;
-                    gbox[warp][3 + d] = d < DIM ? whi[d] + margin : 0.f;
+                    gbox[warp][d] = d < DIM ? (wlo[d] - margin - G.lo[d]) * G.inv[d] - (float)c[d] - ueps[d] : 0.f;
+                    gbox[warp][3 + d] = d < DIM ? (whi[d] + margin - G.lo[d]) * G.inv[d] - (float)c[d] + ueps[d] : 0.f;
                 }
                 gminp[warp] = pmin;
             }
@@ -1706,43 +1726,43 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
                 atomicMin(&b.bkey[p], partner_key<float>(d2, __float_as_uint(__ldg(&b.posA[q].w))));
                 atomicMin(&b.bkey[q], partner_key<float>(d2, tag));
             };
-            // the candidates of cluster cl (two staged pairs) against this lane's home
-            auto test_cluster = [&](auto has_shift, int cl, const PairShift& ps) {
+            // the candidates of cluster cl (two staged pairs) against this lane's home;
+            // slot s of the chunk holds sorted position qb + s (its range's offset)
+            auto test_cluster = [&](auto has_shift, int cl, int32_t qb, const PairShift& ps) {
                 constexpr bool SH = decltype(has_shift)::value;
                 const int k = cl * (kCluster / 2);
                 float2 rr0, a0, b0, rr1, a1, b1;
                 const uint2 w0 = paired_signs<DIM, SH>(ph, ps, pA[k], pB[k], pC[k], rr0, a0, b0);
                 const uint2 w1 = paired_signs<DIM, SH>(ph, ps, pA[k + 1], pB[k + 1], pC[k + 1], rr1, a1, b1);
                 if ((int)(w0.x | w0.y | w1.x | w1.y) < 0) {   // some candidate may pass: exact tests
-                    const int2 q0 = pQ[k], q1 = pQ[k + 1];
-                    if ((int)w0.x < 0 && pair_passes(ph, rr0.x, a0.x, b0.x)) close(rr0.x, a0.x, b0.x, q0.x);
-                    if ((int)w0.y < 0 && pair_passes(ph, rr0.y, a0.y, b0.y)) close(rr0.y, a0.y, b0.y, q0.y);
-                    if ((int)w1.x < 0 && pair_passes(ph, rr1.x, a1.x, b1.x)) close(rr1.x, a1.x, b1.x, q1.x);
-                    if ((int)w1.y < 0 && pair_passes(ph, rr1.y, a1.y, b1.y)) close(rr1.y, a1.y, b1.y, q1.y);
+                    const int32_t q = qb + 2 * k;   // a pad never passes (NaN)
+                    if ((int)w0.x < 0 && pair_passes(ph, rr0.x, a0.x, b0.x)) close(rr0.x, a0.x, b0.x, q);
+                    if ((int)w0.y < 0 && pair_passes(ph, rr0.y, a0.y, b0.y)) close(rr0.y, a0.y, b0.y, q + 1);
+                    if ((int)w1.x < 0 && pair_passes(ph, rr1.x, a1.x, b1.x)) close(rr1.x, a1.x, b1.x, q + 2);
+                    if ((int)w1.y < 0 && pair_passes(ph, rr1.y, a1.y, b1.y)) close(rr1.y, a1.y, b1.y, q + 3);
                 }
             };
             // clusters [cb0, cb1) of one range part: 32 box tests per ballot, then
             // the overlapping clusters.  A cluster whose positions all lie at or
             // below the group's lowest home holds no pair the group tests.
-            auto scan_batch = [&](auto has_shift, int cb0, int cb1, const float sh[3]) {
+            auto scan_batch = [&](auto has_shift, int cb0, int cb1, int32_t qb, const float sh[3]) {
                 const PairShift ps = pair_shift(sh);
                 for (int cb = cb0; cb < cb1; cb += 32) {
-                    // the group's box moved by the image shift meets the cluster's box
-                    // (x_i - (x_j - shift) = (x_i + shift) - x_j)
+                    // the group's box meets the cluster's (both in the block's frame)
                     const int cl = cb + lane;
                     bool ov = false;
                     if (cl < cb1) {
-                        const float2 bx = cbx[cl], by = cby[cl];
-                        ov = cqmax[cl] > pmin && bx.x <= whi[0] + sh[0] && wlo[0] + sh[0] <= bx.y &&
-                             by.x <= whi[1] + sh[1] && wlo[1] + sh[1] <= by.y;
+                        const float2 bx = __half22float2(cbx[cl]), by = __half22float2(cby[cl]);
+                        ov = cqmax[cl] > pmin && bx.x <= whi[0] && wlo[0] <= bx.y && by.x <= whi[1] &&
+                             wlo[1] <= by.y;
                         if (DIM == 3) {
-                            const float2 bz = cbz[cl];
-                            ov = ov && bz.x <= whi[2] + sh[2] && wlo[2] + sh[2] <= bz.y;
+                            const float2 bz = __half22float2(cbz[cl]);
+                            ov = ov && bz.x <= whi[2] && wlo[2] <= bz.y;
                         }
                     }
                     const unsigned m = __ballot_sync(kFull, ov);
                     wtests += (unsigned)(__popc(m) * kCluster) * ghomes;
-                    for (unsigned mm = m; mm; mm &= mm - 1) test_cluster(has_shift, cb + __ffs(mm) - 1, ps);
+                    for (unsigned mm = m; mm; mm &= mm - 1) test_cluster(has_shift, cb + __ffs(mm) - 1, qb, ps);
                 }
             };
             while (true) {
@@ -1789,8 +1809,9 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
                 const int r = batch[bi] >> 16, cb0 = batch[bi] & 0xffff;
                 const int cb1 = min(cb0 + kBatch, pb1[r] / kCluster);
                 const float sh[3] = {rsh[r][0], rsh[r][1], rsh[r][2]};
-                if (sh[0] != 0.f || sh[1] != 0.f || sh[2] != 0.f) scan_batch(std::true_type{}, cb0, cb1, sh);
-                else scan_batch(std::false_type{}, cb0, cb1, sh);
+                const int32_t qb = rq0[r] + c0 - ppre[r];   // sorted position of chunk slot s: qb + s
+                if (sh[0] != 0.f || sh[1] != 0.f || sh[2] != 0.f) scan_batch(std::true_type{}, cb0, cb1, qb, sh);
+                else scan_batch(std::false_type{}, cb0, cb1, qb, sh);
             }
         }
         __syncthreads();   // the next home chunk rewrites the group boxes and counters
