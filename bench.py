@@ -351,7 +351,7 @@ def ours(args):
     # ---------------- device-resident throughput (inputs already in HBM)
     r = run_device(k, w, seed, args.steps, args.warmup, stream, occ=args.occ, clocks=ClockSampler(local),
                    barrier=barrier, tile=(args.tile_threads, args.tile_cap, args.tile_split),
-                   flags=k.KMC_FLAG_NO_TILE_PRUNE if args.no_prune else 0)
+                   flags=(k.KMC_FLAG_NO_TILE_PRUNE if args.no_prune else 0) | args.flags)
     elapsed_ms = max_over_ranks([r["prof"]["total"]], world, "cuda")[0]
     pos, vel, cfg = r.pop("pos"), r.pop("vel"), r["cfg"]
 
@@ -715,6 +715,7 @@ def main():
     ap.add_argument("--tile-cap", type=int, default=0, help="tile search staging capacity (0: default)")
     ap.add_argument("--tile-split", type=int, default=0, help="tile search blocks per c-bin (0: default)")
     ap.add_argument("--no-prune", action="store_true", help="binary32 tile search without cluster pruning")
+    ap.add_argument("--flags", type=int, default=0, help="extra KMC_FLAG_* bits of the timed handle")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
