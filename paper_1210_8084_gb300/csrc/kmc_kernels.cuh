@@ -2317,7 +2317,7 @@ __global__ void __launch_bounds__(kStageThreads) search_staged_kernel(Bufs<T> b)
 // next step's search key / slot / histogram.  The particle's collisional
 // virial goes to vel.w for the moment pass.
 template <typename T, int DIM>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 1) move_kernel(Bufs<T> b) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 8 : 1) move_kernel(Bufs<T> b) {
     using V = typename Vec4<T>::type;
     __shared__ GeoT<T> G;
     if (threadIdx.x == 0) G.load(b.geo);
