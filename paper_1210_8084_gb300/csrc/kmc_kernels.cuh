@@ -2523,7 +2523,7 @@ __device__ __forceinline__ uint32_t tags_below(const uint32_t* __restrict__ t, u
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) scatter_kernel(Bufs<T> b) {
+__global__ void __launch_bounds__(kThreads, 8) scatter_kernel(Bufs<T> b) {
     using V = typename Vec4<T>::type;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= b.n) return;
