@@ -1435,12 +1435,17 @@ __device__ __forceinline__ uint32_t cell_key(const InstDev& I, int gx, int gy, i
 }
 
 // One block per c-bin c of a pruned instance.
-template <int DIM>
+template <int DIM, int CAPC>
 __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const GeoT<float>& G, const InstDev& I,
                                                    int inst, const int c[3], unsigned char* smem) {
     constexpr int F = DIM - 1;   // fastest key dimension
-    const int CAP = b.tile_cap & ~15;   // staged slots per chunk (a multiple of kCluster)
-    const int tid = threadIdx.x, lane = tid & 31, nthr = blockDim.x, warp = tid >> 5, nwarps = nthr >> 5;
+    // staged slots per chunk (a multiple of kCluster): for the default launch a
+    // compile-time constant (the shared-memory offsets become immediates), else
+    // the handle's
+    const int CAP = CAPC ? CAPC : (b.tile_cap & ~15);
+    // the default launch (CAPC != 0) has kTileThreads threads
+    const int tid = threadIdx.x, lane = tid & 31, nthr = CAPC ? kTileThreads : (int)blockDim.x;
+    const int warp = tid >> 5, nwarps = nthr >> 5;
     // staged pair k (slots 2k, 2k + 1): pA (-x, -x', -y, -y'), pB (-z, -z', -vx, -vx'),
     // pC (-vy, -vy', -vz, -vz')
     float4* pA = reinterpret_cast<float4*>(smem);
@@ -1847,7 +1852,7 @@ __device__ __forceinline__ int cbin_of_block(const Bufs<float>& b, const Geo& ge
 // The pruned tile search: one block per c-bin of the pruned instances (grid:
 // every c-bin; the others' blocks return at once).  A kernel of its own, so
 // that its registers are allocated apart from the plain tile search's.
-template <int DIM>
+template <int DIM, int CAPC>
 __global__ void __launch_bounds__(kTileThreads, 4) tile_pruned_kernel(Bufs<float> b) {
     extern __shared__ __align__(32) unsigned char tile_smem[];
     __shared__ GeoT<float> G;
@@ -1864,7 +1869,7 @@ __global__ void __launch_bounds__(kTileThreads, 4) tile_pruned_kernel(Bufs<float
     const InstDev& I = b.inst[inst_s];
     if (!I.prune) return;   // block-uniform
     const int c[3] = {c_s[0], c_s[1], c_s[2]};
-    tile_search_pruned<DIM>(b, G, I, inst_s, c, tile_smem);
+    tile_search_pruned<DIM, CAPC>(b, G, I, inst_s, c, tile_smem);
 }
 
 // The plain tile search: one block per c-bin of the tiled instances whose
@@ -3032,8 +3037,14 @@ cudaError_t launch_tile_search(const Bufs<T>& b, cudaStream_t s) {
     if constexpr (sizeof(T) == 4) {
         if (b.tile_prune) {
             const size_t smem = pruned_smem_bytes(b.tile_cap);
-            if (b.geo.dim == 3) tile_pruned_kernel<3><<<grid, b.tile_threads, smem, s>>>(b);
-            else tile_pruned_kernel<2><<<grid, b.tile_threads, smem, s>>>(b);
+            const bool dflt = (b.tile_cap & ~15) == kPrunedCap && b.tile_threads == kTileThreads;
+            if (b.geo.dim == 3) {
+                if (dflt) tile_pruned_kernel<3, kPrunedCap><<<grid, b.tile_threads, smem, s>>>(b);
+                else tile_pruned_kernel<3, 0><<<grid, b.tile_threads, smem, s>>>(b);
+            } else {
+                if (dflt) tile_pruned_kernel<2, kPrunedCap><<<grid, b.tile_threads, smem, s>>>(b);
+                else tile_pruned_kernel<2, 0><<<grid, b.tile_threads, smem, s>>>(b);
+            }
         }
     }
     return cudaGetLastError();
@@ -3053,8 +3064,11 @@ cudaError_t prepare_tile(const Bufs<T>& b) {
         e = cudaFuncSetAttribute(tile_search_kernel<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if constexpr (sizeof(T) == 4) {
         const int pb = (int)pruned_smem_bytes(b.tile_cap);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(tile_pruned_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(tile_pruned_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, pb);
+        const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(tile_pruned_kernel<3, kPrunedCap>, attr, pb);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(tile_pruned_kernel<3, 0>, attr, pb);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(tile_pruned_kernel<2, kPrunedCap>, attr, pb);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(tile_pruned_kernel<2, 0>, attr, pb);
     }
     return e;
 }
