@@ -1767,6 +1767,7 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
                     }
                     const unsigned m = __ballot_sync(kFull, ov);
                     wtests += (unsigned)(__popc(m) * kCluster) * ghomes;
+#pragma unroll 2
                     for (unsigned mm = m; mm; mm &= mm - 1) test_cluster(has_shift, cb + __ffs(mm) - 1, qb, ps);
                 }
             };
