@@ -21,7 +21,7 @@ constexpr int kFoldCap = 64;           // wall folds per coordinate per step
 constexpr int kAccFields = 10;         // per c-bin accumulator: N, Sum v (3), Sum v^2 (3), Sum W, collided
 constexpr int kTestSlots = 256;        // counters of the pruned tile search's pair tests (blocks spread over them)
 constexpr int kCbinRows = 4;           // rows of search cells per c-bin up to which moments go one warp per c-bin
-constexpr int kPrunedCap = 1920;       // default staging capacity of the pruned tile search (28 B per slot)
+constexpr int kPrunedCap = 1888;       // default staging capacity of the pruned tile search (28 B per slot)
                                        // count, Sum v.r_hat
 constexpr int kMomStride = 18;         // per c-bin output: 8 raw, 8 derived, Sum v.r_hat, v_r
 constexpr uint32_t kCanonMax = 16384;  // search cells up to this many particles are put in id order

@@ -1341,16 +1341,20 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
 // too far apart to meet within the step: a pair can pass criteria 1-2 only if,
 // at some time t in [0, dt], the two particles are within R of each other in
 // every coordinate.  So every particle is bounded by its swept box (the box of
-// the segment x .. x + v dt), a group of 32 homes and each cluster of kCluster
-// staged candidates by the union of theirs, and a warp tests a cluster only
-// when the group's box, widened by R and a rounding margin, overlaps the
-// cluster's.  For small boxes these instances search on half c-bins (2 search
-// cells per c-bin and dimension): the canonical (search cell, id) order then
-// groups every c-bin's particles by half c-bin, so consecutive homes and
-// consecutive candidates are close in space without any sort in the block.
-// The window is still the 3^D c-bin neighbourhood (criterion 3), as rows of
-// half c-bins.  The order of the tests changes nothing: every home's key and
-// every candidate's key take the minimum of theirs by atomicMin.
+// the segment x .. x + v dt), and each cluster of kCluster staged candidates and
+// each group of 32 homes by the union of theirs.  Two filters, both with boxes
+// widened by R and a rounding margin: a warp first checks 32 clusters against
+// its group's box (a lane per cluster), then every cluster that meets it
+// against each lane's own home box; the (home, cluster) pairs that meet go to
+// a per-warp queue, and the warp tests 32 queued pairs at a time (a lane per
+// pair: about one in seven of the group's pairs).  For small boxes these
+// instances search on half c-bins (2 search cells per c-bin and dimension):
+// the canonical (search cell, id) order then groups every c-bin's particles by
+// half c-bin, so consecutive homes and consecutive candidates are close in
+// space without any sort in the block.  The window is still the 3^D c-bin
+// neighbourhood (criterion 3), as rows of half c-bins.  The order of the tests
+// changes nothing: every home's key and every candidate's key take the minimum
+// of theirs by atomicMin.
 //
 // Rounding margin.  For a pair that the binary32 test accepts, exact arithmetic
 // on its rounded differences gives d^2 <= R^2 + 15 u |dr|^2 (u = 2^-24; the
@@ -1360,13 +1364,16 @@ __device__ __forceinline__ void tile_search_cell(const Bufs<T>& b, const GeoT<T>
 // [0, dt] the two particles are within R + sqrt(15 u) |dr| + 3 u |dr| +
 // 7 u |dv| dt + 6 u C of each other in every coordinate.  With |dr| <=
 // 2 sqrt(3) w (w the widest c-bin: both lie in one 3^D neighbourhood) that is
-// below R (1 + 2^-10) + 2^-7 w + 2^-16 C, the group's widening, plus 2^-12 of
-// each particle's |v dt|_1, the widening of every swept box.
+// below R (1 + 2^-10) + 2^-7 w + 2^-16 C, the widening of a home's or a
+// group's box, plus 2^-12 of each particle's |v dt|_1, the widening of every
+// swept box.
 constexpr int kSub = 2;          // search cells per c-bin and position dimension of a pruned instance
 constexpr int kSubRanges = 72;   // window rows (6 x 6 in 3-D) x 2 parts of the fast dimension
 constexpr int kCluster = 4;      // staged candidates per cluster (two staged pairs: one step of the loop)
 constexpr int kBatch = 64;       // clusters of one work item (a home group against them)
-constexpr int kMaxBatches = 128; // batches of one staged chunk: 6144 / kCluster / kBatch + kSubRanges < 128
+constexpr int kMaxBatches = 96;  // batches of one staged chunk: 6144 / kCluster / kBatch + kSubRanges = 96
+constexpr int kQueue = 64;       // (home, cluster) pairs a warp holds before testing them (a power of two)
+constexpr int32_t kNoHome = 0x7fffffff;   // sorted position of a lane without a home: above every cluster's
 
 // Swept box of one particle over the step, widened by 2^-12 |v dt|_1.
 template <int DIM>
@@ -1385,18 +1392,64 @@ __device__ __forceinline__ void swept_box(const float x[3], const float v[3], fl
     }
 }
 
+// One cluster of kCluster staged candidates: its box per dimension in the
+// block's frame in the form (lo, -hi) (two halves, c-bin units; the bits of a
+// __half2), and the sorted position of its first slot (slot j holds position
+// q0 + j; a pad slot holds NaN).
+struct __align__(16) ClusterBox {
+    uint32_t x, y, z;
+    int q0;
+};
+
+__device__ __forceinline__ uint32_t half2_bits(__half2 h) {
+    uint32_t u;
+    memcpy(&u, &h, sizeof(u));
+    return u;
+}
+
 // Dynamic shared memory of the pruned search for a capacity of `cap` staged
 // candidates (cap rounded down to a multiple of 16): six floats per staged
-// candidate, three half2 and one int per cluster.
+// candidate and one ClusterBox per cluster.
 __host__ __device__ constexpr size_t pruned_smem_bytes(int cap) {
     return (size_t)(24 + 16 / kCluster) * (size_t)(cap & ~15);
 }
 
-// Conservative half-precision bounds of a box coordinate in c-bin units of the
-// block's frame: lo rounded down, hi up, both widened by eps (the rounding of
-// the float map into those units).
-__device__ __forceinline__ __half2 unit_bounds(float lo, float hi, float eps) {
-    return __halves2half2(__float2half_rd(lo - eps), __float2half_ru(hi + eps));
+// Conservative half-precision bounds of a box [lo, hi] in c-bin units of the
+// block's frame, widened by eps (the rounding of the float map into those
+// units), in the two forms of one test: (lo, -hi) rounded down and (hi, -lo)
+// rounded up.  Boxes a and b meet in a dimension when both halves of a as
+// (lo, -hi) are at most those of b as (hi, -lo): lo_a <= hi_b and lo_b <= hi_a.
+__device__ __forceinline__ uint32_t box_lo_neghi(float lo, float hi, float eps) {
+    return half2_bits(__halves2half2(__float2half_rd(lo - eps), __float2half_rd(-(hi + eps))));
+}
+__device__ __forceinline__ uint32_t box_hi_neglo(float lo, float hi, float eps) {
+    return half2_bits(__halves2half2(__float2half_ru(hi + eps), __float2half_ru(eps - lo)));
+}
+
+// 1 when the boxes meet in all three dimensions (a: (lo, -hi), b: (hi, -lo)
+// per dimension), else 0: paired half-precision compares, no branch.
+__device__ __forceinline__ uint32_t boxes_meet3(uint32_t ax, uint32_t ay, uint32_t az, uint32_t bx, uint32_t by,
+                                                uint32_t bz) {
+    uint32_t r;
+    asm("{\n\t.reg .pred p0, p1, p2, p3, p4, p5;\n\t"
+        "setp.le.f16x2 p0|p1, %1, %4;\n\t"
+        "setp.le.f16x2 p2|p3, %2, %5;\n\t"
+        "setp.le.f16x2 p4|p5, %3, %6;\n\t"
+        "and.pred p0, p0, p1;\n\t"
+        "and.pred p2, p2, p3;\n\t"
+        "and.pred p4, p4, p5;\n\t"
+        "and.pred p0, p0, p2;\n\t"
+        "and.pred p0, p0, p4;\n\t"
+        "selp.u32 %0, 1, 0, p0;\n\t}"
+        : "=r"(r)
+        : "r"(ax), "r"(ay), "r"(az), "r"(bx), "r"(by), "r"(bz));
+    return r;
+}
+
+// Cluster c meets the box b (hi, -lo) per dimension and may hold a position
+// above q (in 2-D the third halves are 0 <= 0).
+__device__ __forceinline__ bool cluster_meets(const ClusterBox& c, const uint32_t b[3], int32_t q) {
+    return ((uint32_t)(c.q0 > q - (kCluster - 1)) & boxes_meet3(c.x, c.y, c.z, b[0], b[1], b[2])) != 0u;
 }
 
 // Exclusive prefix sums of v(0) ... v(n - 1), n <= 96, by one whole warp: lane
@@ -1451,21 +1504,18 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
     float4* pA = reinterpret_cast<float4*>(smem);
     float4* pB = pA + CAP / 2;
     float4* pC = pB + CAP / 2;
-    // cluster c: its box (lo, hi) per dimension in the block's frame (c-bin units
-    // from the c-bin's low corner, its range's image shift applied), and the
-    // largest sorted position in it
-    __half2* cbx = reinterpret_cast<__half2*>(pC + CAP / 2);
-    __half2* cby = cbx + CAP / kCluster;
-    __half2* cbz = cby + CAP / kCluster;
-    int* cqmax = reinterpret_cast<int*>(cbz + CAP / kCluster);
+    // cluster c: its box in the block's frame (c-bin units from the c-bin's low
+    // corner, its range's image shift applied) and its largest sorted position
+    ClusterBox* cbox = reinterpret_cast<ClusterBox*>(pC + CAP / 2);
     __shared__ int rq0[kSubRanges], rlen[kSubRanges], ppre[kSubRanges + 1], pb0[kSubRanges], pb1[kSubRanges];
     __shared__ float rsh[kSubRanges][3];
     __shared__ int hq0[4], hpre[5];                       // the c-bin's own rows (homes)
-    __shared__ float gbox[kTileThreads / 32][6];          // home group boxes (lo, hi), widened
+    __shared__ uint32_t gbox[kTileThreads / 32][3];       // home group boxes (hi, -lo), widened
     __shared__ int gminp[kTileThreads / 32];              // lowest sorted position of each home group
     __shared__ int gnext[kTileThreads / 32];              // next batch of each home group
-    __shared__ int batch[kMaxBatches];                    // batch i: range << 16 | first cluster
-    __shared__ int bpre[kSubRanges + 1];                  // first batch of each range's part
+    __shared__ int batch[kMaxBatches];                    // batch i: range << 18 | (clusters - 1) << 12 | first
+    __shared__ int bpre[kSubRanges + 1];                  // first batch of each segment (at its first range)
+    __shared__ unsigned short wqueue[kTileThreads / 32][kQueue];   // per warp: cluster << 5 | home lane
     __shared__ int nr_s;
     __shared__ unsigned long long blk_tests;
 
@@ -1570,6 +1620,14 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
 #pragma unroll
     for (int d = 0; d < DIM; ++d) ueps[d] = 0x1p-10f + 0x1p-21f * (cmax + lmax) * G.inv[d];
     const float qnan = __int_as_float(0x7fc00000);
+    // a swept box [lo, hi], widened by the margin, as (hi, -lo) in the block's frame
+    auto home_box = [&](const float lo[3], const float hi[3], uint32_t hb[3]) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            hb[d] = d < DIM ? box_hi_neglo((lo[d] - margin - G.lo[d]) * G.inv[d] - (float)c[d],
+                                           (hi[d] + margin - G.lo[d]) * G.inv[d] - (float)c[d], ueps[d])
+                            : 0u;
+    };
 
     // Stage chunk [c0, c0 + per) of the padded ranges: a warp per range part,
     // each slot gathers its candidate (a pad: NaN, position -1) with the next
@@ -1619,7 +1677,6 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
                 const float x[3] = {P.x, P.y, P.z}, v[3] = {Q.x, Q.y, Q.z};
                 float lo[3], hi[3];
                 swept_box<DIM>(x, v, dt, lo, hi);
-                int32_t q = sl < sv ? qb + sl : -1;
 #pragma unroll
                 for (int o = 1; o < kCluster; o <<= 1) {   // a pad's NaN drops out of fminf / fmaxf
 #pragma unroll
@@ -1627,33 +1684,69 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
                         lo[d] = fminf(lo[d], __shfl_xor_sync(kFull, lo[d], o));
                         hi[d] = fmaxf(hi[d], __shfl_xor_sync(kFull, hi[d], o));
                     }
-                    q = max(q, __shfl_xor_sync(kFull, q, o));
                 }
                 if ((lane & (kCluster - 1)) == 0 && sl < s1) {
                     // the test takes x_i - (x_j - shift): the box of x_j - shift, in c-bin
                     // units from the block's c-bin corner
-                    const int cl = sl / kCluster;
                     float ul[3], uh[3];
 #pragma unroll
                     for (int d = 0; d < DIM; ++d) {
                         ul[d] = (lo[d] - rsh[r][d] - G.lo[d]) * G.inv[d] - (float)c[d];
                         uh[d] = (hi[d] - rsh[r][d] - G.lo[d]) * G.inv[d] - (float)c[d];
                     }
-                    cbx[cl] = unit_bounds(ul[0], uh[0], ueps[0]);
-                    cby[cl] = unit_bounds(ul[1], uh[1], ueps[1]);
-                    if (DIM == 3) cbz[cl] = unit_bounds(ul[2], uh[2], ueps[2]);
-                    cqmax[cl] = q;
+                    ClusterBox cb;
+                    cb.x = box_lo_neghi(ul[0], uh[0], ueps[0]);
+                    cb.y = box_lo_neghi(ul[1], uh[1], ueps[1]);
+                    cb.z = DIM == 3 ? box_lo_neghi(ul[2], uh[2], ueps[2]) : 0u;
+                    cb.q0 = qb + sl;   // sl is the cluster's first slot (s0 and e0 are multiples of kCluster)
+                    cbox[sl / kCluster] = cb;
                 }
                 P = Pn;
                 Q = Qn;
             }
         }
-        if (warp == 0) {   // batch i: range << 16 | first cluster, ranges in order
-            warp_exclusive_scan96(nr, [&](int r) { return ((pb1[r] - pb0[r]) / kCluster + kBatch - 1) / kBatch; }, bpre);
+        if (warp == 0) {
+            // Segments: runs of consecutive ranges with the same image shift, whose
+            // clusters lie consecutively in the chunk.  Batches of up to kBatch
+            // clusters of one segment: range (the shift's) << 18 | (clusters - 1) << 12
+            // | first cluster.
+            auto starts = [&](int r) {   // range r starts a segment
+                return r < nr && (r == 0 || rsh[r][0] != rsh[r - 1][0] || rsh[r][1] != rsh[r - 1][1] ||
+                                  rsh[r][2] != rsh[r - 1][2]);
+            };
+            // bit r of the 96-bit word (m0, m1, m2): range r starts a segment
+            const unsigned m0 = __ballot_sync(kFull, starts(lane)), m1 = __ballot_sync(kFull, starts(32 + lane)),
+                           m2 = __ballot_sync(kFull, starts(64 + lane));
+            auto is_start = [&](int r) { return ((r < 32 ? m0 : r < 64 ? m1 : m2) >> (r & 31)) & 1u; };
+            auto seg_end = [&](int r) {   // the first range after segment start r that starts another, or nr
+                const int f = r + 1;
+                const unsigned w0 = f < 32 ? m0 & (~0u << f) : 0u;
+                const unsigned w1 = f < 32 ? m1 : f < 64 ? m1 & (~0u << (f - 32)) : 0u;
+                const unsigned w2 = f < 64 ? m2 : f < 96 ? m2 & (~0u << (f - 64)) : 0u;
+                const int e = w0 ? __ffs(w0) - 1 : w1 ? 31 + __ffs(w1) : w2 ? 63 + __ffs(w2) : nr;
+                return min(e, nr);
+            };
+            // clusters [a, z) of the segment starting at range r: ranges wholly before
+            // the chunk have pb0 = pb1 = 0, those wholly after it pb0 = pb1 >= cn
+            auto seg_span = [&](int r, int& a, int& z) {
+                a = min(pb0[r], cn) / kCluster;
+                z = min(pb1[seg_end(r) - 1], cn) / kCluster;
+            };
+            auto seg_batches = [&](int r) {
+                if (!is_start(r)) return 0;
+                int a, z;
+                seg_span(r, a, z);
+                return (z - a + kBatch - 1) / kBatch;
+            };
+            warp_exclusive_scan96(nr, seg_batches, bpre);
             __syncwarp();
-            for (int r = lane; r < nr; r += 32)
-                for (int j = 0, cl = pb0[r] / kCluster; cl < pb1[r] / kCluster; ++j, cl += kBatch)
-                    batch[bpre[r] + j] = (r << 16) | cl;
+            for (int r = lane; r < nr; r += 32) {
+                if (!is_start(r)) continue;
+                int a, z;
+                seg_span(r, a, z);
+                for (int j = bpre[r], cl = a; cl < z; ++j, cl += kBatch)
+                    batch[j] = (r << 18) | ((min(kBatch, z - cl) - 1) << 12) | cl;
+            }
         }
     };
 
@@ -1674,6 +1767,7 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
         while (k + 1 < kHomeRows && hpre[k + 1] <= i) ++k;
         return hq0[k] + (i - hpre[k]);
     };
+    unsigned short* queue = wqueue[warp];
     for (int hc = 0; hc < nh_all; hc += nthr) {
         const int nh = min(nthr, nh_all - hc);
         const int ngroups = (nh + 31) >> 5;
@@ -1700,12 +1794,11 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
                 }
                 pmin = min(pmin, __shfl_xor_sync(kFull, pmin, o));
             }
-            if (lane == 0) {   // widened by the margin, in c-bin units of the block's frame
+            if (lane == 0) {
+                uint32_t gb[3];
+                home_box(wlo, whi, gb);
 #pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    gbox[warp][d] = d < DIM ? (wlo[d] - margin - G.lo[d]) * G.inv[d] - (float)c[d] - ueps[d] : 0.f;
-                    gbox[warp][3 + d] = d < DIM ? (whi[d] + margin - G.lo[d]) * G.inv[d] - (float)c[d] + ueps[d] : 0.f;
-                }
+                for (int d = 0; d < 3; ++d) gbox[warp][d] = gb[d];
                 gminp[warp] = pmin;
             }
         }
@@ -1718,57 +1811,87 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
             __syncthreads();
             const int nbatch = bpre[nr];
             int g = warp % ngroups, loaded = -1;
-            PairHome ph;
-            float wlo[3], whi[3];
-            int32_t p = -1, pmin = 0;
+            float hx[3], hv[3];          // this lane's home
+            uint32_t hb[3];              // its box, (hi, -lo)
+            int32_t p = kNoHome;
             uint32_t tag = 0;
-            unsigned ghomes = 0;
-            // d^2 of a candidate that passed criteria 1-2; a home tests only
-            // candidates at higher sorted positions (each pair once)
-            auto close = [&](float rr, float a, float bb, int32_t q) {
-                if (q <= p) return;
+            // The warp's queue: (home lane, cluster) pairs whose boxes meet, n from
+            // qhead on (a ring of kQueue entries)
+            int qhead = 0, qn = 0;
+            // d^2 of a candidate that passed criteria 1-2, offered to both keys
+            auto close = [&](float rr, float a, float bb, int32_t hp, uint32_t htag, int32_t q, uint32_t qtag) {
                 const float d2 = R<float>::sub(rr, R<float>::div(R<float>::mul(a, a), bb));
-                atomicMin(&b.bkey[p], partner_key<float>(d2, __float_as_uint(__ldg(&b.posA[q].w))));
-                atomicMin(&b.bkey[q], partner_key<float>(d2, tag));
+                atomicMin(&b.bkey[hp], partner_key<float>(d2, qtag));
+                atomicMin(&b.bkey[q], partner_key<float>(d2, htag));
             };
-            // the candidates of cluster cl (two staged pairs) against this lane's home;
-            // slot s of the chunk holds sorted position qb + s (its range's offset)
-            auto test_cluster = [&](auto has_shift, int cl, int32_t qb, const PairShift& ps) {
+            // Test n (<= 32) queued pairs from qhead on: lane l takes entry qhead + l,
+            // the home of the entry's lane (by shuffles) against the entry's cluster
+            // (two staged pairs).  A home tests only candidates at higher sorted
+            // positions (each pair once).
+            auto test_queued = [&](auto has_shift, int n, const PairShift& ps) {
                 constexpr bool SH = decltype(has_shift)::value;
-                const int k = cl * (kCluster / 2);
-                float2 rr0, a0, b0, rr1, a1, b1;
-                const uint2 w0 = paired_signs<DIM, SH>(ph, ps, pA[k], pB[k], pC[k], rr0, a0, b0);
-                const uint2 w1 = paired_signs<DIM, SH>(ph, ps, pA[k + 1], pB[k + 1], pC[k + 1], rr1, a1, b1);
-                if ((int)(w0.x | w0.y | w1.x | w1.y) < 0) {   // some candidate may pass: exact tests
-                    const int32_t q = qb + 2 * k;   // a pad never passes (NaN)
-                    if ((int)w0.x < 0 && pair_passes(ph, rr0.x, a0.x, b0.x)) close(rr0.x, a0.x, b0.x, q);
-                    if ((int)w0.y < 0 && pair_passes(ph, rr0.y, a0.y, b0.y)) close(rr0.y, a0.y, b0.y, q + 1);
-                    if ((int)w1.x < 0 && pair_passes(ph, rr1.x, a1.x, b1.x)) close(rr1.x, a1.x, b1.x, q + 2);
-                    if ((int)w1.y < 0 && pair_passes(ph, rr1.y, a1.y, b1.y)) close(rr1.y, a1.y, b1.y, q + 3);
+                __syncwarp();   // the entries written by other lanes
+                const unsigned e = lane < n ? queue[(qhead + lane) & (kQueue - 1)] : 0u;
+                const int src = (int)(e & 31u), k = (int)(e >> 5) * (kCluster / 2);
+                const int32_t q = cbox[e >> 5].q0;   // candidate j at q + j (a pad never passes: NaN)
+                float xi[3], vi[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    xi[d] = __shfl_sync(kFull, hx[d], src);
+                    vi[d] = __shfl_sync(kFull, hv[d], src);
                 }
+                const int32_t hp = __shfl_sync(kFull, p, src);
+                const uint32_t htag = __shfl_sync(kFull, tag, src);
+                if (lane >= n) xi[0] = qnan;   // an empty lane fails every test
+                const PairHome h = pair_home(xi, vi, dt, R2);
+                float2 rr0, a0, b0, rr1, a1, b1;
+                const uint2 w0 = paired_signs<DIM, SH>(h, ps, pA[k], pB[k], pC[k], rr0, a0, b0);
+                const uint2 w1 = paired_signs<DIM, SH>(h, ps, pA[k + 1], pB[k + 1], pC[k + 1], rr1, a1, b1);
+                if ((int)(w0.x | w0.y | w1.x | w1.y) < 0) {   // some candidate may pass: exact tests
+                    unsigned pm = (w0.x >> 31) | (w0.y >> 31 << 1) | (w1.x >> 31 << 2) | (w1.y >> 31 << 3);
+                    const int32_t dj = hp - q;   // candidates j <= dj lie at or below the home
+                    if (dj >= 0) pm &= dj >= 3 ? 0u : 0xfu << (dj + 1);
+                    while (pm) {   // this lane's flagged candidates, one at a time
+                        const int j = __ffs(pm) - 1;
+                        pm &= pm - 1;
+                        const float rr = j == 0 ? rr0.x : j == 1 ? rr0.y : j == 2 ? rr1.x : rr1.y;
+                        const float a = j == 0 ? a0.x : j == 1 ? a0.y : j == 2 ? a1.x : a1.y;
+                        const float bb = j == 0 ? b0.x : j == 1 ? b0.y : j == 2 ? b1.x : b1.y;
+                        if (pair_passes(h, rr, a, bb))
+                            close(rr, a, bb, hp, htag, q + j, __float_as_uint(__ldg(&b.posA[q + j].w)));
+                    }
+                }
+                wtests += (unsigned)(n * kCluster);
+                qhead += n;
+                __syncwarp();   // the entries are read before they are written again
             };
-            // clusters [cb0, cb1) of one range part: 32 box tests per ballot, then
-            // the overlapping clusters.  A cluster whose positions all lie at or
-            // below the group's lowest home holds no pair the group tests.
-            auto scan_batch = [&](auto has_shift, int cb0, int cb1, int32_t qb, const float sh[3]) {
+            // clusters [cb0, cb1) of one range part: 32 checks against the group's box
+            // per ballot, then each overlapping cluster against every lane's own box;
+            // the pairs that meet go to the queue, which is tested 32 at a time.  A
+            // cluster whose positions all lie at or below a home holds no pair the
+            // home tests.
+            auto scan_batch = [&](auto has_shift, int cb0, int cb1, const float sh[3]) {
                 const PairShift ps = pair_shift(sh);
                 for (int cb = cb0; cb < cb1; cb += 32) {
-                    // the group's box meets the cluster's (both in the block's frame)
                     const int cl = cb + lane;
                     bool ov = false;
-                    if (cl < cb1) {
-                        const float2 bx = __half22float2(cbx[cl]), by = __half22float2(cby[cl]);
-                        ov = cqmax[cl] > pmin && bx.x <= whi[0] && wlo[0] <= bx.y && by.x <= whi[1] &&
-                             wlo[1] <= by.y;
-                        if (DIM == 3) {
-                            const float2 bz = __half22float2(cbz[cl]);
-                            ov = ov && bz.x <= whi[2] && wlo[2] <= bz.y;
+                    if (cl < cb1) ov = cluster_meets(cbox[cl], gbox[g], gminp[g]);
+                    for (unsigned m = __ballot_sync(kFull, ov); m; m &= m - 1) {
+                        const int cm = cb + __ffs(m) - 1;
+                        const bool hit = cluster_meets(cbox[cm], hb, p);
+                        const unsigned hm = __ballot_sync(kFull, hit);
+                        if (hit) queue[(qhead + qn + __popc(hm & ((1u << lane) - 1u))) & (kQueue - 1)] =
+                            (unsigned short)((cm << 5) | lane);
+                        qn += __popc(hm);
+                        if (qn >= 32) {
+                            test_queued(has_shift, 32, ps);
+                            qn -= 32;
                         }
                     }
-                    const unsigned m = __ballot_sync(kFull, ov);
-                    wtests += (unsigned)(__popc(m) * kCluster) * ghomes;
-#pragma unroll 2
-                    for (unsigned mm = m; mm; mm &= mm - 1) test_cluster(has_shift, cb + __ffs(mm) - 1, qb, ps);
+                }
+                if (qn > 0) {   // the batch's shift and positions end here
+                    test_queued(has_shift, qn, ps);
+                    qn = 0;
                 }
             };
             while (true) {
@@ -1791,33 +1914,27 @@ __device__ __forceinline__ void tile_search_pruned(const Bufs<float>& b, const G
                     g = -2 - bi;
                     continue;
                 }
-                if (g != loaded) {   // this group's homes (a lane without one fails every test)
+                if (g != loaded) {   // this group's homes (a lane without one meets no cluster)
                     loaded = g;
                     const int hi = g * 32 + lane;
                     float4 P = make_float4(qnan, qnan, qnan, qnan), Q = P;
-                    p = -1;
+                    p = kNoHome;
                     if (hi < nh) {
                         p = home_pos(hc + hi);
                         P = b.posA[p];
                         Q = b.velA[p];
                     }
-                    const float xi[3] = {P.x, P.y, P.z}, vi[3] = {Q.x, Q.y, Q.z};
-                    ph = pair_home(xi, vi, dt, R2);
+                    hx[0] = P.x; hx[1] = P.y; hx[2] = P.z;
+                    hv[0] = Q.x; hv[1] = Q.y; hv[2] = Q.z;
                     tag = __float_as_uint(P.w);
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        wlo[d] = gbox[g][d];
-                        whi[d] = gbox[g][3 + d];
-                    }
-                    pmin = gminp[g];
-                    ghomes = (unsigned)min(32, nh - g * 32);
+                    float lo[3], hi_[3];
+                    swept_box<DIM>(hx, hv, dt, lo, hi_);
+                    home_box(lo, hi_, hb);
                 }
-                const int r = batch[bi] >> 16, cb0 = batch[bi] & 0xffff;
-                const int cb1 = min(cb0 + kBatch, pb1[r] / kCluster);
+                const int be = batch[bi], r = be >> 18, cb0 = be & 0xfff, cb1 = cb0 + ((be >> 12) & 63) + 1;
                 const float sh[3] = {rsh[r][0], rsh[r][1], rsh[r][2]};
-                const int32_t qb = rq0[r] + c0 - ppre[r];   // sorted position of chunk slot s: qb + s
-                if (sh[0] != 0.f || sh[1] != 0.f || sh[2] != 0.f) scan_batch(std::true_type{}, cb0, cb1, qb, sh);
-                else scan_batch(std::false_type{}, cb0, cb1, qb, sh);
+                if (sh[0] != 0.f || sh[1] != 0.f || sh[2] != 0.f) scan_batch(std::true_type{}, cb0, cb1, sh);
+                else scan_batch(std::false_type{}, cb0, cb1, sh);
             }
         }
         __syncthreads();   // the next home chunk rewrites the group boxes and counters
