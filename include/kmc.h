@@ -88,7 +88,8 @@ extern "C" {
                                     * have 6 c-bins or more searches on half c-bins (sub_cells 2 per position
                                     * dimension) with one block per c-bin, where each group of 32 homes skips every
                                     * cluster of 4 candidates whose swept box (positions over the step) stays farther
-                                    * than R, plus a rounding margin, from the group's; same results */
+                                    * than R, plus a rounding margin, from the group's, and each home then every
+                                    * remaining cluster that stays as far from its own; same results */
 #define KMC_FLAG_ADAPTIVE_DT 16  /* timestep dt(t) = dx_min / v_max(t) of each step's start state (Sect. "Simulation
                                   * setup"; dx_min the smallest c-bin width, v_max the largest speed of the instance,
                                   * |v|^2 = fma(vz, vz, fma(vy, vy, vx vx)) in the state precision, the quotient in
@@ -148,10 +149,9 @@ typedef struct kmc_config {
 KMC_API int kmc_window_size(kmc_handle* h, double* mean_candidates);
 
 /* Pair tests the binary32 tile search has evaluated since kmc_init with its
- * pruning (KMC_FLAG_NO_TILE_PRUNE unset): for every cluster of 4 staged
- * candidates that a group of homes tests, 4 x the homes of the group (padding
- * slots of a window row's last cluster included).  0 for handles without that
- * search.
+ * pruning (KMC_FLAG_NO_TILE_PRUNE unset): 4 for every (home, cluster of 4
+ * staged candidates) pair whose boxes meet (padding slots of a window row's
+ * last cluster included).  0 for handles without that search.
  * The plain tile search tests (C_p - 1) / 2 pairs per particle, C_p from
  * kmc_window_size.  Synchronises the handle's stream. */
 KMC_API int kmc_tile_tests(kmc_handle* h, double* tests);
